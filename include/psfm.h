@@ -1,0 +1,259 @@
+/*
+ * psfm.h -- C ABI of the GB300 PSF-matching library (libpsfm.so).
+ *
+ * The library implements the data-parallel hot path of the PSF-matching method of Price &
+ * Magnier, "Pan-STARRS PSF-Matching for Subtraction and Stacking" (arXiv:1901.09999):
+ *   - solving for a spatially varying convolution kernel K that matches the PSF of a
+ *     reference image I1 to a science image I2 (Sec. 2, Eq. 2-6 with c_i = 0, p_i = 0),
+ *     with the ISIS Gaussian x polynomial basis (Eq. 7), stamps chosen per subregion and
+ *     discrepant stamps rejected over several iterations (Sec. 3.2-3.6);
+ *   - applying K to the whole image (Eq. 12), propagating the variance map (Eq. 13), the
+ *     covariance pseudo-matrix (Eq. 10-11, Sec. 4.3-4.4) and the mask (Sec. 3.4);
+ *   - PSF-homogenised stacking of several inputs (Sec. 5.1).
+ *
+ * Conventions shared by every entry point
+ *   Images are row-major, indexed [y][x] with x the fast axis, and share one row pitch
+ *   (in elements, >= width) given in psfm_shape.  float images are IEEE binary32;
+ *   masks are uint16 bit sets.  Unless a parameter says "host", every array pointer is
+ *   DEVICE memory on the current CUDA device, owned by the caller; the library never
+ *   frees or retains it.  Scratch memory comes from the caller's `workspace` (device,
+ *   256-byte aligned, at least psfm_workspace_size() bytes); the library allocates no
+ *   device memory on these paths.
+ *   Work is enqueued on `stream` (0 = legacy default stream).  psfm_convolve is
+ *   asynchronous; psfm_solve_kernel, psfm_subtract and psfm_stack synchronise `stream`
+ *   before returning because they fill host-side results.
+ *   Errors are returned as psfm_status; no exception or signal crosses the ABI.  Outputs
+ *   are undefined unless the call returns PSFM_OK.  Invalid sizes or pointers are rejected
+ *   with PSFM_ERR_BAD_ARG before any work is enqueued.
+ *
+ * Kernel convention (Eq. 12): O(x, y) = sum_{u,v} K_{x,y}(u, v) R(x-u, y-v) + d0, where
+ *   R is I1 with masked pixels set to zero (Sec. 3.4), off-image pixels count as zero,
+ *   and K_{x,y} = b0 delta + sum_k a_k(x, y) B_k with a_k(x, y) = sum_s a_{k,s} g_s(x, y),
+ *   g_s = xt^l yt^m, xt = 2x/(W-1) - 1, yt = 2y/(H-1) - 1 (Sec. 2).
+ * Basis (Eq. 7): for Gaussian g (width sigma_g, degree d_g) and p + q <= d_g,
+ *   B'_k(u, v) = psi_k u^p v^q exp(-(u^2+v^2) / (2 sigma_g^2)), psi_k giving unit L2 norm,
+ *   and B_k = B'_k - s_k delta with s_k = sum B'_k for p, q both even (else 0), so that
+ *   every B_k has zero sum (Sec. 2).
+ * Coefficient order ("canonical"): g ascending, then p = 0..d_g, then q = 0..d_g - p, then
+ *   the spatial term (l, m) with l = 0..S, m = 0..S-l; index = k * N_s + s.
+ */
+#ifndef PSFM_H
+#define PSFM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* psfm_stream; /* same handle as cudaStream_t */
+
+typedef int32_t psfm_status;
+#define PSFM_OK 0
+#define PSFM_ERR_BAD_ARG 1        /* invalid size, pointer, alignment or option */
+#define PSFM_ERR_TOO_FEW_STAMPS 2 /* fewer than 3 usable stamps (Sec. 3.7 quality cut) */
+#define PSFM_ERR_SINGULAR 3       /* normal equations not solvable (Cholesky and LU fail) */
+#define PSFM_ERR_NONFINITE 4      /* NaN or Inf in an unmasked input pixel used by the fit */
+#define PSFM_ERR_CUDA 5           /* a CUDA runtime call or kernel launch failed */
+#define PSFM_ERR_TIMEOUT 6        /* a bounded device-side wait ran out */
+#define PSFM_ERR_WORKSPACE 8      /* workspace too small, or a fixed-capacity table overflowed */
+#define PSFM_ERR_UNSUPPORTED 9    /* option combination this build does not implement */
+
+#define PSFM_MAX_GAUSS 4
+#define PSFM_MAX_DEGREE 8
+#define PSFM_MAX_HALF_WIDTH 24
+#define PSFM_MAX_SPATIAL_ORDER 3
+
+/* Image geometry: width W (x), height H (y), row pitch in elements (>= W). */
+typedef struct {
+  int32_t width, height;
+  int64_t pitch;
+} psfm_shape;
+
+/* Stamp centre pixel (Sec. 3.3). */
+typedef struct {
+  int32_t x, y;
+} psfm_stamp;
+
+/* ISIS kernel basis (Eq. 7): n_gauss Gaussians of width sigma[g] (pixels) carrying
+ * polynomials of total degree degree[g]; kernel (2*half_width+1)^2; spatial polynomial
+ * order spatial_order (Sec. 2).  bg_order must be 0 (constant differential background d0). */
+typedef struct {
+  int32_t n_gauss;
+  double sigma[PSFM_MAX_GAUSS];
+  int32_t degree[PSFM_MAX_GAUSS];
+  int32_t half_width;
+  int32_t spatial_order;
+  int32_t bg_order;
+} psfm_basis_spec;
+
+#define PSFM_NORM_SEPARATE 0 /* b0, d0 first, unweighted footprint sums (Sec. 3.2) */
+#define PSFM_NORM_JOINT 1    /* b0, d0 in the weighted fit with the kernel terms */
+
+#define PSFM_PREC_FP32 0     /* stamp Gram on CUDA cores, FP32 products, FP64 chunk sums */
+#define PSFM_PREC_TF32 1     /* stamp Gram on tensor cores (reserved) */
+#define PSFM_PREC_BF16X3 2   /* stamp Gram on tensor cores, 3xBF16 split (reserved) */
+
+/* Options; psfm_config_default() fills the defaults noted in brackets. */
+typedef struct {
+  int32_t grid_nx, grid_ny; /* stamp subregion grid [6, 5] (Sec. 3.3) */
+  int32_t stamp_half;       /* s: stamps are (2s+1)^2 pixels; < 0 means s = half_width [-1] */
+  int32_t max_cand;         /* candidates kept per subregion, 1..16 [8] */
+  double thresh_nsigma;     /* detection threshold over background [5] (Sec. 3.3) */
+  double reject_nsigma;     /* reject chi2 > mean + this * std [3] (Sec. 3.3) */
+  double soften_alpha;      /* chi2 denominator V1 + V2 + alpha |I2| [0.1] (Sec. 3.6) */
+  double bad_frac;          /* CONV.BAD radius: K^2 outside <= bad_frac of total [0.2] (Sec. 3.4) */
+  int32_t max_iter;         /* solves of the rejection loop, 1..16 [5] */
+  int32_t var_tile;         /* constant-kernel patch for variance, 8..256 [64] (Sec. 4.4) */
+  int32_t cov_grid;         /* n x n kernels averaged for the pseudo-matrix, 1..8 [5] (Sec. 4.4) */
+  int32_t norm_mode;        /* PSFM_NORM_* [SEPARATE] */
+  int32_t precision;        /* PSFM_PREC_* [FP32] */
+  uint16_t badmask;         /* input mask bits that mark a pixel unusable [0x00FF] */
+  uint16_t conv_bad;        /* CONV.BAD output bit [1 << 14] */
+  uint16_t conv_poor;       /* CONV.POOR output bit [1 << 15] */
+  uint16_t nodata;          /* stack pixel with no contributing input [1 << 0] */
+} psfm_config;
+
+#define PSFM_CAND_UNUSED 0
+#define PSFM_CAND_USED 1
+#define PSFM_CAND_REJECTED 2
+
+/* Result of a kernel solve.  All pointers are HOST memory owned by the caller; any of
+ * coeff, cand, cand_status, chi2 may be NULL to skip that output.  Candidate tables are
+ * laid out [region][rank], region = j * grid_nx + i (or one region per caller stamp). */
+typedef struct {
+  double b0;             /* normalisation (kernel sum), Sec. 3.2 */
+  double d0;             /* differential background */
+  double* coeff;         /* [n_coeff] canonical order a_{k,s} */
+  int32_t n_coeff;       /* capacity of coeff; must be >= N_b * N_s when coeff != NULL */
+  int32_t n_regions;     /* filled: number of regions */
+  int32_t max_cand;      /* filled: candidates per region */
+  int32_t cand_capacity; /* capacity of cand / cand_status / chi2 in entries */
+  psfm_stamp* cand;      /* [n_regions * max_cand] candidate centres, (-1,-1) = empty */
+  int32_t* cand_status;  /* PSFM_CAND_* */
+  double* chi2;          /* last chi^2 of each candidate, NaN if never active */
+  int32_t n_used;        /* stamps in the final solve */
+  int32_t n_iter;        /* solves performed */
+  int32_t r_bad;         /* CONV.BAD box radius (Sec. 3.4) */
+  double chi2_mean;      /* mean chi^2 over the final stamps (Sec. 3.6) */
+  double chi2_rms;       /* population std of chi^2 over the final stamps */
+  float median;          /* background of the detection image I1 + I2 */
+} psfm_solution;
+
+/* Fill `cfg` with the defaults listed in psfm_config. */
+void psfm_config_default(psfm_config* cfg);
+
+/* Human-readable name of a status code (static storage). */
+const char* psfm_status_string(psfm_status s);
+
+/* Number of basis terms N_b, spatial terms N_s and the width of the output covariance
+ * pseudo-matrix for an input pseudo-matrix of width cov_in_w (1 for white noise) combined
+ * with a science pseudo-matrix of width cov_img_w (0 if not subtracting): 2w + c - 2 with
+ * w = 2h+1 (Sec. 4.3), at least cov_img_w.  Return -1 on an invalid basis. */
+int32_t psfm_basis_size(const psfm_basis_spec* basis);
+int32_t psfm_spatial_size(const psfm_basis_spec* basis);
+int32_t psfm_cov_width(const psfm_basis_spec* basis, int32_t cov_in_w, int32_t cov_img_w);
+
+#define PSFM_OP_SOLVE 1
+#define PSFM_OP_CONVOLVE 2
+#define PSFM_OP_SUBTRACT 3
+#define PSFM_OP_STACK 4
+
+/* Bytes of device workspace an operation needs for this geometry and options
+ * (n_stamps: caller stamps, 0 to run the extractor; for PSFM_OP_STACK, the number of
+ * sources of the largest input).  0 on invalid arguments. */
+size_t psfm_workspace_size(int32_t op, psfm_shape shape, const psfm_basis_spec* basis,
+                           const psfm_config* cfg, int32_t n_stamps);
+
+/* Solve for the PSF-matching kernel (Sec. 2 Eq. 2-6 with c_i = p_i = 0; Sec. 3.2-3.6).
+ *   img = I2 (science, target), ref = I1 (reference, to be convolved); var_* are their
+ *   variance maps; mask_* their masks (pixels with any `badmask` bit are unusable).
+ *   Weights in the fit are 1 / (V1 + V2) (Eq. 5-6).
+ *   stamps / n_stamps: caller-chosen stamp centres (host), one region each, no
+ *   replacement; n_stamps == 0 runs the extractor (grid_nx x grid_ny subregions, up to
+ *   max_cand candidates each, replacement on rejection).
+ *   out: host result (see psfm_solution).  Synchronises `stream`. */
+psfm_status psfm_solve_kernel(const float* img, const float* ref, const float* var_img,
+                              const float* var_ref, const uint16_t* mask_img,
+                              const uint16_t* mask_ref, psfm_shape shape,
+                              const psfm_stamp* stamps, int32_t n_stamps,
+                              const psfm_basis_spec* basis, const psfm_config* cfg,
+                              psfm_solution* out, void* workspace, size_t ws_bytes,
+                              psfm_stream stream);
+
+/* Apply a solved kernel (Eq. 12-13, Sec. 3.4, Sec. 4.3-4.4).
+ *   ref, var_ref, mask_ref: I1 and its variance and mask (device).
+ *   img, var_img, mask_img: I2 and its maps, or all NULL.  With img set the outputs are the
+ *     difference D = I2 - (K (x) I1 + d0), its variance V2 + V' and mask m1 | m2 | flags;
+ *     without, the convolved image K (x) I1 + d0, V' and m1 | flags.
+ *   sol: host solution (b0, d0, coeff, r_bad are read).
+ *   cov_ref (device, cov_ref_w^2 doubles, odd width, centre = zero lag) is the input
+ *     pseudo-matrix of I1, NULL for white noise; cov_img likewise for I2 (difference only).
+ *   out, out_var, out_mask: device outputs with the input pitch; out_var / out_mask may be
+ *     NULL to skip them.  cov_out: device, cov_out_w^2 doubles, may be NULL; cov_out_w must
+ *     equal psfm_cov_width(basis, cov_ref_w or 1, cov_img_w or (img ? 1 : 0)).
+ *   V'(x, y) = f_t sum K_t(u,v)^2 V1(x-u, y-v) with K_t realised at the centre of the
+ *     var_tile x var_tile patch t and f_t its covariance factor (Sec. 4.4).
+ *   Asynchronous on `stream`. */
+psfm_status psfm_convolve(const float* ref, const float* var_ref, const uint16_t* mask_ref,
+                          const float* img, const float* var_img, const uint16_t* mask_img,
+                          psfm_shape shape, const psfm_basis_spec* basis,
+                          const psfm_config* cfg, const psfm_solution* sol,
+                          const double* cov_ref, int32_t cov_ref_w, const double* cov_img,
+                          int32_t cov_img_w, float* out, float* out_var, uint16_t* out_mask,
+                          double* cov_out, int32_t cov_out_w, void* workspace,
+                          size_t ws_bytes, psfm_stream stream);
+
+/* psfm_solve_kernel followed by psfm_convolve in difference mode, with the solution kept
+ * on the device between the two (one pass of the whole subtraction path).  `out` receives
+ * the solution as in psfm_solve_kernel.  Synchronises `stream` once, at the end. */
+psfm_status psfm_subtract(const float* img, const float* ref, const float* var_img,
+                          const float* var_ref, const uint16_t* mask_img,
+                          const uint16_t* mask_ref, psfm_shape shape,
+                          const psfm_stamp* stamps, int32_t n_stamps,
+                          const psfm_basis_spec* basis, const psfm_config* cfg,
+                          const double* cov_ref, int32_t cov_ref_w, const double* cov_img,
+                          int32_t cov_img_w, float* diff, float* diff_var,
+                          uint16_t* diff_mask, double* cov_out, int32_t cov_out_w,
+                          psfm_solution* out, void* workspace, size_t ws_bytes,
+                          psfm_stream stream);
+
+/* PSF-homogenised stack (Sec. 5.1-5.2).  For each of the n inputs (device image, variance,
+ * mask, all with `shape`): render the fake target, a circular Gaussian of FWHM
+ * target_fwhm at every source of src_xyf[i] (host, n_src[i] triples x, y, flux), solve for
+ * the kernel matching the input to it (I1 = input, I2 = target, V2 = 0), convolve the
+ * input, its variance and mask, and accumulate with weight w_i = 1 / mean(V'_i) over
+ * pixels without badmask or CONV.BAD bits:
+ *   out = sum w_i I'_i / sum w_i,  out_var = sum w_i^2 V'_i / (sum w_i)^2,
+ *   out_count = number of contributing inputs, out_mask = nodata where none contributed,
+ *   cov_out = pseudo-matrices averaged with weights w_i^2 mean(V'_i) (Sec. 4.4).
+ * basis[i] is the basis of input i (host array of n specs).  sols (host, may be NULL)
+ * receives the n solutions.  cov_out (device, may be NULL) has width
+ * max_i psfm_cov_width(&basis[i], 1, 0) = cov_out_w.  Synchronises `stream`. */
+psfm_status psfm_stack(int32_t n, const float* const* imgs, const float* const* vars,
+                       const uint16_t* const* masks, psfm_shape shape,
+                       const double* const* src_xyf, const int32_t* n_src, double target_fwhm,
+                       const psfm_basis_spec* basis, const psfm_config* cfg, float* out,
+                       float* out_var, uint16_t* out_mask, int32_t* out_count,
+                       double* cov_out, int32_t cov_out_w, psfm_solution* sols,
+                       void* workspace, size_t ws_bytes, psfm_stream stream);
+
+/* Instrumentation (no counterpart in the paper).  psfm_profile_enable(1) clears the stage
+ * table and starts recording a CUDA event pair around every stage the library enqueues
+ * (on the caller's stream); psfm_profile_enable(0) stops.  psfm_profile_entry(i, ...) reports
+ * stage i: its name (NUL-terminated, truncated to name_cap), total device milliseconds
+ * (synchronising on its events), kernels launched and times run; returns -1 if i is out of
+ * range.  psfm_launch_count() is the number of kernels the library has launched so far in
+ * this process, counted whether or not profiling is on. */
+void psfm_profile_enable(int32_t on);
+int32_t psfm_profile_count(void);
+int32_t psfm_profile_entry(int32_t i, char* name, int32_t name_cap, double* ms,
+                           long long* launches, long long* calls);
+long long psfm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSFM_H */

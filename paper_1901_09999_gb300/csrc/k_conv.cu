@@ -1,0 +1,264 @@
+// Spatially varying PSF-matching convolution of the whole image (Eq. 12 with the kernel of
+// Sec. 2): O(x, y) = b0 R + sum_k a_k(x, y) (B_k (x) R)(x, y) + d0, written as separable
+// passes.  With B_k = psi_k f_{g,p}(u) f_{g,q}(v) - s_k delta:
+//   H_{g,p}(x, y) = sum_u f_{g,p}(u) R(x-u, y)              (horizontal pass, one per plane)
+//   V_k(x, y)     = sum_v f_{g,q}(v) H_{g,p}(x, y-v)        (vertical pass, one per term)
+//   O(x, y)       = sum_k [a_k(x, y) psi_k] V_k + beta(x, y) R(x, y) + d0,
+//   beta(x, y)    = b0 - sum_k a_k(x, y) s_k,
+// where a_k(x, y) = sum_s a_{k,s} xt^l yt^m is evaluated per output pixel (Horner in xt, yt).
+//
+// One CTA computes a 32 x 64 output tile.  The masked reference with a halo of h pixels is
+// staged in shared memory once; for each Gaussian the horizontal passes of all its degrees
+// share each register window of the staged rows, and for each (g, p) plane every vertical
+// tap read from shared memory feeds the 8 output rows a thread owns and all degrees q.
+// Weights live in shared memory and are read as broadcast float4s.
+#include "psfm_internal.h"
+
+namespace psfm {
+namespace {
+
+struct ConvParams {
+  BasisDev b;
+  ImgGeom g;
+  const float* ref;
+  const uint16_t* mref;
+  const float* img;
+  float* out;
+  const float* f1d;
+  const double* psi;
+  const double* sk;
+  const double* dsol;
+  float xscale, yscale;
+  uint16_t badmask;
+};
+
+template <int HW>
+struct ConvShape {
+  static constexpr int W = 2 * HW + 1;
+  static constexpr int RS = kConvTX + ((2 * HW + 3) / 4) * 4;  // staged row stride (x4 floats)
+  static constexpr int RR = kConvTY + 2 * HW;                   // staged rows
+  static constexpr int NV4 = (4 + 2 * HW + 3) / 4;              // float4s per H window
+};
+
+__device__ __forceinline__ int spatial_index(int l, int m, int S) {
+  // l = 0..S, m = 0..S-l  ->  sum_{l'<l} (S - l' + 1) + m
+  return l * (S + 1) - (l * (l - 1)) / 2 + m;
+}
+
+// Polynomial sum_m yt^m (sum_l c[m][l] xt^l) with c laid out [m][l], (S+1)^2 entries.
+__device__ __forceinline__ void xpoly(const float* c, int S, float xt, float out[4]) {
+  const int S1 = S + 1;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float acc = 0.f;
+    if (m <= S) {
+#pragma unroll
+      for (int l = 3; l >= 0; --l)
+        if (l + m <= S) acc = fmaf(acc, xt, c[m * S1 + l]);
+    }
+    out[m] = acc;
+  }
+}
+
+__device__ __forceinline__ float ypoly(const float cm[4], int S, float yt) {
+  float acc = 0.f;
+#pragma unroll
+  for (int m = 3; m >= 0; --m)
+    if (m <= S) acc = fmaf(acc, yt, cm[m]);
+  return acc;
+}
+
+template <int HW>
+__global__ void __launch_bounds__(256, 2) k_conv_image(ConvParams P) {
+  using CS = ConvShape<HW>;
+  constexpr int TX = kConvTX, TY = kConvTY, W = CS::W, RS = CS::RS, RR = CS::RR;
+  constexpr int NV4 = CS::NV4;
+  extern __shared__ float4 smem4[];
+  float* Rs = reinterpret_cast<float*>(smem4);
+  float* Hs = Rs + RR * RS;
+  const int S = P.b.S, S1 = S + 1;
+  float* Ws = Hs + (P.b.dmax + 1) * RR * TX;
+  float* alpha = Ws + P.b.NH * P.b.wpad;
+  float* beta = alpha + P.b.Nb * S1 * S1;
+
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+
+  for (int i = tid; i < P.b.NH * P.b.wpad; i += 256) Ws[i] = P.f1d[i];
+  for (int i = tid; i < P.b.Nb * S1 * S1; i += 256) {
+    const int k = i / (S1 * S1), r = i - k * S1 * S1, m = r / S1, l = r - m * S1;
+    float v = 0.f;
+    if (l + m <= S) v = (float)(P.dsol[2 + k * P.b.Ns + spatial_index(l, m, S)] * P.psi[k]);
+    alpha[i] = v;
+  }
+  if (tid < S1 * S1) {
+    const int m = tid / S1, l = tid - m * S1;
+    double v = 0.0;
+    if (l + m <= S) {
+      const int s = spatial_index(l, m, S);
+      if (s == 0) v = P.dsol[0];
+      for (int k = 0; k < P.b.Nb; ++k) v -= P.dsol[2 + k * P.b.Ns + s] * P.sk[k];
+    }
+    beta[tid] = (float)v;
+  }
+  // masked reference tile with halo; zero padding to the row stride
+  for (int i = tid; i < RR * RS; i += 256) {
+    const int r = i / RS, c = i - r * RS;
+    const int gx = x0 - HW + c, gy = y0 - HW + r;
+    float v = 0.f;
+    if (c < TX + 2 * HW && gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
+      const int64_t o = (int64_t)gy * P.g.pitch + gx;
+      if (!(P.mref[o] & P.badmask)) v = P.ref[o];
+    }
+    Rs[i] = v;
+  }
+  __syncthreads();
+
+  const int lane = tid & 31, wi = tid >> 5;
+  const int gx = x0 + lane;
+  const float xt = (float)gx * P.xscale - 1.f;
+  float yt[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) yt[i] = (float)(y0 + wi * 8 + i) * P.yscale - 1.f;
+  float out[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) out[i] = 0.f;
+
+  for (int g = 0; g < P.b.ng; ++g) {
+    const int dg = P.b.deg[g];
+    const int pb = P.b.plane_base[g];
+    // ---- horizontal passes of every degree of Gaussian g over the staged rows
+    for (int item = tid; item < RR * 8; item += 256) {
+      const int row = item >> 3, xg = item & 7;
+      float rv[4 * NV4];
+      const float4* src = reinterpret_cast<const float4*>(Rs + row * RS + xg * 4);
+#pragma unroll
+      for (int j = 0; j < NV4; ++j) {
+        const float4 t = src[j];
+        rv[4 * j] = t.x;
+        rv[4 * j + 1] = t.y;
+        rv[4 * j + 2] = t.z;
+        rv[4 * j + 3] = t.w;
+      }
+      for (int n = 0; n <= dg; ++n) {
+        const float4* wn = reinterpret_cast<const float4*>(Ws + (pb + n) * P.b.wpad);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+        for (int t4 = 0; t4 < (W + 3) / 4; ++t4) {
+          const float4 wv = wn[t4];
+          const float wt[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int t = 4 * t4 + e;  // tap index, u = t - HW; R(x_j - u) = rv[j - t + 2HW]
+            if (t < W) {
+              a0 = fmaf(wt[e], rv[0 - t + 2 * HW], a0);
+              a1 = fmaf(wt[e], rv[1 - t + 2 * HW], a1);
+              a2 = fmaf(wt[e], rv[2 - t + 2 * HW], a2);
+              a3 = fmaf(wt[e], rv[3 - t + 2 * HW], a3);
+            }
+          }
+        }
+        *reinterpret_cast<float4*>(Hs + (n * RR + row) * TX + xg * 4) = make_float4(a0, a1, a2, a3);
+      }
+    }
+    __syncthreads();
+    // ---- vertical passes: each H value in registers serves 8 outputs and all q
+    for (int p = 0; p <= dg; ++p) {
+      float col[8 + 2 * HW];
+      const float* hp = Hs + (p * RR + wi * 8) * TX + lane;
+#pragma unroll
+      for (int t = 0; t < 8 + 2 * HW; ++t) col[t] = hp[t * TX];
+      const int kgp = P.b.kbase[g] + p * (dg + 1) - (p * (p - 1)) / 2;
+      for (int q = 0; q <= dg - p; ++q) {
+        const float4* wq = reinterpret_cast<const float4*>(Ws + (pb + q) * P.b.wpad);
+        float acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+#pragma unroll
+        for (int t4 = 0; t4 < (W + 3) / 4; ++t4) {
+          const float4 wv = wq[t4];
+          const float wt[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int t = 4 * t4 + e;  // v = t - HW; H(y_i - v) = col[i - t + 2HW]
+            if (t < W) {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) acc[i] = fmaf(wt[e], col[i - t + 2 * HW], acc[i]);
+            }
+          }
+        }
+        float cm[4];
+        xpoly(alpha + (kgp + q) * S1 * S1, S, xt, cm);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) out[i] = fmaf(ypoly(cm, S, yt[i]), acc[i], out[i]);
+      }
+    }
+    __syncthreads();
+  }
+
+  float cb[4];
+  xpoly(beta, S, xt, cb);
+  const float d0 = (float)P.dsol[1];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gy = y0 + wi * 8 + i;
+    const float r = Rs[(wi * 8 + i + HW) * RS + lane + HW];
+    float o = fmaf(ypoly(cb, S, yt[i]), r, out[i]) + d0;
+    if (gx < P.g.W && gy < P.g.H) {
+      const int64_t off = (int64_t)gy * P.g.pitch + gx;
+      if (P.img) o = P.img[off] - o;
+      P.out[off] = o;
+    }
+  }
+}
+
+template <int HW>
+cudaError_t launch_hw(const ConvParams& P, cudaStream_t st) {
+  using CS = ConvShape<HW>;
+  const int S1 = P.b.S + 1;
+  const size_t smem = sizeof(float) * ((size_t)CS::RR * CS::RS +
+                                       (size_t)(P.b.dmax + 1) * CS::RR * kConvTX +
+                                       (size_t)P.b.NH * P.b.wpad + (size_t)P.b.Nb * S1 * S1 +
+                                       (size_t)S1 * S1);
+  cudaError_t e = cudaFuncSetAttribute(k_conv_image<HW>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((P.g.W + kConvTX - 1) / kConvTX, (P.g.H + kConvTY - 1) / kConvTY);
+  k_conv_image<HW><<<grid, 256, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_conv_image(const Plan& p, const DevTables& t, const double* dsol,
+                              const float* ref, const uint16_t* mref, const float* img,
+                              float* out, cudaStream_t st) {
+  ConvParams P;
+  P.b = basis_dev(p);
+  P.g = ImgGeom{p.W, p.H, p.pitch};
+  P.ref = ref;
+  P.mref = mref;
+  P.img = img;
+  P.out = out;
+  P.f1d = t.f1d;
+  P.psi = t.psi;
+  P.sk = t.sk;
+  P.dsol = dsol;
+  P.xscale = p.W > 1 ? (float)(2.0 / (p.W - 1)) : 0.f;
+  P.yscale = p.H > 1 ? (float)(2.0 / (p.H - 1)) : 0.f;
+  P.badmask = p.cfg.badmask;
+  switch (p.h) {
+#define PSFM_CASE(n) \
+  case n:            \
+    return launch_hw<n>(P, st);
+    PSFM_CASE(1) PSFM_CASE(2) PSFM_CASE(3) PSFM_CASE(4) PSFM_CASE(5) PSFM_CASE(6)
+    PSFM_CASE(7) PSFM_CASE(8) PSFM_CASE(9) PSFM_CASE(10) PSFM_CASE(11) PSFM_CASE(12)
+    PSFM_CASE(13) PSFM_CASE(14) PSFM_CASE(15) PSFM_CASE(16) PSFM_CASE(17) PSFM_CASE(18)
+    PSFM_CASE(19) PSFM_CASE(20) PSFM_CASE(21) PSFM_CASE(22) PSFM_CASE(23) PSFM_CASE(24)
+#undef PSFM_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace psfm

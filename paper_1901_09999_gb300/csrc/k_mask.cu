@@ -1,0 +1,182 @@
+// Mask propagation through the convolution (Sec. 3.4) and the CONV.BAD radius.
+//
+// A masked input pixel (or the image edge) within Chebyshev distance r_bad of an output pixel
+// flags it CONV.BAD; one within h but none within r_bad flags CONV.POOR.  r_bad is the
+// smallest box radius outside which the squared kernel, realised at the image centre, holds
+// at most bad_frac of its total (Sec. 3.4).
+//
+// The dilation runs on bit planes: one 32-bit word per 32 pixels of a row, built with warp
+// ballots, dilated horizontally with funnel shifts, then vertically by OR-ing rows while the
+// output mask is written.
+#include "psfm_internal.h"
+
+namespace psfm {
+namespace {
+
+__global__ void k_mask_bits(const uint16_t* m1, const uint16_t* m2, int W, int H, int64_t pitch,
+                            int nwords, uint16_t badmask, uint32_t* bits) {
+  const int y = blockIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (x < W) {
+    const int64_t o = (int64_t)y * pitch + x;
+    uint16_t m = m1[o];
+    if (m2) m |= m2[o];
+    bad = (m & badmask) != 0;
+  }
+  const uint32_t word = __ballot_sync(0xffffffffu, bad);
+  const int wx = x >> 5;
+  if ((threadIdx.x & 31) == 0 && wx < nwords) bits[(int64_t)y * nwords + wx] = word;
+}
+
+// Bits beyond the row end count as masked (off-image).
+__device__ __forceinline__ uint32_t word_at(const uint32_t* row, int wx, int nwords, int W) {
+  if (wx < 0 || wx >= nwords) return 0xffffffffu;
+  uint32_t v = row[wx];
+  const int valid = W - wx * 32;
+  if (valid < 32) v |= ~((1u << valid) - 1u);
+  return v;
+}
+
+__device__ __forceinline__ uint32_t hdilate(uint32_t prev, uint32_t cur, uint32_t next, int r) {
+  const uint64_t lo = ((uint64_t)cur << 32) | prev;
+  const uint64_t hi = ((uint64_t)next << 32) | cur;
+  uint32_t out = cur;
+  for (int d = 1; d <= r; ++d) {
+    out |= (uint32_t)(lo >> (32 - d));  // neighbour at -d
+    out |= (uint32_t)(hi >> d);         // neighbour at +d
+  }
+  return out;
+}
+
+__global__ void k_mask_hdilate(const uint32_t* bits, int W, int H, int nwords, int r_fixed,
+                               const DevState* st, int h, uint32_t* hb_bad, uint32_t* hb_poor) {
+  const int y = blockIdx.y;
+  const int wx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (wx >= nwords) return;
+  const uint32_t* row = bits + (int64_t)y * nwords;
+  const uint32_t p = word_at(row, wx - 1, nwords, W);
+  const uint32_t c = word_at(row, wx, nwords, W);
+  const uint32_t n = word_at(row, wx + 1, nwords, W);
+  const int rb = r_fixed >= 0 ? r_fixed : st->r_bad;
+  hb_bad[(int64_t)y * nwords + wx] = hdilate(p, c, n, rb);
+  hb_poor[(int64_t)y * nwords + wx] = hdilate(p, c, n, h);
+}
+
+__global__ void k_mask_out(const uint32_t* hb_bad, const uint32_t* hb_poor, const uint16_t* m1,
+                           const uint16_t* m2, int W, int H, int64_t pitch, int nwords,
+                           int r_fixed, const DevState* st, int h, uint16_t conv_bad,
+                           uint16_t conv_poor, uint16_t* out) {
+  const int y = blockIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= W) return;
+  const int rb = r_fixed >= 0 ? r_fixed : st->r_bad;
+  const int wx = x >> 5;
+  const uint32_t bit = 1u << (x & 31);
+  bool bad = false, poor = false;
+  for (int dy = -h; dy <= h; ++dy) {
+    const int yy = y + dy;
+    const bool off = yy < 0 || yy >= H;
+    const int ady = dy < 0 ? -dy : dy;
+    if (ady <= rb) bad |= off || (hb_bad[(int64_t)yy * nwords + wx] & bit);
+    poor |= off || (hb_poor[(int64_t)yy * nwords + wx] & bit);
+  }
+  const int64_t o = (int64_t)y * pitch + x;
+  uint16_t m = m1[o];
+  if (m2) m |= m2[o];
+  if (bad)
+    m |= conv_bad;
+  else if (poor)
+    m |= conv_poor;
+  out[o] = m;
+}
+
+// r_bad from the kernel at the image centre (xt = yt = 0, so only the constant spatial term
+// survives), in FP64: K_c(u, v) = sum_k a_{k,0} psi_k f_{g,p}(u) f_{g,q}(v) + delta (b0 -
+// sum_k a_{k,0} s_k).  One CTA.
+__global__ void k_rbad(BasisDev b, const double* f1d64, const double* psi, const double* sk,
+                       const double* dsol, double bad_frac, DevState* st) {
+  extern __shared__ double sh[];
+  const int W = b.w, h = b.h;
+  double* colgp = sh;            // [NH][W]
+  double* K2 = colgp + b.NH * W; // [W*W]
+  double* part = K2 + W * W;     // [h+2]
+  const int tid = threadIdx.x;
+  if (st->error) return;
+  for (int i = tid; i < b.NH * W; i += blockDim.x) {
+    const int pl = i / W, v = i - pl * W;
+    int g = 0;
+    while (g + 1 < b.ng && pl >= b.plane_base[g + 1]) ++g;
+    const int p = pl - b.plane_base[g], dg = b.deg[g];
+    const int kgp = b.kbase[g] + p * (dg + 1) - (p * (p - 1)) / 2;
+    double c = 0.0;
+    for (int q = 0; q <= dg - p; ++q)
+      c += dsol[2 + (kgp + q) * b.Ns] * psi[kgp + q] * f1d64[(b.plane_base[g] + q) * W + v];
+    colgp[i] = c;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double dc = dsol[0];
+    for (int k = 0; k < b.Nb; ++k) dc -= dsol[2 + k * b.Ns] * sk[k];
+    part[h + 1] = dc;
+  }
+  __syncthreads();
+  for (int i = tid; i < W * W; i += blockDim.x) {
+    const int v = i / W, u = i - v * W;
+    double kv = 0.0;
+    for (int pl = 0; pl < b.NH; ++pl) kv += f1d64[pl * W + u] * colgp[pl * W + v];
+    if (u == h && v == h) kv += part[h + 1];
+    K2[i] = kv * kv;
+  }
+  __syncthreads();
+  // outside(r) = sum over max(|u|, |v|) > r, one thread per r
+  for (int r = tid; r <= h; r += blockDim.x) {
+    double o = 0.0;
+    for (int i = 0; i < W * W; ++i) {
+      const int v = i / W - h, u = i % W - h;
+      const int c = max(v < 0 ? -v : v, u < 0 ? -u : u);
+      if (c > r) o += K2[i];
+    }
+    part[r] = o;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < W * W; ++i) tot += K2[i];
+    int rb = h;
+    for (int r = 0; r <= h; ++r)
+      if (part[r] <= bad_frac * tot) {
+        rb = r;
+        break;
+      }
+    st->r_bad = rb;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_mask(const Plan& p, const ApplyBuffers& b, const uint16_t* mref,
+                        const uint16_t* mimg, uint16_t* out, cudaStream_t st) {
+  const int nwords = (p.W + 31) / 32;
+  dim3 blk(256);
+  k_mask_bits<<<dim3((p.W + 255) / 256, p.H), blk, 0, st>>>(mref, nullptr, p.W, p.H, p.pitch,
+                                                            nwords, p.cfg.badmask, b.bits);
+  k_mask_hdilate<<<dim3((nwords + 127) / 128, p.H), 128, 0, st>>>(
+      b.bits, p.W, p.H, nwords, -1, b.st, p.h, b.hb_bad, b.hb_poor);
+  k_mask_out<<<dim3((p.W + 255) / 256, p.H), blk, 0, st>>>(
+      b.hb_bad, b.hb_poor, mref, mimg, p.W, p.H, p.pitch, nwords, -1, b.st, p.h, p.cfg.conv_bad,
+      p.cfg.conv_poor, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rbad(const Plan& p, const DevTables& t, const double* dsol, DevState* ds,
+                        cudaStream_t st) {
+  const size_t smem = sizeof(double) * ((size_t)p.NH * p.w + (size_t)p.w * p.w + p.h + 2);
+  cudaError_t e = cudaFuncSetAttribute(k_rbad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_rbad<<<1, 256, smem, st>>>(basis_dev(p), t.f1d64, t.psi, t.sk, dsol, p.cfg.bad_frac, ds);
+  return cudaGetLastError();
+}
+
+}  // namespace psfm

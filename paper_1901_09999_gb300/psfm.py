@@ -1,0 +1,441 @@
+"""Python binding of libpsfm (the C ABI declared in include/psfm.h).
+
+The functions named like the C entry points (``psfm_solve_kernel``, ``psfm_convolve``,
+``psfm_subtract``, ``psfm_stack``, ``psfm_workspace_size`` ...) only marshal arguments:
+torch CUDA tensors are passed as device pointers, the current torch stream as the CUDA
+stream, and host results are converted to numpy.  Every pixel operation runs in the CUDA
+kernels of libpsfm.  If the shared library is missing, importing the functions raises: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpsfm.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "psfm.h")
+
+PSFM_OK = 0
+STATUS = {0: "OK", 1: "BAD_ARG", 2: "TOO_FEW_STAMPS", 3: "SINGULAR", 4: "NONFINITE", 5: "CUDA",
+          6: "TIMEOUT", 8: "WORKSPACE", 9: "UNSUPPORTED"}
+OP_SOLVE, OP_CONVOLVE, OP_SUBTRACT, OP_STACK = 1, 2, 3, 4
+NORM_SEPARATE, NORM_JOINT = 0, 1
+PREC_FP32, PREC_TF32, PREC_BF16X3 = 0, 1, 2
+CAND_UNUSED, CAND_USED, CAND_REJECTED = 0, 1, 2
+MAX_GAUSS = 4
+
+
+class PsfmError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = int(code)
+        super().__init__(f"{where}: psfm status {code} ({STATUS.get(int(code), '?')})")
+
+
+class psfm_shape(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("pitch", C.c_int64)]
+
+
+class psfm_stamp(C.Structure):
+    _fields_ = [("x", C.c_int32), ("y", C.c_int32)]
+
+
+class psfm_basis_spec(C.Structure):
+    _fields_ = [("n_gauss", C.c_int32), ("sigma", C.c_double * MAX_GAUSS),
+                ("degree", C.c_int32 * MAX_GAUSS), ("half_width", C.c_int32),
+                ("spatial_order", C.c_int32), ("bg_order", C.c_int32)]
+
+
+class psfm_config(C.Structure):
+    _fields_ = [("grid_nx", C.c_int32), ("grid_ny", C.c_int32), ("stamp_half", C.c_int32),
+                ("max_cand", C.c_int32), ("thresh_nsigma", C.c_double),
+                ("reject_nsigma", C.c_double), ("soften_alpha", C.c_double),
+                ("bad_frac", C.c_double), ("max_iter", C.c_int32), ("var_tile", C.c_int32),
+                ("cov_grid", C.c_int32), ("norm_mode", C.c_int32), ("precision", C.c_int32),
+                ("badmask", C.c_uint16), ("conv_bad", C.c_uint16), ("conv_poor", C.c_uint16),
+                ("nodata", C.c_uint16)]
+
+
+class psfm_solution(C.Structure):
+    _fields_ = [("b0", C.c_double), ("d0", C.c_double), ("coeff", C.POINTER(C.c_double)),
+                ("n_coeff", C.c_int32), ("n_regions", C.c_int32), ("max_cand", C.c_int32),
+                ("cand_capacity", C.c_int32), ("cand", C.POINTER(psfm_stamp)),
+                ("cand_status", C.POINTER(C.c_int32)), ("chi2", C.POINTER(C.c_double)),
+                ("n_used", C.c_int32), ("n_iter", C.c_int32), ("r_bad", C.c_int32),
+                ("chi2_mean", C.c_double), ("chi2_rms", C.c_double), ("median", C.c_float)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libpsfm.so (built by ``paper_1901_09999_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpsfm.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+    P = C.POINTER
+    lib.psfm_config_default.argtypes = [P(psfm_config)]
+    lib.psfm_config_default.restype = None
+    lib.psfm_status_string.argtypes = [i32]
+    lib.psfm_status_string.restype = C.c_char_p
+    lib.psfm_basis_size.argtypes = [P(psfm_basis_spec)]
+    lib.psfm_basis_size.restype = i32
+    lib.psfm_spatial_size.argtypes = [P(psfm_basis_spec)]
+    lib.psfm_spatial_size.restype = i32
+    lib.psfm_cov_width.argtypes = [P(psfm_basis_spec), i32, i32]
+    lib.psfm_cov_width.restype = i32
+    lib.psfm_workspace_size.argtypes = [i32, psfm_shape, P(psfm_basis_spec), P(psfm_config), i32]
+    lib.psfm_workspace_size.restype = sz
+    lib.psfm_solve_kernel.argtypes = [vp, vp, vp, vp, vp, vp, psfm_shape, P(psfm_stamp), i32,
+                                      P(psfm_basis_spec), P(psfm_config), P(psfm_solution), vp,
+                                      sz, vp]
+    lib.psfm_solve_kernel.restype = i32
+    lib.psfm_convolve.argtypes = [vp, vp, vp, vp, vp, vp, psfm_shape, P(psfm_basis_spec),
+                                  P(psfm_config), P(psfm_solution), vp, i32, vp, i32, vp, vp, vp,
+                                  vp, i32, vp, sz, vp]
+    lib.psfm_convolve.restype = i32
+    lib.psfm_subtract.argtypes = [vp, vp, vp, vp, vp, vp, psfm_shape, P(psfm_stamp), i32,
+                                  P(psfm_basis_spec), P(psfm_config), vp, i32, vp, i32, vp, vp, vp,
+                                  vp, i32, P(psfm_solution), vp, sz, vp]
+    lib.psfm_subtract.restype = i32
+    lib.psfm_stack.argtypes = [i32, P(vp), P(vp), P(vp), psfm_shape, P(P(C.c_double)), P(i32),
+                               C.c_double, P(psfm_basis_spec), P(psfm_config), vp, vp, vp, vp, vp,
+                               i32, P(psfm_solution), vp, sz, vp]
+    lib.psfm_stack.restype = i32
+    _lib = lib
+    return lib
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions include/psfm.h declares."""
+    txt = open(path).read()
+    return sorted(set(re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(psfm_\w+)\s*\(", txt, re.M)))
+
+
+# ------------------------------------------------------------------------ host structures
+
+def config(**kw) -> psfm_config:
+    c = psfm_config()
+    load().psfm_config_default(C.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise AttributeError(k)
+        setattr(c, k, v)
+    return c
+
+
+def basis_spec(sigma, degree, half_width, spatial_order=0) -> psfm_basis_spec:
+    b = psfm_basis_spec()
+    b.n_gauss = len(sigma)
+    for i, (s, d) in enumerate(zip(sigma, degree)):
+        b.sigma[i] = float(s)
+        b.degree[i] = int(d)
+    b.half_width = int(half_width)
+    b.spatial_order = int(spatial_order)
+    b.bg_order = 0
+    return b
+
+
+def basis_size(b):
+    return load().psfm_basis_size(C.byref(b))
+
+
+def spatial_size(b):
+    return load().psfm_spatial_size(C.byref(b))
+
+
+def cov_width(b, cov_in_w=1, cov_img_w=0):
+    return load().psfm_cov_width(C.byref(b), cov_in_w, cov_img_w)
+
+
+def status_string(s):
+    return load().psfm_status_string(int(s)).decode()
+
+
+def psfm_workspace_size(op, shape, basis, cfg, n_stamps=0) -> int:
+    return int(load().psfm_workspace_size(op, shape, C.byref(basis), C.byref(cfg), n_stamps))
+
+
+# ------------------------------------------------------------------------ torch marshalling
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _shape_of(*tensors) -> psfm_shape:
+    t0 = tensors[0]
+    H, W = t0.shape
+    pitch = t0.stride(0)
+    for t in tensors:
+        if t is None:
+            continue
+        if tuple(t.shape) != (H, W) or t.stride(1) != 1 or t.stride(0) != pitch:
+            raise ValueError("all images must share shape and row pitch, unit column stride")
+        if not t.is_cuda:
+            raise ValueError("images must be CUDA tensors")
+    return psfm_shape(W, H, pitch)
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _workspace(op, shape, basis, cfg, n_stamps, workspace, device):
+    torch = _torch()
+    need = psfm_workspace_size(op, shape, basis, cfg, n_stamps)
+    if need == 0:
+        raise PsfmError(1, "psfm_workspace_size")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=device)
+    return workspace, need
+
+
+class Solution:
+    """Host copy of a psfm_solution with numpy arrays."""
+
+    def __init__(self, ncoef, ncand):
+        self.coeff = np.zeros(max(1, ncoef))
+        self.cand = (psfm_stamp * max(1, ncand))()
+        self.status = np.zeros(max(1, ncand), np.int32)
+        self.chi2 = np.zeros(max(1, ncand))
+        self.c = psfm_solution()
+        self.c.coeff = self.coeff.ctypes.data_as(C.POINTER(C.c_double))
+        self.c.n_coeff = ncoef
+        self.c.cand_capacity = ncand
+        self.c.cand = C.cast(self.cand, C.POINTER(psfm_stamp))
+        self.c.cand_status = self.status.ctypes.data_as(C.POINTER(C.c_int32))
+        self.c.chi2 = self.chi2.ctypes.data_as(C.POINTER(C.c_double))
+        self.ncoef = ncoef
+        self.ncand = ncand
+
+    @classmethod
+    def from_values(cls, b0, d0, coeff, r_bad=0):
+        s = cls(len(coeff), 1)
+        s.coeff[:] = coeff
+        s.c.b0, s.c.d0, s.c.r_bad = float(b0), float(d0), int(r_bad)
+        return s
+
+    @property
+    def b0(self):
+        return self.c.b0
+
+    @property
+    def d0(self):
+        return self.c.d0
+
+    @property
+    def r_bad(self):
+        return self.c.r_bad
+
+    @property
+    def n_used(self):
+        return self.c.n_used
+
+    @property
+    def n_iter(self):
+        return self.c.n_iter
+
+    @property
+    def chi2_mean(self):
+        return self.c.chi2_mean
+
+    @property
+    def chi2_rms(self):
+        return self.c.chi2_rms
+
+    @property
+    def median(self):
+        return self.c.median
+
+    def candidates(self):
+        n = self.c.n_regions * self.c.max_cand
+        xy = np.array([(self.cand[i].x, self.cand[i].y) for i in range(n)], np.int32)
+        return (xy.reshape(self.c.n_regions, self.c.max_cand, 2),
+                self.status[:n].reshape(self.c.n_regions, self.c.max_cand).copy(),
+                self.chi2[:n].reshape(self.c.n_regions, self.c.max_cand).copy())
+
+
+def _stamps_arg(stamps):
+    if stamps is None or len(stamps) == 0:
+        return None, 0, None
+    arr = (psfm_stamp * len(stamps))(*[psfm_stamp(int(x), int(y)) for x, y in stamps])
+    return C.cast(arr, C.POINTER(psfm_stamp)), len(stamps), arr
+
+
+def _ncand(basis, cfg, n_stamps):
+    return n_stamps if n_stamps > 0 else cfg.grid_nx * cfg.grid_ny * cfg.max_cand
+
+
+def psfm_solve_kernel(img, ref, var_img, var_ref, mask_img, mask_ref, basis, cfg, stamps=None,
+                      workspace=None, stream=None) -> Solution:
+    """Solve for the PSF-matching kernel on the GPU (C: psfm_solve_kernel)."""
+    lib = load()
+    shape = _shape_of(img, ref, var_img, var_ref, mask_img, mask_ref)
+    sp, ns, _keep = _stamps_arg(stamps)
+    ws, need = _workspace(OP_SOLVE, shape, basis, cfg, ns, workspace, img.device)
+    sol = Solution(basis_size(basis) * spatial_size(basis), _ncand(basis, cfg, ns))
+    st = lib.psfm_solve_kernel(_ptr(img), _ptr(ref), _ptr(var_img), _ptr(var_ref), _ptr(mask_img),
+                               _ptr(mask_ref), shape, sp, ns, C.byref(basis), C.byref(cfg),
+                               C.byref(sol.c), _ptr(ws), need, _stream(stream))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_solve_kernel")
+    return sol
+
+
+def psfm_convolve(ref, var_ref, mask_ref, basis, cfg, sol: Solution, img=None, var_img=None,
+                  mask_img=None, cov_ref=None, cov_img=None, out=None, out_var=None,
+                  out_mask=None, want_var=True, want_mask=True, want_cov=True, workspace=None,
+                  stream=None):
+    """Apply a solved kernel (C: psfm_convolve).  Returns (out, out_var, out_mask, cov)."""
+    torch = _torch()
+    lib = load()
+    shape = _shape_of(ref, var_ref, mask_ref, img, var_img, mask_img)
+    dev = ref.device
+    if out is None:
+        out = torch.empty_like(ref)
+    if want_var and out_var is None:
+        out_var = torch.empty_like(ref)
+    if want_mask and out_mask is None:
+        out_mask = torch.empty_like(mask_ref)
+    c_ref = 1 if cov_ref is None else cov_ref.shape[0]
+    c_img = 0 if img is None else (1 if cov_img is None else cov_img.shape[0])
+    cov = None
+    ncov = 0
+    if want_cov:
+        ncov = cov_width(basis, c_ref, c_img)
+        cov = torch.empty((ncov, ncov), dtype=torch.float64, device=dev)
+    ws, need = _workspace(OP_CONVOLVE, shape, basis, cfg, 0, workspace, dev)
+    st = lib.psfm_convolve(_ptr(ref), _ptr(var_ref), _ptr(mask_ref), _ptr(img), _ptr(var_img),
+                           _ptr(mask_img), shape, C.byref(basis), C.byref(cfg), C.byref(sol.c),
+                           _ptr(cov_ref), c_ref, _ptr(cov_img), c_img if cov_img is not None else 0,
+                           _ptr(out), _ptr(out_var), _ptr(out_mask), _ptr(cov), ncov, _ptr(ws), need,
+                           _stream(stream))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_convolve")
+    return out, out_var, out_mask, cov
+
+
+def psfm_subtract(img, ref, var_img, var_ref, mask_img, mask_ref, basis, cfg, stamps=None,
+                  cov_ref=None, cov_img=None, out=None, out_var=None, out_mask=None,
+                  want_cov=True, workspace=None, stream=None, solution=True):
+    """Solve and subtract in one call (C: psfm_subtract).
+
+    Returns (diff, diff_var, diff_mask, cov, Solution or None)."""
+    torch = _torch()
+    lib = load()
+    shape = _shape_of(img, ref, var_img, var_ref, mask_img, mask_ref)
+    dev = img.device
+    sp, ns, _keep = _stamps_arg(stamps)
+    out = torch.empty_like(img) if out is None else out
+    out_var = torch.empty_like(img) if out_var is None else out_var
+    out_mask = torch.empty_like(mask_img) if out_mask is None else out_mask
+    c_ref = 1 if cov_ref is None else cov_ref.shape[0]
+    c_img = 1 if cov_img is None else cov_img.shape[0]
+    cov, ncov = None, 0
+    if want_cov:
+        ncov = cov_width(basis, c_ref, c_img)
+        cov = torch.empty((ncov, ncov), dtype=torch.float64, device=dev)
+    ws, need = _workspace(OP_SUBTRACT, shape, basis, cfg, ns, workspace, dev)
+    sol = Solution(basis_size(basis) * spatial_size(basis), _ncand(basis, cfg, ns)) if solution else None
+    st = lib.psfm_subtract(_ptr(img), _ptr(ref), _ptr(var_img), _ptr(var_ref), _ptr(mask_img),
+                           _ptr(mask_ref), shape, sp, ns, C.byref(basis), C.byref(cfg),
+                           _ptr(cov_ref), c_ref, _ptr(cov_img), c_img if cov_img is not None else 0,
+                           _ptr(out), _ptr(out_var), _ptr(out_mask), _ptr(cov), ncov,
+                           C.byref(sol.c) if sol else None, _ptr(ws), need, _stream(stream))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_subtract")
+    return out, out_var, out_mask, cov, sol
+
+
+def psfm_stack(imgs, vars_, masks, sources, target_fwhm, bases, cfg, want_cov=True,
+               workspace=None, stream=None):
+    """PSF-homogenised stack (C: psfm_stack).  ``sources`` is a list of (n, 3) float64 numpy
+    arrays (x, y, flux) per input; ``bases`` a list of psfm_basis_spec.
+
+    Returns (image, variance, mask, count, cov, [Solution])."""
+    torch = _torch()
+    lib = load()
+    n = len(imgs)
+    shape = _shape_of(*imgs, *vars_, *masks)
+    dev = imgs[0].device
+    out = torch.empty_like(imgs[0])
+    out_var = torch.empty_like(imgs[0])
+    out_mask = torch.empty_like(masks[0])
+    out_count = torch.empty(imgs[0].shape, dtype=torch.int32, device=dev)
+    if out_count.stride(0) != shape.pitch:
+        raise ValueError("stack inputs must be contiguous")
+    srcs = [np.ascontiguousarray(s, np.float64) for s in sources]
+    nsrc = (C.c_int32 * n)(*[len(s) for s in srcs])
+    sp = (C.POINTER(C.c_double) * n)(*[s.ctypes.data_as(C.POINTER(C.c_double)) for s in srcs])
+    bs = (psfm_basis_spec * n)(*bases)
+    big = max(range(n), key=lambda i: psfm_workspace_size(OP_STACK, shape, bases[i], cfg, max(len(s) for s in srcs)))
+    need = psfm_workspace_size(OP_STACK, shape, bases[big], cfg, max(len(s) for s in srcs))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    ncov = max(cov_width(b, 1, 0) for b in bases)
+    cov = torch.empty((ncov, ncov), dtype=torch.float64, device=dev) if want_cov else None
+    sols = [Solution(basis_size(b) * spatial_size(b), _ncand(b, cfg, 0)) for b in bases]
+    csols = (psfm_solution * n)(*[s.c for s in sols])
+    ptrs = lambda ts: (C.c_void_p * n)(*[t.data_ptr() for t in ts])
+    st = lib.psfm_stack(n, ptrs(imgs), ptrs(vars_), ptrs(masks), shape, sp, nsrc, float(target_fwhm),
+                        bs, C.byref(cfg), _ptr(out), _ptr(out_var), _ptr(out_mask), _ptr(out_count),
+                        _ptr(cov), ncov if want_cov else 0, csols, _ptr(workspace), need,
+                        _stream(stream))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_stack")
+    for s, c in zip(sols, csols):
+        s.c = c
+    return out, out_var, out_mask, out_count, cov, sols
+
+
+# ------------------------------------------------------------------------ instrumentation
+
+def _prof_types(lib):
+    lib.psfm_profile_enable.argtypes = [C.c_int32]
+    lib.psfm_profile_enable.restype = None
+    lib.psfm_profile_count.argtypes = []
+    lib.psfm_profile_count.restype = C.c_int32
+    lib.psfm_profile_entry.argtypes = [C.c_int32, C.c_char_p, C.c_int32, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+    lib.psfm_profile_entry.restype = C.c_int32
+    lib.psfm_launch_count.argtypes = []
+    lib.psfm_launch_count.restype = C.c_longlong
+
+
+def psfm_profile_enable(on: bool):
+    lib = load()
+    _prof_types(lib)
+    lib.psfm_profile_enable(1 if on else 0)
+
+
+def psfm_launch_count() -> int:
+    lib = load()
+    _prof_types(lib)
+    return int(lib.psfm_launch_count())
+
+
+def psfm_profile_read() -> dict:
+    """{stage: (device ms total, kernel launches, calls)} since psfm_profile_enable(True)."""
+    lib = load()
+    _prof_types(lib)
+    out = {}
+    for i in range(lib.psfm_profile_count()):
+        name = C.create_string_buffer(64)
+        ms, nl, nc = C.c_double(), C.c_longlong(), C.c_longlong()
+        if lib.psfm_profile_entry(i, name, 64, C.byref(ms), C.byref(nl), C.byref(nc)) == 0:
+            out[name.value.decode()] = (ms.value, nl.value, nc.value)
+    return out

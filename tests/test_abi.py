@@ -1,0 +1,63 @@
+"""The C ABI library builds, loads without a GPU and exports every function include/psfm.h
+declares; host-only entry points (defaults, sizes, argument checks) behave as documented."""
+import ctypes as C
+
+import pytest
+
+from paper_1901_09999_gb300 import build as B
+from paper_1901_09999_gb300 import psfm as P
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return P.load()
+
+
+def test_exports_every_declared_function(lib):
+    names = P.header_functions()
+    assert {"psfm_solve_kernel", "psfm_convolve", "psfm_subtract", "psfm_stack",
+            "psfm_workspace_size", "psfm_status_string"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_defaults_and_sizes(lib):
+    cfg = P.config()
+    assert (cfg.grid_nx, cfg.grid_ny, cfg.max_iter, cfg.var_tile, cfg.cov_grid) == (6, 5, 5, 64, 5)
+    assert cfg.thresh_nsigma == 5.0 and cfg.reject_nsigma == 3.0 and cfg.bad_frac == 0.2
+    assert cfg.conv_bad == 1 << 14 and cfg.conv_poor == 1 << 15
+    b1 = P.basis_spec((0.7, 1.5, 3.0), (4, 2, 2), 10, 0)
+    b2 = P.basis_spec((0.8, 1.6, 3.2), (6, 4, 2), 15, 2)
+    assert P.basis_size(b1) == 27 and P.basis_size(b2) == 49
+    assert P.spatial_size(b1) == 1 and P.spatial_size(b2) == 6
+    assert P.cov_width(b2, 1, 0) == 61 and P.cov_width(b2, 5, 0) == 65 and P.cov_width(b2, 1, 101) == 101
+    assert P.cov_width(b2, 2, 0) == -1
+    assert P.status_string(2).startswith("fewer than 3")
+    shape = P.psfm_shape(4846, 4868, 4848)
+    for op in (P.OP_SOLVE, P.OP_CONVOLVE, P.OP_SUBTRACT):
+        assert P.psfm_workspace_size(op, shape, b2, P.config(grid_nx=15, grid_ny=20)) > 0
+    assert P.psfm_workspace_size(7, shape, b2, cfg) == 0
+    bad = P.basis_spec((0.8,), (6,), 40, 0)          # half width above the maximum
+    assert P.psfm_workspace_size(P.OP_CONVOLVE, shape, bad, cfg) == 0
+
+
+def test_argument_errors_are_caught_on_the_host(lib):
+    """Null or inconsistent arguments return BAD_ARG before any CUDA call."""
+    cfg = P.config()
+    b = P.basis_spec((1.0,), (2,), 5, 0)
+    shape = P.psfm_shape(64, 64, 64)
+    sol = P.Solution(6, 1)
+    st = lib.psfm_convolve(None, None, None, None, None, None, shape, C.byref(b), C.byref(cfg),
+                           C.byref(sol.c), None, 1, None, 0, None, None, None, None, 0, None, 0,
+                           None)
+    assert st == 1
+    bad_shape = P.psfm_shape(64, 64, 32)             # pitch below width
+    st = lib.psfm_solve_kernel(None, None, None, None, None, None, bad_shape, None, 0, C.byref(b),
+                               C.byref(cfg), C.byref(sol.c), None, 0, None)
+    assert st == 1
+    cfg2 = P.config(var_tile=32)
+    st = lib.psfm_convolve(None, None, None, None, None, None, shape, C.byref(b), C.byref(cfg2),
+                           C.byref(sol.c), None, 1, None, 0, None, None, None, None, 0, None, 0,
+                           None)
+    assert st == 9

@@ -1,0 +1,148 @@
+"""GPU parity of the kernel solve (psfm_solve_kernel / psfm_subtract through the C ABI)
+against the FP64 oracle: stamp candidates, rejection decisions and statuses bit-exact;
+normalisation, coefficients and realised kernels within tolerance; error codes."""
+import numpy as np
+import pytest
+
+from gpu_common import (IMG_TOL_SIGMA, VAR_RTOL, coeff_rel_err, device, host, kernel_rel_err,
+                        oracle_solution_from_gpu, specs, upload)
+from oracle import psfm_oracle as O
+from paper_1901_09999_gb300 import psfm as P
+from paper_1901_09999_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+# Realised-kernel agreement (normwise, at sample points) and b0: the stamp design blocks are
+# FP32 on the GPU, so the solution differs from the FP64 oracle by the FP32 perturbation of
+# the normal equations amplified by their condition number.
+KERNEL_RTOL = 1e-4
+B0_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return device()
+
+
+def _check_solution(sol, osol, ob, W, H):
+    cand, stat, chi2 = sol.candidates()
+    assert np.array_equal(cand, osol.cand)
+    assert np.array_equal(stat, osol.status)
+    assert sol.n_iter == osol.n_iter and sol.n_used == osol.n_used
+    both = ~np.isnan(osol.chi2)
+    assert np.array_equal(np.isnan(chi2), np.isnan(osol.chi2))
+    assert np.allclose(chi2[both], osol.chi2[both], rtol=1e-4)
+    assert abs(sol.b0 - osol.b0) <= B0_RTOL * abs(osol.b0)
+    gsol = oracle_solution_from_gpu(sol, ob, W, H)
+    pts = [(x, y) for x in (0, W // 2, W - 1) for y in (0, H // 2, H - 1)]
+    ke = kernel_rel_err(gsol, osol, pts)
+    assert ke <= KERNEL_RTOL, ke
+    assert sol.r_bad == O.r_bad(osol)
+    return ke, coeff_rel_err(sol.coeff[:osol.a.size], osol.a.ravel())
+
+
+def test_solve_small_field_with_extractor(dev):
+    f = synth.small_gaussian_field(1)
+    b, c, ob, oc = specs((0.7, 1.5, 3.0), (4, 2, 2), 10, 0, badmask=synth.BADMASK)
+    t = upload(f, dev, pad=3)
+    sol = P.psfm_solve_kernel(t["sci"], t["ref"], t["var_sci"], t["var_ref"], t["mask_sci"],
+                              t["mask_ref"], b, c)
+    ocand, med = O.extract_candidates(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref,
+                                      f.mask_sci, ob, oc)
+    assert np.float32(sol.median) == med
+    osol = O.solve_kernel(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, ob, oc,
+                          ocand)
+    _check_solution(sol, osol, ob, 512, 512)
+
+
+@pytest.mark.parametrize("mode", ["separate", "joint"])
+def test_solve_spatial_order_2_with_rejection(dev, mode):
+    """Spatially varying PSF, S = 2; a cosmic ray planted in the science image makes the
+    rejection loop remove and replace a stamp."""
+    f = synth.small_gaussian_field(9, size=384, n_stars=260, fwhm_ref=3.5, fwhm_sci=5.0)
+    sci = f.sci.copy()
+    b, c, ob, oc = specs((0.8, 1.6, 3.0), (4, 2, 2), 8, 2, badmask=synth.BADMASK, grid_nx=5,
+                         grid_ny=4, norm_mode=P.NORM_JOINT if mode == "joint" else P.NORM_SEPARATE)
+    ocand, _ = O.extract_candidates(f.ref, sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, ob, oc)
+    hit = next(r for r in range(ocand.shape[0]) if ocand[r, 1, 0] >= 0)
+    x, y = ocand[hit, 0]
+    sci[y + 2, x - 1] += 5000.0
+    f.sci = sci
+    t = upload(f, dev)
+    sol = P.psfm_solve_kernel(t["sci"], t["ref"], t["var_sci"], t["var_ref"], t["mask_sci"],
+                              t["mask_ref"], b, c)
+    osol = O.solve_kernel(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, ob, oc)
+    assert osol.status[hit, 0] == O.STATUS_REJECTED
+    _check_solution(sol, osol, ob, 384, 384)
+
+
+def test_caller_stamps(dev):
+    f = synth.small_gaussian_field(2, size=256, n_stars=80)
+    b, c, ob, oc = specs((0.7, 1.5, 3.0), (2, 2, 2), 7, 1, badmask=synth.BADMASK)
+    ocand, _ = O.extract_candidates(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci,
+                                    ob, O.Config(grid_nx=4, grid_ny=4, badmask=synth.BADMASK))
+    stamps = [tuple(xy) for xy in ocand[:, 0] if xy[0] >= 0]
+    t = upload(f, dev)
+    sol = P.psfm_solve_kernel(t["sci"], t["ref"], t["var_sci"], t["var_ref"], t["mask_sci"],
+                              t["mask_ref"], b, c, stamps=stamps)
+    cand = np.array([[s] for s in stamps], np.int32)
+    osol = O.solve_kernel(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, ob, oc, cand)
+    _check_solution(sol, osol, ob, 256, 256)
+
+
+def test_subtract_end_to_end_small(dev):
+    f = synth.small_gaussian_field(1)
+    b, c, ob, oc = specs((0.7, 1.5, 3.0), (4, 2, 2), 10, 0, badmask=synth.BADMASK)
+    t = upload(f, dev)
+    D, V, M, cov, sol = P.psfm_subtract(t["sci"], t["ref"], t["var_sci"], t["var_ref"],
+                                        t["mask_sci"], t["mask_ref"], b, c)
+    osol = O.solve_kernel(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, ob, oc)
+    _check_solution(sol, osol, ob, 512, 512)
+    oD, oV, oM, oP = O.subtract(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, osol,
+                                oc)
+    sig = np.sqrt(oV)
+    assert float((np.abs(host(D) - oD) / sig).max()) <= IMG_TOL_SIGMA
+    assert float((np.abs(host(V) - oV) / oV).max()) <= VAR_RTOL
+    assert np.array_equal(host(M), oM)
+    assert float(np.abs(cov.cpu().numpy() - oP).max()) <= 1e-6
+
+
+def test_too_few_stamps_and_bad_arguments(dev):
+    f = synth.small_gaussian_field(3, size=128, n_stars=2)
+    b, c, ob, oc = specs((1.0,), (2,), 5, 0, badmask=synth.BADMASK)
+    t = upload(f, dev)
+    with pytest.raises(P.PsfmError) as e:
+        P.psfm_solve_kernel(t["sci"], t["ref"], t["var_sci"], t["var_ref"], t["mask_sci"],
+                            t["mask_ref"], b, c)
+    assert e.value.code == 2
+    with pytest.raises(P.PsfmError) as e:
+        P.psfm_solve_kernel(t["sci"], t["ref"], t["var_sci"], t["var_ref"], t["mask_sci"],
+                            t["mask_ref"], b, c, stamps=[(500, 5), (6, 6), (7, 7)])
+    assert e.value.code == 1
+    # fully masked image: no background pixels
+    f.mask_ref[:] = synth.MASK_BAD
+    t = upload(f, dev)
+    with pytest.raises(P.PsfmError) as e:
+        P.psfm_solve_kernel(t["sci"], t["ref"], t["var_sci"], t["var_ref"], t["mask_sci"],
+                            t["mask_ref"], b, c)
+    assert e.value.code == 2
+    # the library still works after the errors
+    f2 = synth.small_gaussian_field(1)
+    b2, c2, ob2, oc2 = specs((0.7, 1.5, 3.0), (4, 2, 2), 10, 0, badmask=synth.BADMASK)
+    t2 = upload(f2, dev)
+    sol = P.psfm_solve_kernel(t2["sci"], t2["ref"], t2["var_sci"], t2["var_ref"], t2["mask_sci"],
+                              t2["mask_ref"], b2, c2)
+    assert sol.n_used >= 3
+
+
+def test_nonfinite_unmasked_pixel(dev):
+    f = synth.small_gaussian_field(1)
+    b, c, ob, oc = specs((0.7, 1.5, 3.0), (4, 2, 2), 10, 0, badmask=synth.BADMASK)
+    f.sci[100, 100] = np.nan
+    f.mask_sci[100, 100] = 0
+    f.mask_ref[100, 100] = 0
+    t = upload(f, dev)
+    with pytest.raises(P.PsfmError) as e:
+        P.psfm_solve_kernel(t["sci"], t["ref"], t["var_sci"], t["var_ref"], t["mask_sci"],
+                            t["mask_ref"], b, c)
+    assert e.value.code == 4
