@@ -91,9 +91,12 @@ typedef struct {
 #define PSFM_NORM_SEPARATE 0 /* b0, d0 first, unweighted footprint sums (Sec. 3.2) */
 #define PSFM_NORM_JOINT 1    /* b0, d0 in the weighted fit with the kernel terms */
 
-#define PSFM_PREC_FP32 0     /* stamp Gram on CUDA cores, FP32 products, FP64 chunk sums */
-#define PSFM_PREC_TF32 1     /* stamp Gram on tensor cores (reserved) */
-#define PSFM_PREC_BF16X3 2   /* stamp Gram on tensor cores, 3xBF16 split (reserved) */
+/* Arithmetic of the stamp design blocks and their Gram matrices (the normal equations are
+ * always assembled and solved in FP64; the image, variance and mask passes are FP32). */
+#define PSFM_PREC_FP64 0     /* design and Gram in FP64: matches the FP64 definition */
+#define PSFM_PREC_FP32 1     /* FP32 design and products, FP64 sums over 32-pixel chunks */
+#define PSFM_PREC_TF32 2     /* reserved: Gram on tensor cores in TF32 */
+#define PSFM_PREC_BF16X3 3   /* reserved: Gram on tensor cores, 3 x BF16 split products */
 
 /* Options; psfm_config_default() fills the defaults noted in brackets. */
 typedef struct {
@@ -108,7 +111,7 @@ typedef struct {
   int32_t var_tile;         /* constant-kernel patch for variance, 8..256 [64] (Sec. 4.4) */
   int32_t cov_grid;         /* n x n kernels averaged for the pseudo-matrix, 1..8 [5] (Sec. 4.4) */
   int32_t norm_mode;        /* PSFM_NORM_* [SEPARATE] */
-  int32_t precision;        /* PSFM_PREC_* [FP32] */
+  int32_t precision;        /* PSFM_PREC_* [FP64] */
   uint16_t badmask;         /* input mask bits that mark a pixel unusable [0x00FF] */
   uint16_t conv_bad;        /* CONV.BAD output bit [1 << 14] */
   uint16_t conv_poor;       /* CONV.POOR output bit [1 << 15] */

@@ -279,7 +279,7 @@ void psfm_config_default(psfm_config* c) {
   c->var_tile = 64;
   c->cov_grid = 5;
   c->norm_mode = PSFM_NORM_SEPARATE;
-  c->precision = PSFM_PREC_FP32;
+  c->precision = PSFM_PREC_FP64;
   c->badmask = 0x00FF;
   c->conv_bad = (uint16_t)(1u << 14);
   c->conv_poor = (uint16_t)(1u << 15);

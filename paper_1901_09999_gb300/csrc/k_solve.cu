@@ -49,39 +49,48 @@ struct StampParams {
   const uint16_t* m2;
   uint16_t badmask;
   int s, sw, P, foot, max_cand, Nc;
-  const float* f1d;  // [NH][wpad]
+  const float* f1d;     // [NH][wpad]
+  const double* f1d64;  // [NH][w]
   const double* psi;
   const double* sk;
   const int32_t* cand;
   const int32_t* ptr;
   int32_t* have;
-  float* C;
+  void* C;  // [nreg][Nb][P] of T (float or double, by precision mode)
   double* G;
   double* footsum;
   DevState* st;
 };
 
-// grid (nreg, ng): basis-convolved footprint of one Gaussian's terms.
+template <typename T>
+__device__ __forceinline__ T tap(const StampParams& P, int plane, int t) {
+  if (sizeof(T) == 8) return (T)P.f1d64[plane * P.b.w + t];
+  return (T)P.f1d[plane * P.b.wpad + t];
+}
+
+// grid (nreg, ng): basis-convolved footprint of one Gaussian's terms, in T arithmetic.
+template <typename T>
 __global__ void __launch_bounds__(256) k_stamp_design(StampParams P) {
-  extern __shared__ float sh[];
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  T* sh = reinterpret_cast<T*>(sh_raw);
   const int r = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
   if (P.st->error || P.st->done) return;
   int cx, cy;
   if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return;
   if (P.have[r] == P.ptr[r]) return;
   const int h = P.b.h, W = P.b.w, foot = P.foot, sw = P.sw;
-  float* F = sh;                  // foot x foot
-  float* Hp = F + foot * foot;    // foot x sw
+  T* F = sh;                  // foot x foot
+  T* Hp = F + foot * foot;    // foot x sw
   const int x0 = cx - P.s - h, y0 = cy - P.s - h;
   double f1 = 0.0, f2 = 0.0, nf = 0.0;
   for (int i = tid; i < foot * foot; i += 256) {
     const int rr = i / foot, cc = i - rr * foot;
     const int gx = x0 + cc, gy = y0 + rr;
-    float v = 0.f;
+    T v = 0;
     if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
       const int64_t o = (int64_t)gy * P.g.pitch + gx;
       const uint16_t a = P.m1[o] & P.badmask, b = P.m2[o] & P.badmask;
-      if (!a) v = P.i1[o];
+      if (!a) v = (T)P.i1[o];
       if (g == 0 && !a && !b) {
         f1 += v;
         f2 += P.i2[o];
@@ -119,24 +128,22 @@ __global__ void __launch_bounds__(256) k_stamp_design(StampParams P) {
   __syncthreads();
   const int dg = P.b.deg[g], pb = P.b.plane_base[g];
   for (int p = 0; p <= dg; ++p) {
-    const float* fp = P.f1d + (pb + p) * P.b.wpad;
     for (int i = tid; i < foot * sw; i += 256) {
       const int rr = i / sw, px = i - rr * sw;
-      const float* src = F + rr * foot + px + 2 * h;
-      float a = 0.f;
-      for (int t = 0; t < W; ++t) a = fmaf(fp[t], src[-t], a);
+      const T* src = F + rr * foot + px + 2 * h;
+      T a = 0;
+      for (int t = 0; t < W; ++t) a = fma(tap<T>(P, pb + p, t), src[-t], a);
       Hp[i] = a;
     }
     __syncthreads();
     const int kgp = P.b.kbase[g] + p * (dg + 1) - (p * (p - 1)) / 2;
     for (int q = 0; q <= dg - p; ++q) {
-      const float* fq = P.f1d + (pb + q) * P.b.wpad;
-      float* out = P.C + ((int64_t)r * P.b.Nb + kgp + q) * P.P;
+      T* out = reinterpret_cast<T*>(P.C) + ((int64_t)r * P.b.Nb + kgp + q) * P.P;
       for (int i = tid; i < P.P; i += 256) {
         const int py = i / sw, px = i - py * sw;
-        const float* src = Hp + (py + 2 * h) * sw + px;
-        float a = 0.f;
-        for (int t = 0; t < W; ++t) a = fmaf(fq[t], src[-t * sw], a);
+        const T* src = Hp + (py + 2 * h) * sw + px;
+        T a = 0;
+        for (int t = 0; t < W; ++t) a = fma(tap<T>(P, pb + q, t), src[-t * sw], a);
         out[i] = a;
       }
     }
@@ -144,7 +151,9 @@ __global__ void __launch_bounds__(256) k_stamp_design(StampParams P) {
   }
 }
 
-// grid (nreg): weighted Gram of the augmented design block of one stamp.
+// grid (nreg): weighted Gram of the augmented design block of one stamp; products in T,
+// sums over 32-pixel chunks in T, chunk sums accumulated in FP64.
+template <typename T>
 __global__ void __launch_bounds__(256) k_stamp_gram(StampParams P) {
   extern __shared__ double shd[];
   const int r = blockIdx.x, tid = threadIdx.x;
@@ -154,16 +163,16 @@ __global__ void __launch_bounds__(256) k_stamp_gram(StampParams P) {
   if (P.have[r] == P.ptr[r]) return;
   const int Nc = P.Nc, Nb = P.b.Nb;
   const int nblk = (Nc + 3) / 4, npair = nblk * (nblk + 1) / 2;
-  double* acc = shd;                                           // [npair][16]
-  float* A = reinterpret_cast<float*>(acc + (size_t)npair * 16);  // [nblk*4][32]
-  float* wgt = A + nblk * 4 * 32;                              // [32]
+  double* acc = shd;                                        // [npair][16]
+  T* A = reinterpret_cast<T*>(acc + (size_t)npair * 16);    // [nblk*4][32]
+  T* wgt = A + nblk * 4 * 32;                               // [32]
   for (int i = tid; i < npair * 16; i += 256) acc[i] = 0.0;
-  const float* Cr = P.C + (int64_t)r * Nb * P.P;
+  const T* Cr = reinterpret_cast<const T*>(P.C) + (int64_t)r * Nb * P.P;
   for (int base = 0; base < P.P; base += 32) {
     __syncthreads();
     for (int i = tid; i < nblk * 4 * 32; i += 256) {
       const int c = i >> 5, j = i & 31, pix = base + j;
-      float v = 0.f;
+      T v = 0;
       if (pix < P.P && c < Nc) {
         const int py = pix / P.sw, px = pix - py * P.sw;
         const int gx = cx - P.s + px, gy = cy - P.s + py;
@@ -173,16 +182,16 @@ __global__ void __launch_bounds__(256) k_stamp_gram(StampParams P) {
           v = Cr[(int64_t)c * P.P + pix];
         } else if (on) {
           const bool ok1 = !(P.m1[o] & P.badmask);
-          if (c == Nb) v = ok1 ? P.i1[o] : 0.f;
-          else if (c == Nb + 1) v = 1.f;
-          else v = P.i2[o];
+          if (c == Nb) v = ok1 ? (T)P.i1[o] : (T)0;
+          else if (c == Nb + 1) v = 1;
+          else v = (T)P.i2[o];
         }
       }
       A[i] = v;
     }
     if (tid < 32) {
       const int pix = base + tid;
-      float w = 0.f;
+      T w = 0;
       if (pix < P.P) {
         const int py = pix / P.sw, px = pix - py * P.sw;
         const int gx = cx - P.s + px, gy = cy - P.s + py;
@@ -191,7 +200,7 @@ __global__ void __launch_bounds__(256) k_stamp_gram(StampParams P) {
           if (!((P.m1[o] | P.m2[o]) & P.badmask)) {
             const float a = P.i1[o], b = P.i2[o], vv = P.v1[o] + P.v2[o];
             if (!isfinite(a) || !isfinite(b) || !isfinite(vv)) raise_error(P.st, PSFM_ERR_NONFINITE);
-            w = (float)(1.0 / ((double)P.v1[o] + (double)P.v2[o]));
+            w = (T)(1.0 / ((double)P.v1[o] + (double)P.v2[o]));
             if (!isfinite(w)) raise_error(P.st, PSFM_ERR_NONFINITE);
           }
         }
@@ -207,12 +216,12 @@ __global__ void __launch_bounds__(256) k_stamp_gram(StampParams P) {
         ++bi;
       }
       const int bj = bi + rem;
-      float s[16];
+      T s[16];
 #pragma unroll
-      for (int e = 0; e < 16; ++e) s[e] = 0.f;
+      for (int e = 0; e < 16; ++e) s[e] = 0;
       for (int j = 0; j < 32; ++j) {
-        const float w = wgt[j];
-        float a[4], b[4];
+        const T w = wgt[j];
+        T a[4], b[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           a[e] = A[(bi * 4 + e) * 32 + j];
@@ -221,7 +230,7 @@ __global__ void __launch_bounds__(256) k_stamp_gram(StampParams P) {
 #pragma unroll
         for (int e = 0; e < 4; ++e)
 #pragma unroll
-          for (int f = 0; f < 4; ++f) s[e * 4 + f] = fmaf(a[e], b[f], s[e * 4 + f]);
+          for (int f = 0; f < 4; ++f) s[e * 4 + f] = fma(a[e], b[f], s[e * 4 + f]);
       }
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[pr * 16 + e] += (double)s[e];
@@ -538,6 +547,7 @@ struct Chi2Params {
 };
 
 // grid (nreg): chi^2 of the active stamp with the current solution (FP64).
+template <typename T>
 __global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
   const StampParams& P = Q.sp;
   extern __shared__ double ak[];  // [Nb]: a_k(stamp) psi_k
@@ -566,7 +576,7 @@ __global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
   for (int k = tid; k < Nb; k += 256) ak[k] *= P.psi[k];
   __syncthreads();
   const double delta = s_delta, d0 = Q.dsol[1];
-  const float* Cr = P.C + (int64_t)r * Nb * P.P;
+  const T* Cr = reinterpret_cast<const T*>(P.C) + (int64_t)r * Nb * P.P;
   double q = 0.0, n = 0.0;
   for (int pix = tid; pix < P.P; pix += 256) {
     const int py = pix / P.sw, px = pix - py * P.sw;
@@ -679,7 +689,7 @@ void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b) {
   b.cand_chi2 = ws.take<double>((size_t)p.nreg * p.max_cand);
   b.ptr = ws.take<int32_t>(p.nreg);
   b.have = ws.take<int32_t>(p.nreg);
-  b.C = ws.take<float>((size_t)p.nreg * p.Nb * p.P);
+  b.C = ws.take<double>((size_t)p.nreg * p.Nb * p.P);
   b.G = ws.take<double>((size_t)p.nreg * p.Nc * p.Nc);
   b.foot = ws.take<double>((size_t)p.nreg * 4);
   b.chi2 = ws.take<double>(p.nreg);
@@ -721,6 +731,7 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   sp.max_cand = p.max_cand;
   sp.Nc = p.Nc;
   sp.f1d = t.f1d;
+  sp.f1d64 = t.f1d64;
   sp.psi = t.psi;
   sp.sk = t.sk;
   sp.cand = b.cand;
@@ -759,20 +770,25 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   cq.chi2 = b.chi2;
   cq.cand_chi2 = b.cand_chi2;
 
-  const size_t sm_design = sizeof(float) * ((size_t)p.foot * p.foot + (size_t)p.foot * p.sw);
+  const bool fp64 = p.cfg.precision == PSFM_PREC_FP64;
+  const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+  const size_t sm_design = esz * ((size_t)p.foot * p.foot + (size_t)p.foot * p.sw);
   const int nblk = (p.Nc + 3) / 4, npair = nblk * (nblk + 1) / 2;
-  const size_t sm_gram = sizeof(double) * npair * 16 + sizeof(float) * (nblk * 4 * 32 + 32);
+  const size_t sm_gram = sizeof(double) * npair * 16 + esz * (nblk * 4 * 32 + 32);
   if (sm_design > 200 * 1024 || sm_gram > 200 * 1024) return PSFM_ERR_UNSUPPORTED;
-  if (cudaFuncSetAttribute(k_stamp_design, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm_design) != cudaSuccess ||
-      cudaFuncSetAttribute(k_stamp_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sm_gram) != cudaSuccess)
+  auto design = fp64 ? k_stamp_design<double> : k_stamp_design<float>;
+  auto gram = fp64 ? k_stamp_gram<double> : k_stamp_gram<float>;
+  auto chi2 = fp64 ? k_chi2<double> : k_chi2<float>;
+  if (cudaFuncSetAttribute(design, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_design) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_gram) !=
+          cudaSuccess)
     return PSFM_ERR_CUDA;
   const int64_t nn = (int64_t)p.Nsys * p.Nsys;
   for (int it = 0; it < p.cfg.max_iter; ++it) {
     prof_begin("stamps", s);
-    k_stamp_design<<<dim3(p.nreg, p.ng), 256, sm_design, s>>>(sp);
-    k_stamp_gram<<<p.nreg, 256, sm_gram, s>>>(sp);
+    design<<<dim3(p.nreg, p.ng), 256, sm_design, s>>>(sp);
+    gram<<<p.nreg, 256, sm_gram, s>>>(sp);
     prof_end("stamps", s, 2);
     prof_begin("system", s);
     k_norm<<<1, 32, 0, s>>>(sy);
@@ -783,7 +799,7 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
                                       st);
     prof_end("cholesky", s, 1);
     prof_begin("chi2_reject", s);
-    k_chi2<<<p.nreg, 256, sizeof(double) * p.Nb, s>>>(cq);
+    chi2<<<p.nreg, 256, sizeof(double) * p.Nb, s>>>(cq);
     k_reject<<<1, 32, 0, s>>>(p.nreg, p.max_cand, p.cfg.max_iter, p.cfg.reject_nsigma, b.cand,
                               b.ptr, b.cand_stat, b.chi2, st);
     prof_end("chi2_reject", s, 2);

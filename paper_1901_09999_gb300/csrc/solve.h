@@ -20,7 +20,7 @@ struct SolveBuffers {
   int32_t* ptr;        // [nreg] rank of the active candidate
   int32_t* have;       // [nreg] rank whose design block is cached, -1 none
   // per-region stamp data
-  float* C;      // [nreg][Nb][P] basis-convolved masked reference at the stamp pixels
+  void* C;       // [nreg][Nb][P] basis-convolved masked reference at the stamp pixels (float or double)
   double* G;     // [nreg][Nc][Nc] weighted Gram of (basis columns, R, 1, I2)
   double* foot;  // [nreg][4] footprint sums F1, F2, n, unused
   double* chi2;  // [nreg] chi^2 of the active stamp

@@ -24,7 +24,7 @@ STATUS = {0: "OK", 1: "BAD_ARG", 2: "TOO_FEW_STAMPS", 3: "SINGULAR", 4: "NONFINI
           6: "TIMEOUT", 8: "WORKSPACE", 9: "UNSUPPORTED"}
 OP_SOLVE, OP_CONVOLVE, OP_SUBTRACT, OP_STACK = 1, 2, 3, 4
 NORM_SEPARATE, NORM_JOINT = 0, 1
-PREC_FP32, PREC_TF32, PREC_BF16X3 = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16X3 = 0, 1, 2, 3
 CAND_UNUSED, CAND_USED, CAND_REJECTED = 0, 1, 2
 MAX_GAUSS = 4
 
@@ -188,6 +188,16 @@ def _shape_of(*tensors) -> psfm_shape:
     return psfm_shape(W, H, pitch)
 
 
+def _like(t, dtype=None):
+    """Empty CUDA tensor with the shape and row pitch of ``t`` (the library writes rows at the
+    input pitch, so outputs must share it)."""
+    torch = _torch()
+    H, W = t.shape
+    pitch = t.stride(0)
+    base = torch.empty((H, pitch), dtype=dtype or t.dtype, device=t.device)
+    return base[:, :W]
+
+
 def _stream(stream):
     torch = _torch()
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -306,11 +316,12 @@ def psfm_convolve(ref, var_ref, mask_ref, basis, cfg, sol: Solution, img=None, v
     shape = _shape_of(ref, var_ref, mask_ref, img, var_img, mask_img)
     dev = ref.device
     if out is None:
-        out = torch.empty_like(ref)
+        out = _like(ref)
     if want_var and out_var is None:
-        out_var = torch.empty_like(ref)
+        out_var = _like(ref)
     if want_mask and out_mask is None:
-        out_mask = torch.empty_like(mask_ref)
+        out_mask = _like(mask_ref)
+    _shape_of(ref, out, out_var, out_mask)
     c_ref = 1 if cov_ref is None else cov_ref.shape[0]
     c_img = 0 if img is None else (1 if cov_img is None else cov_img.shape[0])
     cov = None
@@ -340,9 +351,10 @@ def psfm_subtract(img, ref, var_img, var_ref, mask_img, mask_ref, basis, cfg, st
     shape = _shape_of(img, ref, var_img, var_ref, mask_img, mask_ref)
     dev = img.device
     sp, ns, _keep = _stamps_arg(stamps)
-    out = torch.empty_like(img) if out is None else out
-    out_var = torch.empty_like(img) if out_var is None else out_var
-    out_mask = torch.empty_like(mask_img) if out_mask is None else out_mask
+    out = _like(img) if out is None else out
+    out_var = _like(img) if out_var is None else out_var
+    out_mask = _like(mask_img) if out_mask is None else out_mask
+    _shape_of(img, out, out_var, out_mask)
     c_ref = 1 if cov_ref is None else cov_ref.shape[0]
     c_img = 1 if cov_img is None else cov_img.shape[0]
     cov, ncov = None, 0
@@ -372,12 +384,10 @@ def psfm_stack(imgs, vars_, masks, sources, target_fwhm, bases, cfg, want_cov=Tr
     n = len(imgs)
     shape = _shape_of(*imgs, *vars_, *masks)
     dev = imgs[0].device
-    out = torch.empty_like(imgs[0])
-    out_var = torch.empty_like(imgs[0])
-    out_mask = torch.empty_like(masks[0])
-    out_count = torch.empty(imgs[0].shape, dtype=torch.int32, device=dev)
-    if out_count.stride(0) != shape.pitch:
-        raise ValueError("stack inputs must be contiguous")
+    out = _like(imgs[0])
+    out_var = _like(imgs[0])
+    out_mask = _like(masks[0])
+    out_count = _like(imgs[0], torch.int32)
     srcs = [np.ascontiguousarray(s, np.float64) for s in sources]
     nsrc = (C.c_int32 * n)(*[len(s) for s in srcs])
     sp = (C.POINTER(C.c_double) * n)(*[s.ctypes.data_as(C.POINTER(C.c_double)) for s in srcs])

@@ -12,6 +12,9 @@ IMG_TOL_SIGMA = 1e-3
 VAR_RTOL = 2e-5
 # Pseudo-matrix: FP64 on both sides.
 COV_ATOL = 1e-10
+# Pseudo-matrix of a difference: the combination weights are mean variances taken from the
+# FP32 variance maps (relative error ~1e-7).
+COV_DIFF_ATOL = 1e-6
 
 
 def device():
