@@ -242,6 +242,27 @@ psfm_status psfm_stack(int32_t n, const float* const* imgs, const float* const* 
                        double* cov_out, int32_t cov_out_w, psfm_solution* sols,
                        void* workspace, size_t ws_bytes, psfm_stream stream);
 
+/* psfm_convolve without a workspace (no counterpart in the paper: this is an integration
+ * aid).  For callers that cannot allocate device memory or hand over a workspace -- for
+ * example a plugin running inside another framework's CUDA graph capture, where allocation
+ * is forbidden, or a host whose device memory pool is owned by the application.  Computes
+ * the convolved (or difference) image, variance and mask exactly as psfm_convolve does with
+ * cov_ref = cov_img = NULL and cov_out = NULL; it allocates nothing and calls no allocating
+ * routine.  Its scratch is a fixed 6.1 MiB device array inside the library, present on every
+ * GPU that loads the library until the process exits.
+ *   Limits: width and height at most 4096 (PSFM_ERR_WORKSPACE otherwise).
+ *   The first call on a device looks up the array's device address with that device
+ *   current; make that first call before any stream capture.
+ *   All calls share the array: calls that may overlap on the GPU (other streams, unordered
+ *   host threads) race and give undefined results.  Calls on one stream are ordered.
+ *   Asynchronous on `stream`; errors as for psfm_convolve. */
+psfm_status psfm_convolve_noalloc(const float* ref, const float* var_ref,
+                                  const uint16_t* mask_ref, const float* img,
+                                  const float* var_img, const uint16_t* mask_img,
+                                  psfm_shape shape, const psfm_basis_spec* basis,
+                                  const psfm_config* cfg, const psfm_solution* sol, float* out,
+                                  float* out_var, uint16_t* out_mask, psfm_stream stream);
+
 /* Instrumentation (no counterpart in the paper).  psfm_profile_enable(1) clears the stage
  * table and starts recording a CUDA event pair around every stage the library enqueues
  * (on the caller's stream); psfm_profile_enable(0) stops.  psfm_profile_entry(i, ...) reports

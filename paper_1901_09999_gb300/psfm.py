@@ -109,6 +109,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                C.c_double, P(psfm_basis_spec), P(psfm_config), vp, vp, vp, vp, vp,
                                i32, P(psfm_solution), vp, sz, vp]
     lib.psfm_stack.restype = i32
+    lib.psfm_convolve_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, psfm_shape, P(psfm_basis_spec),
+                                          P(psfm_config), P(psfm_solution), vp, vp, vp, vp]
+    lib.psfm_convolve_noalloc.restype = i32
     _lib = lib
     return lib
 
@@ -338,6 +341,28 @@ def psfm_convolve(ref, var_ref, mask_ref, basis, cfg, sol: Solution, img=None, v
     if st != PSFM_OK:
         raise PsfmError(st, "psfm_convolve")
     return out, out_var, out_mask, cov
+
+
+def psfm_convolve_noalloc(ref, var_ref, mask_ref, basis, cfg, sol: Solution, img=None,
+                          var_img=None, mask_img=None, out=None, out_var=None, out_mask=None,
+                          stream=None):
+    """psfm_convolve without a workspace, for callers that cannot allocate device memory
+    (C: psfm_convolve_noalloc; images up to 4096 x 4096, no pseudo-matrix).  Output tensors
+    may be passed in so that the call allocates nothing; the ones left as None are created
+    here for convenience.  Returns (out, out_var, out_mask)."""
+    lib = load()
+    shape = _shape_of(ref, var_ref, mask_ref, img, var_img, mask_img)
+    out = _like(ref) if out is None else out
+    out_var = _like(ref) if out_var is None else out_var
+    out_mask = _like(mask_ref) if out_mask is None else out_mask
+    _shape_of(ref, out, out_var, out_mask)
+    st = lib.psfm_convolve_noalloc(_ptr(ref), _ptr(var_ref), _ptr(mask_ref), _ptr(img),
+                                   _ptr(var_img), _ptr(mask_img), shape, C.byref(basis),
+                                   C.byref(cfg), C.byref(sol.c), _ptr(out), _ptr(out_var),
+                                   _ptr(out_mask), _stream(stream))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_convolve_noalloc")
+    return out, out_var, out_mask
 
 
 def psfm_subtract(img, ref, var_img, var_ref, mask_img, mask_ref, basis, cfg, stamps=None,
