@@ -45,18 +45,24 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="512x512 plain-method workload")
+    ap.add_argument("--precision", default="f32x2", choices=["fp64", "f32x2", "fp32"],
+                    help="arithmetic of the stamp design blocks and Gram matrices")
     return ap.parse_args()
 
 
-def workload_specs(small):
+PRECISION = {"fp64": 0, "fp32": 1, "f32x2": 4}
+
+
+def workload_specs(small, precision="f32x2"):
     from paper_1901_09999_gb300 import psfm as P
     from paper_1901_09999_gb300 import synth
+    prec = PRECISION[precision]
     if small:
         b = P.basis_spec((0.7, 1.5, 3.0), (4, 2, 2), 10, 0)
-        c = P.config(badmask=synth.BADMASK)
+        c = P.config(badmask=synth.BADMASK, precision=prec)
     else:
         b = P.basis_spec(WORKLOAD["basis_sigma"], WORKLOAD["degrees"], 15, 2)
-        c = P.config(badmask=synth.BADMASK, grid_nx=15, grid_ny=20)
+        c = P.config(badmask=synth.BADMASK, grid_nx=15, grid_ny=20, precision=prec)
     return b, c
 
 
@@ -227,7 +233,7 @@ def main():
     build.build()
     from paper_1901_09999_gb300 import psfm as P
 
-    b, c = workload_specs(args.small)
+    b, c = workload_specs(args.small, args.precision)
     field = make_field(args.small, WORKLOAD["seed"] + rank)
     H, W = field.shape
 
@@ -338,7 +344,8 @@ def main():
         "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(WORKLOAD if not args.small else {"workload": "small_512x512_gaussian_S0_27terms"},
-                       l2="inputs (472 MB) larger than L2, no flush", precision="fp32 gram + fp64 solve",
+                       l2="inputs (472 MB) larger than L2, no flush",
+                       precision=f"stamp design+Gram {args.precision}, FP64 normal equations, FP32 image/variance passes",
                        parallelism=f"replicas x{world}"),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(), "stages_ms": {k: v[0] / args.steps for k, v in stages.items()},

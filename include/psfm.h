@@ -93,10 +93,11 @@ typedef struct {
 
 /* Arithmetic of the stamp design blocks and their Gram matrices (the normal equations are
  * always assembled and solved in FP64; the image, variance and mask passes are FP32). */
-#define PSFM_PREC_FP64 0     /* design and Gram in FP64: matches the FP64 definition */
+#define PSFM_PREC_FP64 0     /* design and Gram in FP64 (slow on this GPU's FP64 pipes) */
 #define PSFM_PREC_FP32 1     /* FP32 design and products, FP64 sums over 32-pixel chunks */
 #define PSFM_PREC_TF32 2     /* reserved: Gram on tensor cores in TF32 */
 #define PSFM_PREC_BF16X3 3   /* reserved: Gram on tensor cores, 3 x BF16 split products */
+#define PSFM_PREC_F32X2 4    /* design and Gram in double-float (FP32 pairs, ~48 bits) */
 
 /* Options; psfm_config_default() fills the defaults noted in brackets. */
 typedef struct {

@@ -63,30 +63,37 @@ __global__ void k_mask_hdilate(const uint32_t* bits, int W, int H, int nwords, i
   hb_poor[(int64_t)y * nwords + wx] = hdilate(p, c, n, h);
 }
 
+// One warp per (row, 32-pixel word): lanes load the rows within h above and below, the warp
+// ORs them (vertical dilation), then each lane writes one output pixel.
 __global__ void k_mask_out(const uint32_t* hb_bad, const uint32_t* hb_poor, const uint16_t* m1,
                            const uint16_t* m2, int W, int H, int64_t pitch, int nwords,
                            int r_fixed, const DevState* st, int h, uint16_t conv_bad,
                            uint16_t conv_poor, uint16_t* out) {
-  const int y = blockIdx.y;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= W) return;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= (int64_t)H * nwords) return;  // uniform per warp
+  const int y = (int)(gw / nwords), wx = (int)(gw - (int64_t)y * nwords);
   const int rb = r_fixed >= 0 ? r_fixed : st->r_bad;
-  const int wx = x >> 5;
-  const uint32_t bit = 1u << (x & 31);
-  bool bad = false, poor = false;
-  for (int dy = -h; dy <= h; ++dy) {
-    const int yy = y + dy;
+  uint32_t vb = 0, vp = 0;
+  for (int d = lane - h; d <= h; d += 32) {
+    const int yy = y + d;
     const bool off = yy < 0 || yy >= H;
-    const int ady = dy < 0 ? -dy : dy;
-    if (ady <= rb) bad |= off || (hb_bad[(int64_t)yy * nwords + wx] & bit);
-    poor |= off || (hb_poor[(int64_t)yy * nwords + wx] & bit);
+    const uint32_t wb = off ? 0xffffffffu : hb_bad[(int64_t)yy * nwords + wx];
+    const uint32_t wp = off ? 0xffffffffu : hb_poor[(int64_t)yy * nwords + wx];
+    if ((d < 0 ? -d : d) <= rb) vb |= wb;
+    vp |= wp;
   }
+  vb = __reduce_or_sync(0xffffffffu, vb);
+  vp = __reduce_or_sync(0xffffffffu, vp);
+  const int x = wx * 32 + lane;
+  if (x >= W) return;
+  const uint32_t bit = 1u << lane;
   const int64_t o = (int64_t)y * pitch + x;
   uint16_t m = m1[o];
   if (m2) m |= m2[o];
-  if (bad)
+  if (vb & bit)
     m |= conv_bad;
-  else if (poor)
+  else if (vp & bit)
     m |= conv_poor;
   out[o] = m;
 }
@@ -163,7 +170,8 @@ cudaError_t launch_mask(const Plan& p, const ApplyBuffers& b, const uint16_t* mr
                                                             nwords, p.cfg.badmask, b.bits);
   k_mask_hdilate<<<dim3((nwords + 127) / 128, p.H), 128, 0, st>>>(
       b.bits, p.W, p.H, nwords, -1, b.st, p.h, b.hb_bad, b.hb_poor);
-  k_mask_out<<<dim3((p.W + 255) / 256, p.H), blk, 0, st>>>(
+  const int64_t warps = (int64_t)p.H * nwords;
+  k_mask_out<<<(unsigned)((warps * 32 + 255) / 256), blk, 0, st>>>(
       b.hb_bad, b.hb_poor, mref, mimg, p.W, p.H, p.pitch, nwords, -1, b.st, p.h, p.cfg.conv_bad,
       p.cfg.conv_poor, out);
   return cudaGetLastError();

@@ -48,28 +48,40 @@ __global__ void k_median_hist(HistParams P) {
   __syncthreads();
   const uint32_t prefix = P.st->sel_prefix;
   const int64_t n = (int64_t)P.W * P.H;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int y = (int)(i / P.W), x = (int)(i - (int64_t)y * P.W);
-    const int64_t o = (int64_t)y * P.pitch + x;
-    if ((P.m1[o] | P.m2[o]) & P.badmask) continue;
-    const float s = P.i1[o] + P.i2[o];
-    if (!isfinite(s)) {
-      raise_error(P.st, PSFM_ERR_NONFINITE);
-      continue;
+  // warp-uniform trip count so that the warp-wide match below sees every lane
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    bool valid = false;
+    uint32_t bin = 0;
+    if (i < n) {
+      const int y = (int)(i / P.W), x = (int)(i - (int64_t)y * P.W);
+      const int64_t o = (int64_t)y * P.pitch + x;
+      if (!((P.m1[o] | P.m2[o]) & P.badmask)) {
+        const float s = P.i1[o] + P.i2[o];
+        if (!isfinite(s)) {
+          raise_error(P.st, PSFM_ERR_NONFINITE);
+        } else {
+          const uint32_t k = fkey(s);
+          if (P.pass == 0) {
+            bin = k >> 21;
+            valid = true;
+          } else if (P.pass == 1) {
+            bin = (k >> 10) & 2047u;
+            valid = (k >> 21) == prefix;
+          } else {
+            bin = k & 1023u;
+            valid = (k >> 10) == prefix;
+          }
+        }
+      }
     }
-    const uint32_t k = fkey(s);
-    uint32_t bin;
-    if (P.pass == 0) {
-      bin = k >> 21;
-    } else if (P.pass == 1) {
-      if ((k >> 21) != prefix) continue;
-      bin = (k >> 10) & 2047u;
-    } else {
-      if ((k >> 10) != prefix) continue;
-      bin = k & 1023u;
+    // sky pixels crowd into a few bins: one shared-memory atomic per distinct bin per warp
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    if (valid) {
+      const unsigned same = __match_any_sync(act, bin);
+      if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&h[bin], (uint32_t)__popc(same));
     }
-    atomicAdd(&h[bin], 1u);
   }
   __syncthreads();
   uint32_t* g = P.hist + P.pass * 2048;
@@ -77,38 +89,68 @@ __global__ void k_median_hist(HistParams P) {
     if (h[i]) atomicAdd(&g[i], h[i]);
 }
 
-// One thread: pick the bin holding the rank-th key and narrow the prefix.
-__global__ void k_median_select(const uint32_t* hist, int pass, DevState* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Pick the bin holding the rank-th key and narrow the prefix: a 1024-thread scan over the
+// histogram (two bins per thread).
+__global__ void __launch_bounds__(1024) k_median_select(const uint32_t* hist, int pass,
+                                                        DevState* st) {
+  __shared__ long long wsum[32];
+  __shared__ long long s_rank;
   const uint32_t* g = hist + pass * 2048;
   const int nb = pass == 2 ? 1024 : 2048;
-  int64_t rank;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int b0 = 2 * tid;
+  const long long c0 = b0 < nb ? g[b0] : 0, c1 = b0 + 1 < nb ? g[b0 + 1] : 0;
+  long long incl = c0 + c1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[w] = incl;
+  if (tid == 0) s_rank = pass == 0 ? -1 : st->sel_rank;
+  __syncthreads();
+  if (w == 0) {
+    long long v = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += t;
+    }
+    wsum[lane] = v;
+  }
+  __syncthreads();
+  if (w > 0) incl += wsum[w - 1];
+  const long long tot = wsum[31];
+  const long long excl = incl - (c0 + c1);
+  long long rank = s_rank;
   if (pass == 0) {
-    int64_t tot = 0;
-    for (int i = 0; i < nb; ++i) tot += g[i];
     if (tot == 0) {
-      raise_error(st, PSFM_ERR_TOO_FEW_STAMPS);
-      st->sel_prefix = 0;
+      if (tid == 0) {
+        raise_error(st, PSFM_ERR_TOO_FEW_STAMPS);
+        st->sel_prefix = 0;
+      }
       return;
     }
     rank = (tot - 1) / 2;  // lower median
-  } else {
-    rank = st->sel_rank;
   }
-  int64_t cum = 0;
-  int b = 0;
-  for (; b < nb; ++b) {
-    if (cum + g[b] > rank) break;
-    cum += g[b];
+  if (excl <= rank && rank < incl) {
+    int b;
+    long long rem;
+    if (rank < excl + c0) {
+      b = b0;
+      rem = rank - excl;
+    } else {
+      b = b0 + 1;
+      rem = rank - excl - c0;
+    }
+    st->sel_rank = (int32_t)rem;
+    if (pass == 0)
+      st->sel_prefix = (uint32_t)b;
+    else if (pass == 1)
+      st->sel_prefix = (st->sel_prefix << 11) | (uint32_t)b;
+    else
+      st->median_key = (st->sel_prefix << 10) | (uint32_t)b;
   }
-  if (b == nb) b = nb - 1;
-  st->sel_rank = (int32_t)(rank - cum);
-  if (pass == 0)
-    st->sel_prefix = (uint32_t)b;
-  else if (pass == 1)
-    st->sel_prefix = (st->sel_prefix << 11) | (uint32_t)b;
-  else
-    st->median_key = (st->sel_prefix << 10) | (uint32_t)b;
 }
 
 __device__ __forceinline__ bool row_clean(const uint32_t* row, int xa, int xb) {
@@ -147,8 +189,15 @@ __global__ void k_detect(DetectParams P) {
   if (x < P.R || x >= P.W - P.R || y < P.R || y >= P.H - P.R) return;
   const int64_t o = (int64_t)y * P.pitch + x;
   const float s = P.i1[o] + P.i2[o];
-  const double med = (double)fkey_inv(P.st->median_key);
-  const double thr = P.thresh * sqrt((double)P.v1[o] + (double)P.v2[o]);
+  const float medf = fkey_inv(P.st->median_key);
+  const float v1 = P.v1[o], v2 = P.v2[o];
+  // FP32 pre-test with a margin far above FP32 rounding: pixels well below the threshold
+  // skip the FP64 test (FP64 runs at 1/64 of the FP32 rate here); the decision itself is
+  // always the FP64 one
+  const float t32 = (float)P.thresh * sqrtf(v1 + v2);
+  if (isfinite(t32) && isfinite(s) && s - medf < 0.999f * t32) return;
+  const double med = (double)medf;
+  const double thr = P.thresh * sqrt((double)v1 + (double)v2);
   if (!((double)s - med > thr)) return;
   const int64_t idx = (int64_t)y * P.W + x;
   for (int dy = -1; dy <= 1; ++dy)
@@ -287,7 +336,7 @@ cudaError_t launch_extract(const Plan& p, DevState* st, const SolveBuffers& b, c
   for (int pass = 0; pass < 3; ++pass) {
     hp.pass = pass;
     k_median_hist<<<4 * 152, 512, 0, s>>>(hp);
-    k_median_select<<<1, 32, 0, s>>>(b.hist, pass, st);
+    k_median_select<<<1, 1024, 0, s>>>(b.hist, pass, st);
   }
   const int nwords = (p.W + 31) / 32;
   k_bad_bits2<<<dim3((p.W + 255) / 256, p.H), 256, 0, s>>>(mask_ref, mask_img, p.W, p.pitch,

@@ -114,7 +114,8 @@ psfm_status make_plan(Plan& p, psfm_shape shape, const psfm_basis_spec* b, const
   if (c->var_tile != kVarTile) return PSFM_ERR_UNSUPPORTED;
   if (c->norm_mode != PSFM_NORM_SEPARATE && c->norm_mode != PSFM_NORM_JOINT)
     return PSFM_ERR_BAD_ARG;
-  if (c->precision != PSFM_PREC_FP64 && c->precision != PSFM_PREC_FP32) {
+  if (c->precision != PSFM_PREC_FP64 && c->precision != PSFM_PREC_FP32 &&
+      c->precision != PSFM_PREC_F32X2) {
     if (c->precision == PSFM_PREC_TF32 || c->precision == PSFM_PREC_BF16X3)
       return PSFM_ERR_UNSUPPORTED;
     return PSFM_ERR_BAD_ARG;

@@ -34,7 +34,8 @@ struct DevState {
   int32_t n_active;     // stamps in the current solve
   int32_t r_bad;        // CONV.BAD radius
   int32_t n_cand_total; // detections seen
-  int32_t pad[2];
+  int32_t chol_fail;    // Cholesky met a non-positive pivot: LU fallback
+  int32_t pad1;
   double sum_var_conv;  // sum of V' over unmasked output pixels
   double sum_var_img;   // sum of V2 over unmasked output pixels
   double n_unmasked;    // count of unmasked output pixels

@@ -22,12 +22,14 @@ struct SolveBuffers {
   // per-region stamp data
   void* C;       // [nreg][Nb][P] basis-convolved masked reference at the stamp pixels (float or double)
   double* G;     // [nreg][Nc][Nc] weighted Gram of (basis columns, R, 1, I2)
+  double* Gt;    // [nreg][Nc][Nc] the same with basis columns psi_k C_k - s_k R
   double* foot;  // [nreg][4] footprint sums F1, F2, n, unused
   double* chi2;  // [nreg] chi^2 of the active stamp
   // normal equations
   double* M;  // [Nsys][Nsys]
   double* v;  // [Nsys]
   double* L;  // [Nsys][Nsys] factor
+  double* Linv;  // [Nsys/32][32][32] inverses of the diagonal blocks of L
   double* y;  // [Nsys]
   int32_t* piv;  // [Nsys] LU pivots
   double* gv;    // [nreg][Ns] spatial factors at the stamp centres, 0 when inactive

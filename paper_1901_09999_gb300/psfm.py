@@ -24,7 +24,7 @@ STATUS = {0: "OK", 1: "BAD_ARG", 2: "TOO_FEW_STAMPS", 3: "SINGULAR", 4: "NONFINI
           6: "TIMEOUT", 8: "WORKSPACE", 9: "UNSUPPORTED"}
 OP_SOLVE, OP_CONVOLVE, OP_SUBTRACT, OP_STACK = 1, 2, 3, 4
 NORM_SEPARATE, NORM_JOINT = 0, 1
-PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16X3 = 0, 1, 2, 3
+PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16X3, PREC_F32X2 = 0, 1, 2, 3, 4
 CAND_UNUSED, CAND_USED, CAND_REJECTED = 0, 1, 2
 MAX_GAUSS = 4
 
