@@ -136,23 +136,27 @@ __global__ void k_rbad(BasisDev b, const double* f1d64, const double* psi, const
     K2[i] = kv * kv;
   }
   __syncthreads();
-  // outside(r) = sum over max(|u|, |v|) > r, one thread per r
-  for (int r = tid; r <= h; r += blockDim.x) {
-    double o = 0.0;
-    for (int i = 0; i < W * W; ++i) {
-      const int v = i / W - h, u = i % W - h;
-      const int c = max(v < 0 ? -v : v, u < 0 ? -u : u);
-      if (c > r) o += K2[i];
-    }
-    part[r] = o;
+  // energy per Chebyshev ring, then outside(r) = sum of the rings beyond r
+  double* ring = part + h + 2;  // [h+1]
+  for (int r = tid; r <= h; r += blockDim.x) ring[r] = 0.0;
+  __syncthreads();
+  for (int i = tid; i < W * W; i += blockDim.x) {
+    const int v = i / W - h, u = i % W - h;
+    const int c = max(v < 0 ? -v : v, u < 0 ? -u : u);
+    atomicAdd(&ring[c], K2[i]);
   }
   __syncthreads();
   if (tid == 0) {
-    double tot = 0.0;
-    for (int i = 0; i < W * W; ++i) tot += K2[i];
+    // suffix sums from the outermost ring inwards: part[c] = sum_{c' >= c} ring[c']
+    double acc = 0.0;
+    for (int c = h; c >= 0; --c) {
+      acc += ring[c];
+      part[c] = acc;
+    }
+    const double tot = part[0];
     int rb = h;
-    for (int r = 0; r <= h; ++r)
-      if (part[r] <= bad_frac * tot) {
+    for (int r = 0; r < h; ++r)
+      if (part[r + 1] <= bad_frac * tot) {
         rb = r;
         break;
       }
@@ -179,7 +183,7 @@ cudaError_t launch_mask(const Plan& p, const ApplyBuffers& b, const uint16_t* mr
 
 cudaError_t launch_rbad(const Plan& p, const DevTables& t, const double* dsol, DevState* ds,
                         cudaStream_t st) {
-  const size_t smem = sizeof(double) * ((size_t)p.NH * p.w + (size_t)p.w * p.w + p.h + 2);
+  const size_t smem = sizeof(double) * ((size_t)p.NH * p.w + (size_t)p.w * p.w + 2 * p.h + 3);
   cudaError_t e = cudaFuncSetAttribute(k_rbad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

@@ -56,6 +56,7 @@ struct StampParams {
   const int32_t* cand;
   const int32_t* ptr;
   int32_t* have;
+  int32_t* fresh;  // [nreg] Gram recomputed in this iteration (added to M by k_system_delta)
   void* C;  // [nreg][Nb][P] of T (float or double, by precision mode)
   double* G;
   double* Gt;
@@ -298,23 +299,28 @@ __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
     for (int q = 0; q <= dg - p; ++q) {
       const float* qh = wh + q * W;
       const float* ql = wl + q * W;
-      double* out = reinterpret_cast<double*>(P.C) + ((int64_t)r * P.b.Nb + kgp + q) * P.P;
+      float2* out = reinterpret_cast<float2*>(P.C) + ((int64_t)r * P.b.Nb + kgp + q) * P.P;
       for (int i = tid; i < P.P; i += 256) {
         const int py = i / sw, px = i - py * sw;
         const int base = (py + 2 * h) * sw + px;
         df a = {0.f, 0.f};
         for (int t = 0; t < W; ++t)
           df_fma(a, df{Hh[base - t * sw], Hl[base - t * sw]}, df{qh[t], ql[t]});
-        out[i] = df_to_d(a);
+        a = df_norm(a);
+        out[i] = make_float2(a.hi, a.lo);
       }
     }
     __syncthreads();
   }
 }
 
-// grid (nreg): weighted Gram of the augmented block in double-float; chunk sums over 32
-// pixels are accumulated in FP64, then transformed as in k_stamp_gram.
-__global__ void __launch_bounds__(256) k_stamp_gram_df(StampParams P) {
+// grid (nreg), 512 threads: weighted Gram of the augmented block in double-float.  Each
+// thread owns a 4 x 4 block of the Gram and one of `nsl` interleaved pixel slices of every
+// 64-pixel chunk; the weighted columns w * A are formed once per chunk in shared memory.
+// Chunk partial sums go to per-slice FP64 accumulators, reduced in a fixed order at the end.
+constexpr int kGramChunk = 64;
+constexpr int kGramThreads = 512;
+__global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
   extern __shared__ double shd[];
   const int r = blockIdx.x, tid = threadIdx.x;
   if (P.st->error || P.st->done) return;
@@ -323,38 +329,22 @@ __global__ void __launch_bounds__(256) k_stamp_gram_df(StampParams P) {
   if (P.have[r] == P.ptr[r]) return;
   const int Nc = P.Nc, Nb = P.b.Nb;
   const int nblk = (Nc + 3) / 4, npair = nblk * (nblk + 1) / 2;
-  double* acc = shd;                                            // [npair][16]
-  float* Ah = reinterpret_cast<float*>(acc + (size_t)npair * 16);  // [nblk*4][32]
-  float* Al = Ah + nblk * 4 * 32;
-  float* wgh = Al + nblk * 4 * 32;                              // [32]
-  float* wgl = wgh + 32;
-  for (int i = tid; i < npair * 16; i += 256) acc[i] = 0.0;
-  const double* Cr = reinterpret_cast<const double*>(P.C) + (int64_t)r * Nb * P.P;
-  for (int base = 0; base < P.P; base += 32) {
+  const int nsl = max(1, kGramThreads / npair);
+  const int ncr = nblk * 4;                                        // padded column count
+  float2* acc = reinterpret_cast<float2*>(shd);                   // [nsl][npair][16] df
+  float* Ah = reinterpret_cast<float*>(acc + (size_t)nsl * npair * 16);  // [ncr][chunk]
+  float* Al = Ah + ncr * kGramChunk;
+  float* Bh = Al + ncr * kGramChunk;                               // w * A
+  float* Bl = Bh + ncr * kGramChunk;
+  float* wh = Bl + ncr * kGramChunk;                               // [chunk] weights
+  float* wl = wh + kGramChunk;
+  for (int i = tid; i < nsl * npair * 16; i += kGramThreads) acc[i] = make_float2(0.f, 0.f);
+  const float2* Cr = reinterpret_cast<const float2*>(P.C) + (int64_t)r * Nb * P.P;
+  for (int base = 0; base < P.P; base += kGramChunk) {
     __syncthreads();
-    for (int i = tid; i < nblk * 4 * 32; i += 256) {
-      const int c = i >> 5, j = i & 31, pix = base + j;
-      df v = {0.f, 0.f};
-      if (pix < P.P && c < Nc) {
-        const int py = pix / P.sw, px = pix - py * P.sw;
-        const int gx = cx - P.s + px, gy = cy - P.s + py;
-        const bool on = gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H;
-        const int64_t o = (int64_t)gy * P.g.pitch + gx;
-        if (c < Nb) {
-          v = df_split(Cr[(int64_t)c * P.P + pix]);
-        } else if (on) {
-          const bool ok1 = !(P.m1[o] & P.badmask);
-          if (c == Nb) v.hi = ok1 ? P.i1[o] : 0.f;
-          else if (c == Nb + 1) v.hi = 1.f;
-          else v.hi = P.i2[o];
-        }
-      }
-      Ah[i] = v.hi;
-      Al[i] = v.lo;
-    }
-    if (tid < 32) {
+    if (tid < kGramChunk) {
       const int pix = base + tid;
-      df w = {0.f, 0.f};
+      df wv = {0.f, 0.f};
       if (pix < P.P) {
         const int py = pix / P.sw, px = pix - py * P.sw;
         const int gx = cx - P.s + px, gy = cy - P.s + py;
@@ -362,18 +352,44 @@ __global__ void __launch_bounds__(256) k_stamp_gram_df(StampParams P) {
           const int64_t o = (int64_t)gy * P.g.pitch + gx;
           if (!((P.m1[o] | P.m2[o]) & P.badmask)) {
             const float a = P.i1[o], b = P.i2[o], vv = P.v1[o] + P.v2[o];
-            if (!isfinite(a) || !isfinite(b) || !isfinite(vv)) raise_error(P.st, PSFM_ERR_NONFINITE);
             const double wd = 1.0 / ((double)P.v1[o] + (double)P.v2[o]);
-            if (!isfinite(wd)) raise_error(P.st, PSFM_ERR_NONFINITE);
-            w = df_split(wd);
+            if (!isfinite(a) || !isfinite(b) || !isfinite(vv) || !isfinite(wd))
+              raise_error(P.st, PSFM_ERR_NONFINITE);
+            wv = df_split(wd);
           }
         }
       }
-      wgh[tid] = w.hi;
-      wgl[tid] = w.lo;
+      wh[tid] = wv.hi;
+      wl[tid] = wv.lo;
     }
     __syncthreads();
-    for (int pr = tid; pr < npair; pr += 256) {
+    for (int i = tid; i < ncr * kGramChunk; i += kGramThreads) {
+      const int c = i / kGramChunk, j = i - c * kGramChunk, pix = base + j;
+      df v = {0.f, 0.f};
+      if (pix < P.P) {
+        if (c < Nb) {
+          const float2 cv = Cr[(int64_t)c * P.P + pix];
+          v = df{cv.x, cv.y};
+        } else if (c < Nc) {
+          const int py = pix / P.sw, px = pix - py * P.sw;
+          const int gx = cx - P.s + px, gy = cy - P.s + py;
+          if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
+            const int64_t o = (int64_t)gy * P.g.pitch + gx;
+            if (c == Nb) v.hi = (P.m1[o] & P.badmask) ? 0.f : P.i1[o];
+            else if (c == Nb + 1) v.hi = 1.f;
+            else v.hi = P.i2[o];
+          }
+        }
+      }
+      const df b = df_mul(df{wh[j], wl[j]}, v);
+      Ah[i] = v.hi;
+      Al[i] = v.lo;
+      Bh[i] = b.hi;
+      Bl[i] = b.lo;
+    }
+    __syncthreads();
+    for (int pp = tid; pp < npair * nsl; pp += kGramThreads) {
+      const int pr = pp % npair, sl = pp / npair;
       int bi = 0, rem = pr;
       while (rem >= nblk - bi) {
         rem -= nblk - bi;
@@ -383,56 +399,67 @@ __global__ void __launch_bounds__(256) k_stamp_gram_df(StampParams P) {
       df s[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) s[e] = df{0.f, 0.f};
-      for (int j = 0; j < 32; ++j) {
-        const df w = {wgh[j], wgl[j]};
+      for (int j = sl; j < kGramChunk; j += nsl) {
         df a[4], b[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          a[e] = df{Ah[(bi * 4 + e) * 32 + j], Al[(bi * 4 + e) * 32 + j]};
-          b[e] = df_mul(w, df{Ah[(bj * 4 + e) * 32 + j], Al[(bj * 4 + e) * 32 + j]});
+          a[e] = df{Ah[(bi * 4 + e) * kGramChunk + j], Al[(bi * 4 + e) * kGramChunk + j]};
+          b[e] = df{Bh[(bj * 4 + e) * kGramChunk + j], Bl[(bj * 4 + e) * kGramChunk + j]};
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e)
 #pragma unroll
           for (int f = 0; f < 4; ++f) df_fma(s[e * 4 + f], a[e], b[f]);
       }
+      float2* ac = acc + ((size_t)sl * npair + pr) * 16;
 #pragma unroll
-      for (int e = 0; e < 16; ++e) acc[pr * 16 + e] += df_to_d(s[e]);
+      for (int e = 0; e < 16; ++e) {
+        df t = {ac[e].x, ac[e].y};
+        df_acc(t, s[e].hi, s[e].lo);
+        t = df_norm(t);
+        ac[e] = make_float2(t.hi, t.lo);
+      }
     }
   }
   __syncthreads();
   double* Gr = P.G + (int64_t)r * Nc * Nc;
-  for (int pr = tid; pr < npair; pr += 256) {
-    int bi = 0, rem = pr;
-    while (rem >= nblk - bi) {
-      rem -= nblk - bi;
-      ++bi;
+  for (int q = tid; q < npair * 16; q += kGramThreads) {
+    const int pq = q / 16, e = (q / 4) % 4, f = q % 4;
+    double v = 0.0;
+    for (int k = 0; k < nsl; ++k) {
+      const float2 a = acc[((size_t)k * npair + pq) * 16 + e * 4 + f];
+      v += (double)a.x + (double)a.y;
     }
-    const int bj = bi + rem;
-    for (int e = 0; e < 4; ++e)
-      for (int f = 0; f < 4; ++f) {
-        const int i = bi * 4 + e, j = bj * 4 + f;
-        if (i < Nc && j < Nc) {
-          Gr[i * Nc + j] = acc[pr * 16 + e * 4 + f];
-          Gr[j * Nc + i] = acc[pr * 16 + e * 4 + f];
-        }
-      }
+    int bi2 = 0, rem2 = pq;
+    while (rem2 >= nblk - bi2) {
+      rem2 -= nblk - bi2;
+      ++bi2;
+    }
+    const int bj2 = bi2 + rem2;
+    const int i = bi2 * 4 + e, j = bj2 * 4 + f;
+    if (i < Nc && j < Nc) {
+      Gr[i * Nc + j] = v;
+      Gr[j * Nc + i] = v;
+    }
   }
   __syncthreads();
   double* Gtr = P.Gt + (int64_t)r * Nc * Nc;
   const int cR = Nb;
-  for (int q = tid; q < Nc * Nc; q += 256) {
+  for (int q = tid; q < Nc * Nc; q += kGramThreads) {
     const int i = q / Nc, j = q - i * Nc;
-    const double ai = i < Nb ? P.psi[i] : 1.0, bi = i < Nb ? P.sk[i] : 0.0;
-    const double aj = j < Nb ? P.psi[j] : 1.0, bj = j < Nb ? P.sk[j] : 0.0;
+    const double ai = i < Nb ? P.psi[i] : 1.0, bi3 = i < Nb ? P.sk[i] : 0.0;
+    const double aj = j < Nb ? P.psi[j] : 1.0, bj3 = j < Nb ? P.sk[j] : 0.0;
     double e = ai * aj * Gr[i * Nc + j];
-    if (bj != 0.0) e -= ai * bj * Gr[i * Nc + cR];
-    if (bi != 0.0) e -= bi * aj * Gr[cR * Nc + j];
-    if (bi != 0.0 && bj != 0.0) e += bi * bj * Gr[cR * Nc + cR];
+    if (bj3 != 0.0) e -= ai * bj3 * Gr[i * Nc + cR];
+    if (bi3 != 0.0) e -= bi3 * aj * Gr[cR * Nc + j];
+    if (bi3 != 0.0 && bj3 != 0.0) e += bi3 * bj3 * Gr[cR * Nc + cR];
     Gtr[q] = e;
   }
   __syncthreads();
-  if (tid == 0) P.have[r] = P.ptr[r];
+  if (tid == 0) {
+    P.have[r] = P.ptr[r];
+    P.fresh[r] = 1;
+  }
 }
 
 // grid (nreg): weighted Gram of the augmented design block of one stamp; products in T,
@@ -554,7 +581,10 @@ __global__ void __launch_bounds__(256) k_stamp_gram(StampParams P) {
     Gtr[q] = e;
   }
   __syncthreads();
-  if (tid == 0) P.have[r] = P.ptr[r];
+  if (tid == 0) {
+    P.have[r] = P.ptr[r];
+    P.fresh[r] = 1;
+  }
 }
 
 struct SysParams {
@@ -566,39 +596,51 @@ struct SysParams {
   const double* Gt;
   const double* footsum;
   double* gv;      // [nreg][Ns] spatial factors at the stamp centre, 0 if inactive
+  double* gp;      // [nreg][(Ns+1)^2] products g_s g_s' (index Ns stands for 1), 0 if inactive
+  const int32_t* fresh;    // [nreg] stamps whose Gram joins M in this iteration
+  const int32_t* removed;  // [nreg] stamps rejected in this iteration (leave M)
   double* dsol;
   double* M;
-  double* L;
+  float* Lh;  // df working copy of M for the factorisation
+  float* Ll;
   double* v;
   DevState* st;
 };
 
-// Fixed-order block sum (deterministic for a given launch shape).
+// Fixed-order block sum (deterministic for a given launch shape): warp trees, then a tree
+// over the warp partials (FP64 chains are long on this GPU, so no sequential loop).
 __device__ double block_sum(double v, double* sh) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh[w] = v;
+  if (lane == 0) sh[w] = v;
   __syncthreads();
-  double t = 0.0;
-  for (int i = 0; i < nw; ++i) t += sh[i];
+  if (w == 0) {
+    double t = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[32] = t;
+  }
   __syncthreads();
-  return t;
+  return sh[32];
 }
 
 // Active count, spatial factors, and (SEPARATE) b0, d0 from the unweighted regression of
 // footprint sums (Sec. 3.2).  One CTA of 1024 threads.
 __global__ void __launch_bounds__(1024) k_norm(SysParams P) {
-  __shared__ double sh[32];
+  __shared__ double sh[33];
   if (P.st->error || P.st->done) return;
   double n = 0, s11 = 0, s12 = 0, s22 = 0, t1 = 0, t2 = 0;
   const double xs = P.g.W > 1 ? 2.0 / (P.g.W - 1) : 0.0, ys = P.g.H > 1 ? 2.0 / (P.g.H - 1) : 0.0;
   for (int r = threadIdx.x; r < P.nreg; r += blockDim.x) {
     int cx, cy;
     double* gr = P.gv + (int64_t)r * P.b.Ns;
+    const int N1 = P.b.Ns + 1;
+    double* gq = P.gp + (int64_t)r * N1 * N1;
     if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) {
       for (int s = 0; s < P.b.Ns; ++s) gr[s] = 0.0;
+      for (int s = 0; s < N1 * N1; ++s) gq[s] = 0.0;
       continue;
     }
     n += 1.0;
@@ -614,6 +656,9 @@ __global__ void __launch_bounds__(1024) k_norm(SysParams P) {
       }
       xp *= xt;
     }
+    for (int a = 0; a < N1; ++a)
+      for (int c = 0; c < N1; ++c)
+        gq[a * N1 + c] = (a < P.b.Ns ? gr[a] : 1.0) * (c < P.b.Ns ? gr[c] : 1.0);
     const double F1 = P.footsum[4 * r], F2 = P.footsum[4 * r + 1], nf = P.footsum[4 * r + 2];
     s11 += F1 * F1;
     s12 += F1 * nf;
@@ -678,143 +723,243 @@ __device__ __forceinline__ void unknown_col(const SysParams& P, int u, int* a, i
   *s = u - *a * P.b.Ns;
 }
 
-// M and v (Eq. 5-6 with g_i at the stamp centres): M_{(c,s),(c',s')} = sum_stamps g_s g_s'
-// Gt[c][c'] with the transformed stamp Grams.  One thread per (u, u') entry; the spatial
-// factors of a chunk of stamps are staged in shared memory.
-constexpr int kAsmChunk = 512;
-__global__ void __launch_bounds__(256) k_assemble(SysParams P) {
-  __shared__ double gsh[kAsmChunk * kMaxSpatial];
+// M (Eq. 5-6 with g_i at the stamp centres): M_{(c,s),(c',s')} = sum_stamps g_s g_s'
+// Gt[c][c'] with the transformed stamp Grams.  M is kept across the rejection iterations and
+// updated by the stamps that change (Sec. 3.5: per-stamp matrices need not be recalculated):
+// mode 0 adds the stamps whose Gram was computed in this iteration and refreshes the
+// double-float copy for the factorisation; mode 1 subtracts the stamps just rejected.  One
+// thread per entry of the upper triangle (mirrored); spatial products staged in shared memory.
+__global__ void __launch_bounds__(256) k_system_delta(SysParams P, int mode, int chunk) {
+  extern __shared__ double gsh[];  // [chunk][(Ns+1)^2]
   if (P.st->error || P.st->done) return;
-  const int Ns = P.b.Ns, Nc = P.Nc, N = P.Nsys;
+  const int Ns = P.b.Ns, N1 = Ns + 1, Nc = P.Nc, N = P.Nsys;
+  const int32_t* flag = mode == 0 ? P.fresh : P.removed;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const bool mine = t < (int64_t)N * N;
   int ui = 0, uj = 0, ai = 0, aj = 0, si = -1, sj = -1;
+  bool mine = t < (int64_t)N * N;
   if (mine) {
     ui = (int)(t / N);
     uj = (int)(t - (int64_t)ui * N);
+    mine = uj >= ui;
     unknown_col(P, ui, &ai, &si);
     unknown_col(P, uj, &aj, &sj);
   }
-  const bool rhs = t < N;
+  const int pidx = (si < 0 ? Ns : si) * N1 + (sj < 0 ? Ns : sj);
+  double acc = 0.0;
+  const int64_t gij = (int64_t)ai * Nc + aj;
+  for (int r0 = 0; r0 < P.nreg; r0 += chunk) {
+    const int nr = min(chunk, P.nreg - r0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < nr * N1 * N1; q += blockDim.x)
+      gsh[q] = flag[r0 + q / (N1 * N1)] ? P.gp[(int64_t)r0 * N1 * N1 + q] : 0.0;
+    __syncthreads();
+    if (mine) {
+      const double* Gr = P.Gt + (int64_t)r0 * Nc * Nc + gij;
+      for (int r = 0; r < nr; ++r) {
+        if (!flag[r0 + r]) continue;
+        acc = fma(gsh[r * N1 * N1 + pidx], Gr[(int64_t)r * Nc * Nc], acc);
+      }
+    }
+  }
+  if (!mine) return;
+  const int64_t a = (int64_t)ui * N + uj, b = (int64_t)uj * N + ui;
+  const double m = mode == 0 ? P.M[a] + acc : P.M[a] - acc;
+  P.M[a] = m;
+  P.M[b] = m;
+  if (mode == 0) {
+    const df d = df_split(m);
+    P.Lh[a] = d.hi;
+    P.Ll[a] = d.lo;
+    P.Lh[b] = d.hi;
+    P.Ll[b] = d.lo;
+  }
+}
+
+// Right-hand side v (Eq. 6): target I2 (JOINT) or I2 - b0 R - d0 (SEPARATE), all stamps.
+// One warp per unknown, lanes over the stamps, fixed-order warp reduction.
+__global__ void __launch_bounds__(256) k_rhs(SysParams P) {
+  if (P.st->error || P.st->done) return;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (t >= P.Nsys) return;
+  const int Ns = P.b.Ns, N1 = Ns + 1, Nc = P.Nc;
   int av = 0, sv = -1;
-  if (rhs) unknown_col(P, (int)t, &av, &sv);
+  unknown_col(P, t, &av, &sv);
   const int colR = P.b.Nb, col1 = P.b.Nb + 1, colI = P.b.Nb + 2;
   const double b0 = P.dsol[0], d0 = P.dsol[1];
-  double acc = 0.0, accv = 0.0;
-  for (int r0 = 0; r0 < P.nreg; r0 += kAsmChunk) {
-    const int nr = min(kAsmChunk, P.nreg - r0);
-    __syncthreads();
-    for (int q = threadIdx.x; q < nr * Ns; q += blockDim.x) gsh[q] = P.gv[(int64_t)r0 * Ns + q];
-    __syncthreads();
-    for (int r = 0; r < nr; ++r) {
-      const double* gr = gsh + r * Ns;
-      if (gr[0] == 0.0) continue;  // inactive (the constant spatial term is 1)
-      const double* Gr = P.Gt + (int64_t)(r0 + r) * Nc * Nc;
-      if (mine) {
-        const double gi = si < 0 ? 1.0 : gr[si], gj = sj < 0 ? 1.0 : gr[sj];
-        acc += gi * gj * Gr[ai * Nc + aj];
-      }
-      if (rhs) {
-        double e = Gr[av * Nc + colI];
-        if (!P.joint) e -= b0 * Gr[av * Nc + colR] + d0 * Gr[av * Nc + col1];
-        accv += (sv < 0 ? 1.0 : gr[sv]) * e;
-      }
-    }
+  double accv = 0.0;
+  for (int r = lane; r < P.nreg; r += 32) {
+    const double gg = P.gp[(int64_t)r * N1 * N1 + (sv < 0 ? Ns : sv) * N1 + Ns];
+    if (gg == 0.0) continue;
+    const double* Gr = P.Gt + (int64_t)r * Nc * Nc;
+    double e = Gr[av * Nc + colI];
+    if (!P.joint) e -= b0 * Gr[av * Nc + colR] + d0 * Gr[av * Nc + col1];
+    accv = fma(gg, e, accv);
   }
-  if (mine) {
-    P.M[t] = acc;
-    P.L[t] = acc;
-  }
-  if (rhs) P.v[t] = accv;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) accv += __shfl_xor_sync(0xffffffffu, accv, o);
+  if (lane == 0) P.v[t] = accv;
 }
 
-// ---- Cholesky of the N x N system in FP64, right-looking by 32-column panels, spread over
-// the GPU: the diagonal block is factored (and inverted) by one CTA, the panel below by
-// 4-row CTAs, the trailing lower triangle by 16 x 16 tiles.  L holds M on entry.
 constexpr int kNB = 32;
 
-// Diagonal block: one warp, lane i holding row i of the 32 x 32 block in registers (rows
-// beyond the matrix are padded with the identity), factored column by column with shuffles;
-// then lane c builds column c of the block's inverse by forward substitution.
-__global__ void __launch_bounds__(32) k_chol_diag(int n, int kb, double* L, double* Linv_all,
-                                                  DevState* st) {
+// ---- Cholesky of the N x N normal equations in double-float (FP32 pairs on the FP32 pipes;
+// FP64 chains on this GPU are slow), right-looking by 32-column panels spread over the GPU,
+// followed by iterative refinement with FP64 residuals of the exact FP64 matrix, which brings
+// the solution to FP64 accuracy (the factor only preconditions the correction).
+
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  df t = a;
+  df_acc(t, b.hi, b.lo);
+  return df_norm(t);
+}
+
+// 1 / sqrt(d): FP32 estimate refined by one Newton step in double-float.
+__device__ __forceinline__ df df_rsqrt(df d) {
+  const float r0 = rsqrtf(d.hi);
+  df t = df_mul(d, df{r0, 0.f});
+  t = df_mul(t, df{r0, 0.f});                    // d r0^2 ~ 1
+  const df e = df_add(df{1.f, 0.f}, df_neg(t));  // 1 - d r0^2
+  df corr = df_mul(e, df{0.5f * r0, 0.f});
+  return df_add(df{r0, 0.f}, corr);
+}
+
+__device__ __forceinline__ df df_shfl(df a, int src) {
+  return df{__shfl_sync(0xffffffffu, a.hi, src), __shfl_sync(0xffffffffu, a.lo, src)};
+}
+
+// Diagonal block, 128 threads with the block in shared memory: column-by-column Cholesky
+// (pivot, scale, rank-1 update of the trailing block, each phase across the CTA), then the
+// inverse of the block by the same column sweep.  The inverse turns the panel solve and the
+// triangular solves into dot products with no sequential chain.
+constexpr int kDiagThreads = 128;
+__global__ void __launch_bounds__(kDiagThreads) k_chol_diag(int n, int kb, float* Lh, float* Ll,
+                                                            float2* Linv_all, DevState* st) {
+  __shared__ float2 A[kNB][kNB + 1];
+  __shared__ float2 X[kNB][kNB + 1];
+  __shared__ float2 rp[kNB];
+  __shared__ int s_fail;
   if (st->error || st->done || st->chol_fail) return;
-  const int k0 = kb * kNB, m = min(kNB, n - k0), lane = threadIdx.x;
-  const unsigned full = 0xffffffffu;
-  double a[kNB];
-#pragma unroll
-  for (int c = 0; c < kNB; ++c)
-    a[c] = (lane < m && c <= lane) ? L[(int64_t)(k0 + lane) * n + k0 + c] : (lane == c ? 1.0 : 0.0);
-  bool fail = false;
-#pragma unroll
-  for (int j = 0; j < kNB; ++j) {
-    const double djj = __shfl_sync(full, a[j], j);
-    if (!(djj > 0.0) || !isfinite(djj)) fail = true;
-    const double ljj = sqrt(djj);
-    const double rinv = 1.0 / ljj;
-    if (lane == j)
-      a[j] = ljj;
-    else if (lane > j)
-      a[j] *= rinv;
-#pragma unroll
-    for (int c = j + 1; c < kNB; ++c) {
-      const double lcj = __shfl_sync(full, a[j], c);
-      if (lane >= c) a[c] = fma(-a[j], lcj, a[c]);
+  const int k0 = kb * kNB, m = min(kNB, n - k0), tid = threadIdx.x;
+  for (int q = tid; q < kNB * kNB; q += kDiagThreads) {
+    const int r = q / kNB, c = q % kNB;
+    float2 v = make_float2(r == c ? 1.f : 0.f, 0.f);
+    if (r < m && c < m && c <= r) {
+      const int64_t o = (int64_t)(k0 + r) * n + k0 + c;
+      v = make_float2(Lh[o], Ll[o]);
+    } else if (r < m && c < m) {
+      v = make_float2(0.f, 0.f);
     }
+    A[r][c] = v;
+    X[r][c] = make_float2(r == c ? 1.f : 0.f, 0.f);
   }
-  if (fail) {
-    if (lane == 0) st->chol_fail = 1;
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  for (int j = 0; j < kNB; ++j) {
+    // pivot and column scaling inside warp 0 (lane j computes the pivot, a shuffle spreads it)
+    if (tid < 32) {
+      df d = {A[j][j].x, A[j][j].y};
+      df r = {0.f, 0.f};
+      if (tid == j) {
+        if (!(d.hi > 0.f) || !isfinite(d.hi)) s_fail = 1;
+        r = df_rsqrt(d);
+        const df l = df_mul(d, r);
+        A[j][j] = make_float2(l.hi, l.lo);
+        rp[j] = make_float2(r.hi, r.lo);
+      }
+      r = df_shfl(r, j);
+      if (tid > j) {
+        const df a = df_mul(df{A[tid][j].x, A[tid][j].y}, r);
+        A[tid][j] = make_float2(a.hi, a.lo);
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    const int rem = kNB - j - 1;
+    for (int q = tid; q < rem * rem; q += kDiagThreads) {
+      const int i = j + 1 + q / rem, c = j + 1 + q % rem;
+      if (c <= i) {
+        df a = {A[i][c].x, A[i][c].y};
+        df_fma(a, df_neg(df{A[i][j].x, A[i][j].y}), df{A[c][j].x, A[c][j].y});
+        a = df_norm(a);
+        A[i][c] = make_float2(a.hi, a.lo);
+      }
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (tid == 0) st->chol_fail = 1;
     return;
   }
-  double x[kNB];  // x[i] = inv(L)[i][lane]
-#pragma unroll
-  for (int i = 0; i < kNB; ++i) {
-    double sacc = lane == i ? 1.0 : 0.0;
-#pragma unroll
-    for (int t = 0; t < i; ++t) sacc = fma(-__shfl_sync(full, a[t], i), x[t], sacc);
-    x[i] = sacc / __shfl_sync(full, a[i], i);
+  // inverse: for t = 0..: row t of X scaled by 1/L_tt, then X[i][:] -= L[i][t] X[t][:]
+  for (int t = 0; t < kNB; ++t) {
+    if (tid < kNB) {
+      // 1 / L_tt is the pivot's reciprocal square root kept from the factorisation
+      const df x = df_mul(df{X[t][tid].x, X[t][tid].y}, df{rp[t].x, rp[t].y});
+      X[t][tid] = make_float2(x.hi, x.lo);
+    }
+    __syncthreads();
+    const int rem = kNB - t - 1;
+    for (int q = tid; q < rem * kNB; q += kDiagThreads) {
+      const int i = t + 1 + q / kNB, c = q % kNB;
+      df x = {X[i][c].x, X[i][c].y};
+      df_fma(x, df_neg(df{A[i][t].x, A[i][t].y}), df{X[t][c].x, X[t][c].y});
+      x = df_norm(x);
+      X[i][c] = make_float2(x.hi, x.lo);
+    }
+    __syncthreads();
   }
-  double* Linv = Linv_all + (int64_t)kb * kNB * kNB;
-#pragma unroll
-  for (int i = 0; i < kNB; ++i) Linv[i * kNB + lane] = x[i];
-  if (lane < m) {
-#pragma unroll
-    for (int c = 0; c < kNB; ++c)
-      if (c <= lane) L[(int64_t)(k0 + lane) * n + k0 + c] = a[c];
+  float2* Linv = Linv_all + (int64_t)kb * kNB * kNB;
+  for (int q = tid; q < kNB * kNB; q += kDiagThreads) {
+    const int r = q / kNB, c = q % kNB;
+    Linv[q] = X[r][c];
+    if (r < m && c <= r) {
+      const int64_t o = (int64_t)(k0 + r) * n + k0 + c;
+      Lh[o] = A[r][c].x;
+      Ll[o] = A[r][c].y;
+    }
   }
 }
 
-// Rows below the diagonal block: L_ik = A_ik inv(L_kk)^T.  4 rows per CTA.
-__global__ void __launch_bounds__(128) k_chol_trsm(int n, int kb, double* L,
-                                                   const double* Linv_all, const DevState* st) {
-  __shared__ double Li[kNB][kNB + 1];
-  __shared__ double Ar[4][kNB];
+// Rows below the diagonal block: L_ik = A_ik inv(L_kk)^T, one output element per thread
+// (8 rows x 32 columns per CTA), no sequential chain.
+__global__ void __launch_bounds__(256) k_chol_trsm(int n, int kb, float* Lh, float* Ll,
+                                                   const float2* Linv_all, const DevState* st) {
+  __shared__ float2 Li[kNB][kNB + 1];
+  __shared__ float2 Ar[8][kNB + 1];
   if (st->error || st->done || st->chol_fail) return;
   const int k0 = kb * kNB, m = min(kNB, n - k0);
-  const int r0 = k0 + m + blockIdx.x * 4;
-  const double* Linv = Linv_all + (int64_t)kb * kNB * kNB;
-  for (int i = threadIdx.x; i < kNB * kNB; i += blockDim.x) Li[i / kNB][i % kNB] = Linv[i];
+  const float2* Linv = Linv_all + (int64_t)kb * kNB * kNB;
+  for (int q = threadIdx.x; q < kNB * kNB; q += blockDim.x) Li[q / kNB][q % kNB] = Linv[q];
   const int rr = threadIdx.x / kNB, c = threadIdx.x % kNB;
-  const int row = r0 + rr;
-  Ar[rr][c] = (row < n && c < m) ? L[(int64_t)row * n + k0 + c] : 0.0;
+  const int row = k0 + m + blockIdx.x * 8 + rr;
+  float2 a = make_float2(0.f, 0.f);
+  if (row < n && c < m) {
+    const int64_t o = (int64_t)row * n + k0 + c;
+    a = make_float2(Lh[o], Ll[o]);
+  }
+  Ar[rr][c] = a;
   __syncthreads();
   if (row < n && c < m) {
-    double sacc = 0.0;
-    for (int t2 = 0; t2 <= c; ++t2) sacc += Ar[rr][t2] * Li[c][t2];
-    L[(int64_t)row * n + k0 + c] = sacc;
+    df sacc = {0.f, 0.f};
+    for (int t = 0; t <= c; ++t) df_fma(sacc, df{Ar[rr][t].x, Ar[rr][t].y}, df{Li[c][t].x, Li[c][t].y});
+    sacc = df_norm(sacc);
+    const int64_t o = (int64_t)row * n + k0 + c;
+    Lh[o] = sacc.hi;
+    Ll[o] = sacc.lo;
   }
 }
 
 // Trailing update of the lower triangle: A_ij -= L_i,panel . L_j,panel, 16 x 16 tiles.
-__global__ void __launch_bounds__(256) k_chol_update(int n, int kb, double* L,
+__global__ void __launch_bounds__(256) k_chol_update(int n, int kb, float* Lh, float* Ll,
                                                      const DevState* st) {
-  __shared__ double Pi[16][kNB + 1];
-  __shared__ double Pj[16][kNB + 1];
+  __shared__ float2 Pi[16][kNB + 1];
+  __shared__ float2 Pj[16][kNB + 1];
   if (st->error || st->done || st->chol_fail) return;
   const int k0 = kb * kNB, m = min(kNB, n - k0);
   const int base = k0 + m;
   const int nt = (n - base + 15) / 16;
-  // tile index -> (ti, tj), tj <= ti
   int t = blockIdx.x, ti = 0;
   while (t >= ti + 1) {
     t -= ti + 1;
@@ -825,90 +970,145 @@ __global__ void __launch_bounds__(256) k_chol_update(int n, int kb, double* L,
   const int r0 = base + ti * 16, c0 = base + tj * 16;
   for (int i = threadIdx.x; i < 16 * kNB; i += blockDim.x) {
     const int r = i / kNB, c = i % kNB;
-    Pi[r][c] = (r0 + r < n && c < m) ? L[(int64_t)(r0 + r) * n + k0 + c] : 0.0;
-    Pj[r][c] = (c0 + r < n && c < m) ? L[(int64_t)(c0 + r) * n + k0 + c] : 0.0;
+    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+    if (r0 + r < n && c < m) {
+      const int64_t o = (int64_t)(r0 + r) * n + k0 + c;
+      a = make_float2(Lh[o], Ll[o]);
+    }
+    if (c0 + r < n && c < m) {
+      const int64_t o = (int64_t)(c0 + r) * n + k0 + c;
+      b = make_float2(Lh[o], Ll[o]);
+    }
+    Pi[r][c] = a;
+    Pj[r][c] = b;
   }
   __syncthreads();
   const int y = threadIdx.x / 16, x = threadIdx.x % 16;
   const int row = r0 + y, col = c0 + x;
   if (row < n && col < n && col <= row) {
-    double sacc = 0.0;
-    for (int c = 0; c < m; ++c) sacc += Pi[y][c] * Pj[x][c];
-    L[(int64_t)row * n + col] -= sacc;
+    df s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+    for (int c = 0; c < m; c += 2) {
+      df_fma(s0, df{Pi[y][c].x, Pi[y][c].y}, df{Pj[x][c].x, Pj[x][c].y});
+      if (c + 1 < m) df_fma(s1, df{Pi[y][c + 1].x, Pi[y][c + 1].y}, df{Pj[x][c + 1].x, Pj[x][c + 1].y});
+    }
+    const int64_t o = (int64_t)row * n + col;
+    df sum = df_add(df_norm(s0), df_norm(s1));
+    df a = df{Lh[o], Ll[o]};
+    a = df_add(a, df_neg(sum));
+    Lh[o] = a.hi;
+    Ll[o] = a.lo;
   }
 }
 
-// L z = v then L^T x = z with the factored blocks and their inverses; one CTA of 1024
-// threads, blocked by panels.  Writes the solution into the device solution vector.
-__global__ void __launch_bounds__(1024) k_chol_solve(int n, int joint, const double* L,
-                                                     const double* Linv_all, const double* v,
-                                                     double* dsol, DevState* st) {
-  extern __shared__ double ys[];  // [n] + [32][33]
-  double* part = ys + n;
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const df u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = df_add(v, u);
+  }
+  return v;
+}
+
+// L z = b then L^T y = z in double-float, with the block inverses: per panel a dot-product
+// phase (warp per row) and a 32 x 32 inverse application (warp per row); x_out = x_in + y.
+__global__ void __launch_bounds__(1024) k_chol_solve(int n, const float* Lh, const float* Ll,
+                                                     const float2* Linv_all, const double* b,
+                                                     const double* x_in, double* x_out,
+                                                     const DevState* st) {
+  extern __shared__ float2 ys[];  // [n] + [33][33] + [32]
+  float2* pw = ys + n;
+  float2* zb = pw + 33 * 33;
   if (st->error || st->done || st->chol_fail) return;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int i = tid; i < n; i += blockDim.x) ys[i] = v[i];
+  for (int i = tid; i < n; i += blockDim.x) {
+    const df d = df_split(b[i]);
+    ys[i] = make_float2(d.hi, d.lo);
+  }
   __syncthreads();
   const int nb = (n + kNB - 1) / kNB;
-  // forward: y_b = inv(L_bb) (v_b - L_b,<b y_<b)
-  for (int b = 0; b < nb; ++b) {
-    const int k0 = b * kNB, m = min(kNB, n - k0);
-    // warp w: row k0 + w, lanes over previous columns
-    double sacc = 0.0;
+  for (int bk = 0; bk < nb; ++bk) {
+    const int k0 = bk * kNB, m = min(kNB, n - k0);
+    df sacc = {0.f, 0.f};
     if (w < m)
-      for (int c = lane; c < k0; c += 32) sacc += L[(int64_t)(k0 + w) * n + c] * ys[c];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      for (int c = lane; c < k0; c += 32) {
+        const int64_t o = (int64_t)(k0 + w) * n + c;
+        df_fma(sacc, df{Lh[o], Ll[o]}, df{ys[c].x, ys[c].y});
+      }
+    sacc = warp_sum_df(df_norm(sacc));
+    if (w < m && lane == 0) {
+      const df y = df_add(df{ys[k0 + w].x, ys[k0 + w].y}, df_neg(sacc));
+      zb[w] = make_float2(y.hi, y.lo);
+    }
     __syncthreads();
-    if (w < m && lane == 0) part[w] = ys[k0 + w] - sacc;
-    __syncthreads();
-    const double* Li = Linv_all + (int64_t)b * kNB * kNB;
+    const float2* Li = Linv_all + (int64_t)bk * kNB * kNB;
     if (w < m) {
-      double t2 = 0.0;
-      if (lane <= w) t2 = Li[w * kNB + lane] * part[lane];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, o);
-      if (lane == 0) ys[k0 + w] = t2;
+      df t2 = {0.f, 0.f};
+      if (lane <= w && lane < m) df_fma(t2, df{Li[w * kNB + lane].x, Li[w * kNB + lane].y}, df{zb[lane].x, zb[lane].y});
+      t2 = warp_sum_df(df_norm(t2));
+      if (lane == 0) ys[k0 + w] = make_float2(t2.hi, t2.lo);
     }
     __syncthreads();
   }
-  // backward: x_b = inv(L_bb)^T (y_b - L_>b,b^T x_>b)
-  for (int b = nb - 1; b >= 0; --b) {
-    const int k0 = b * kNB, m = min(kNB, n - k0);
-    // part[w][lane]: warp w sums rows i = k0 + m + w, +32, ... for column lane
-    double sacc = 0.0;
+  for (int bk = nb - 1; bk >= 0; --bk) {
+    const int k0 = bk * kNB, m = min(kNB, n - k0);
+    df sacc = {0.f, 0.f};
     if (lane < m)
-      for (int i = k0 + m + w; i < n; i += 32) sacc += L[(int64_t)i * n + k0 + lane] * ys[i];
-    __syncthreads();
-    double* pw = ys + n;  // [33][33]: per-warp partial sums, then z in row 32
-    pw[w * 33 + lane] = sacc;
+      for (int i = k0 + m + w; i < n; i += 32) {
+        const int64_t o = (int64_t)i * n + k0 + lane;
+        df_fma(sacc, df{Lh[o], Ll[o]}, df{ys[i].x, ys[i].y});
+      }
+    sacc = df_norm(sacc);
+    pw[w * 33 + lane] = make_float2(sacc.hi, sacc.lo);
     __syncthreads();
     if (tid < m) {
-      double z = ys[k0 + tid];
-      for (int q = 0; q < 32; ++q) z -= pw[q * 33 + tid];
-      pw[32 * 33 + tid] = z;
+      df z = {ys[k0 + tid].x, ys[k0 + tid].y};
+      for (int q = 0; q < 32; ++q) z = df_add(z, df_neg(df{pw[q * 33 + tid].x, pw[q * 33 + tid].y}));
+      zb[tid] = make_float2(z.hi, z.lo);
     }
     __syncthreads();
-    const double* Li = Linv_all + (int64_t)b * kNB * kNB;
+    const float2* Li = Linv_all + (int64_t)bk * kNB * kNB;
     if (w < m) {
-      // x_w = sum_j inv(L)[j][w] z_j for j >= w
-      double t2 = 0.0;
-      if (lane >= w && lane < m) t2 = Li[lane * kNB + w] * pw[32 * 33 + lane];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, o);
-      if (lane == 0) ys[k0 + w] = t2;
+      // x_w = sum_j inv(L)[j][w] z_j, j >= w
+      df t2 = {0.f, 0.f};
+      if (lane >= w && lane < m) df_fma(t2, df{Li[lane * kNB + w].x, Li[lane * kNB + w].y}, df{zb[lane].x, zb[lane].y});
+      t2 = warp_sum_df(df_norm(t2));
+      if (lane == 0) ys[k0 + w] = make_float2(t2.hi, t2.lo);
     }
     __syncthreads();
   }
   for (int i = tid; i < n; i += blockDim.x) {
-    const double x = ys[i];
-    if (!isfinite(x)) raise_error(st, PSFM_ERR_SINGULAR);
+    const double y = (double)ys[i].x + (double)ys[i].y;
+    x_out[i] = x_in ? x_in[i] + y : y;
+  }
+}
+
+// r = b - M x in FP64 (one warp per row).
+__global__ void __launch_bounds__(256) k_residual(int n, const double* M, const double* b,
+                                                  const double* x, double* r,
+                                                  const DevState* st) {
+  if (st->error || st->done || st->chol_fail) return;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int c = lane; c < n; c += 32) s = fma(M[(int64_t)row * n + c], x[c], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) r[row] = b[row] - s;
+}
+
+// Scatter the solution vector into the device solution (b0, d0, a_{k,s}).
+__global__ void k_store_solution(int n, int joint, const double* x, double* dsol,
+                                 DevState* st) {
+  if (st->error || st->done || st->chol_fail) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double v = x[i];
+    if (!isfinite(v)) atomicCAS(&st->error, 0, PSFM_ERR_SINGULAR);
     if (joint) {
-      if (i == 0) dsol[0] = x;
-      else if (i == n - 1) dsol[1] = x;
-      else dsol[2 + (i - 1)] = x;
+      if (i == 0) dsol[0] = v;
+      else if (i == n - 1) dsol[1] = v;
+      else dsol[2 + (i - 1)] = v;
     } else {
-      dsol[2 + i] = x;
+      dsol[2 + i] = v;
     }
   }
 }
@@ -990,6 +1190,34 @@ __global__ void __launch_bounds__(1024) k_lu_solve(int N, int joint, const doubl
   }
 }
 
+__device__ __forceinline__ double cval(float v) { return (double)v; }
+__device__ __forceinline__ double cval(double v) { return v; }
+__device__ __forceinline__ double cval(float2 v) { return (double)v.x + (double)v.y; }
+
+// sum_k a_k C_k(pix): FP64 products for FP32 / FP64 design blocks, double-float products on
+// the FP32 pipes for double-float blocks.
+__device__ __forceinline__ double basis_model(const double* ak, const float2*, const float* C,
+                                              int Nb, int P, int pix) {
+  double m = 0.0;
+  for (int k = 0; k < Nb; ++k) m += ak[k] * (double)C[(int64_t)k * P + pix];
+  return m;
+}
+__device__ __forceinline__ double basis_model(const double* ak, const float2*, const double* C,
+                                              int Nb, int P, int pix) {
+  double m = 0.0;
+  for (int k = 0; k < Nb; ++k) m += ak[k] * C[(int64_t)k * P + pix];
+  return m;
+}
+__device__ __forceinline__ double basis_model(const double*, const float2* akf, const float2* C,
+                                              int Nb, int P, int pix) {
+  df m = {0.f, 0.f};
+  for (int k = 0; k < Nb; ++k) {
+    const float2 c = C[(int64_t)k * P + pix];
+    df_fma(m, df{akf[k].x, akf[k].y}, df{c.x, c.y});
+  }
+  return df_to_d(df_norm(m));
+}
+
 struct Chi2Params {
   StampParams sp;
   const double* gv;
@@ -1026,7 +1254,12 @@ __global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
     s_delta = d;
   }
   __syncthreads();
-  for (int k = tid; k < Nb; k += 256) ak[k] *= P.psi[k];
+  float2* akf = reinterpret_cast<float2*>(ak + Nb);  // the same split into FP32 pairs
+  for (int k = tid; k < Nb; k += 256) {
+    ak[k] *= P.psi[k];
+    const df d = df_split(ak[k]);
+    akf[k] = make_float2(d.hi, d.lo);
+  }
   __syncthreads();
   const double delta = s_delta, d0 = Q.dsol[1];
   const T* Cr = reinterpret_cast<const T*>(P.C) + (int64_t)r * Nb * P.P;
@@ -1038,8 +1271,7 @@ __global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
     const int64_t o = (int64_t)gy * P.g.pitch + gx;
     if ((P.m1[o] | P.m2[o]) & P.badmask) continue;
     const double R = P.i1[o], I2 = P.i2[o];
-    double model = delta * R + d0;
-    for (int k = 0; k < Nb; ++k) model += ak[k] * (double)Cr[(int64_t)k * P.P + pix];
+    const double model = delta * R + d0 + basis_model(ak, akf, Cr, Nb, P.P, pix);
     const double res = I2 - model;
     const double den = ((double)P.v1[o] + (double)P.v2[o]) + Q.alpha * fabs(I2);
     q += res * res / den;
@@ -1071,12 +1303,14 @@ __global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
 __global__ void __launch_bounds__(1024) k_reject(int nreg, int max_cand, int max_iter,
                                                  double nsig, const int32_t* cand, int32_t* ptr,
                                                  int32_t* cand_stat, const double* chi2,
-                                                 DevState* st) {
-  __shared__ double sh[32];
+                                                 int32_t* fresh, int32_t* removed, DevState* st) {
+  __shared__ double sh[33];
   __shared__ int s_finish;
   if (st->error || st->done) return;
   double n = 0.0, sum = 0.0;
   for (int r = threadIdx.x; r < nreg; r += blockDim.x) {
+    fresh[r] = 0;
+    removed[r] = 0;
     int cx, cy;
     if (!region_active(ptr, cand, r, max_cand, &cx, &cy)) continue;
     sum += chi2[r];
@@ -1105,6 +1339,7 @@ __global__ void __launch_bounds__(1024) k_reject(int nreg, int max_cand, int max
       if (chi2[r] > thr) {
         cand_stat[(int64_t)r * max_cand + ptr[r]] = PSFM_CAND_REJECTED;
         ptr[r] += 1;
+        removed[r] = 1;
         nrej += 1.0;
       }
     }
@@ -1163,10 +1398,16 @@ void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b) {
   b.M = ws.take<double>((size_t)p.Nsys * p.Nsys);
   b.v = ws.take<double>(p.Nsys);
   b.L = ws.take<double>((size_t)p.Nsys * p.Nsys);
-  b.Linv = ws.take<double>((size_t)((p.Nsys + kNB - 1) / kNB) * kNB * kNB);
+  b.rinv = ws.take<float2>((size_t)((p.Nsys + kNB - 1) / kNB) * kNB * kNB);
+  b.Lh = ws.take<float>((size_t)p.Nsys * p.Nsys);
+  b.Ll = ws.take<float>((size_t)p.Nsys * p.Nsys);
+  b.x = ws.take<double>(p.Nsys);
   b.y = ws.take<double>(p.Nsys);
   b.piv = ws.take<int32_t>(p.Nsys);
   b.gv = ws.take<double>((size_t)p.nreg * p.Ns);
+  b.gp = ws.take<double>((size_t)p.nreg * (p.Ns + 1) * (p.Ns + 1));
+  b.fresh = ws.take<int32_t>(p.nreg);
+  b.removed = ws.take<int32_t>(p.nreg);
 }
 
 psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* dsol,
@@ -1205,6 +1446,7 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   sp.cand = b.cand;
   sp.ptr = b.ptr;
   sp.have = b.have;
+  sp.fresh = b.fresh;
   sp.C = b.C;
   sp.G = b.G;
   sp.Gt = b.Gt;
@@ -1224,9 +1466,13 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   sy.Gt = b.Gt;
   sy.footsum = b.foot;
   sy.gv = b.gv;
+  sy.gp = b.gp;
+  sy.fresh = b.fresh;
+  sy.removed = b.removed;
   sy.dsol = dsol;
   sy.M = b.M;
-  sy.L = b.L;
+  sy.Lh = b.Lh;
+  sy.Ll = b.Ll;
   sy.v = b.v;
   sy.st = st;
 
@@ -1240,7 +1486,6 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
 
   // design block storage is double for the FP64 and double-float modes, float for FP32
   const int prec = p.cfg.precision;
-  const bool wide = prec != PSFM_PREC_FP32;
   const size_t esz = prec == PSFM_PREC_FP64 ? sizeof(double) : sizeof(float);
   size_t sm_design = esz * ((size_t)p.foot * p.foot + (size_t)p.foot * p.sw);
   const int nblk = (p.Nc + 3) / 4, npair = nblk * (nblk + 1) / 2;
@@ -1248,14 +1493,16 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   if (prec == PSFM_PREC_F32X2) {
     sm_design = sizeof(float) * ((size_t)p.foot * p.foot + 2 * (size_t)p.foot * p.sw +
                                  2 * (size_t)(p.dmax + 1) * p.w);
-    sm_gram = sizeof(double) * npair * 16 + sizeof(float) * (2 * nblk * 4 * 32 + 64);
+    const int nsl = kGramThreads / npair > 1 ? kGramThreads / npair : 1;
+    sm_gram = sizeof(float2) * nsl * npair * 16 + sizeof(float) * (4 * nblk * 4 * kGramChunk + 2 * kGramChunk);
   }
   if (sm_design > 200 * 1024 || sm_gram > 200 * 1024) return PSFM_ERR_UNSUPPORTED;
   auto design = prec == PSFM_PREC_FP64 ? k_stamp_design<double>
                 : prec == PSFM_PREC_F32X2 ? k_stamp_design_df : k_stamp_design<float>;
   auto gram = prec == PSFM_PREC_FP64 ? k_stamp_gram<double>
               : prec == PSFM_PREC_F32X2 ? k_stamp_gram_df : k_stamp_gram<float>;
-  auto chi2 = wide ? k_chi2<double> : k_chi2<float>;
+  auto chi2 = prec == PSFM_PREC_FP64 ? k_chi2<double>
+              : prec == PSFM_PREC_F32X2 ? k_chi2<float2> : k_chi2<float>;
   if (cudaFuncSetAttribute(design, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_design) !=
           cudaSuccess ||
       cudaFuncSetAttribute(gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_gram) !=
@@ -1263,40 +1510,57 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
     return PSFM_ERR_CUDA;
   const int N = p.Nsys;
   const int64_t nthr = (int64_t)N * N;
+  const int N1 = p.Ns + 1;
+  const int asm_chunk = (40 * 1024) / (N1 * N1 * (int)sizeof(double));
+  const size_t sm_asm = sizeof(double) * (size_t)asm_chunk * N1 * N1;
   const int npanel = (N + kNB - 1) / kNB;
-  const size_t sm_solve = sizeof(double) * ((size_t)N + 33 * 33);
+  const size_t sm_solve = sizeof(float2) * ((size_t)N + 33 * 33 + 32);
   if (sm_solve > 200 * 1024) return PSFM_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sm_solve) != cudaSuccess)
     return PSFM_ERR_CUDA;
+  // Gram blocks of regions that never hold a stamp stay zero (they are weighted by zero); M
+  // starts empty and is updated by the stamps that join or leave it
+  if (cudaMemsetAsync(b.Gt, 0, sizeof(double) * (size_t)p.nreg * p.Nc * p.Nc, s) != cudaSuccess ||
+      cudaMemsetAsync(b.M, 0, sizeof(double) * (size_t)p.Nsys * p.Nsys, s) != cudaSuccess ||
+      cudaMemsetAsync(b.fresh, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess ||
+      cudaMemsetAsync(b.removed, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess)
+    return PSFM_ERR_CUDA;
   for (int it = 0; it < p.cfg.max_iter; ++it) {
     prof_begin("stamps", s);
     design<<<dim3(p.nreg, p.ng), 256, sm_design, s>>>(sp);
-    gram<<<p.nreg, 256, sm_gram, s>>>(sp);
+    gram<<<p.nreg, prec == PSFM_PREC_F32X2 ? kGramThreads : 256, sm_gram, s>>>(sp);
     prof_end("stamps", s, 2);
     prof_begin("system", s);
     k_norm<<<1, 1024, 0, s>>>(sy);
-    k_assemble<<<(unsigned)((nthr + 255) / 256), 256, 0, s>>>(sy);
-    prof_end("system", s, 2);
+    k_system_delta<<<(unsigned)((nthr + 255) / 256), 256, sm_asm, s>>>(sy, 0, asm_chunk);
+    k_rhs<<<(N * 32 + 255) / 256, 256, 0, s>>>(sy);
+    prof_end("system", s, 3);
     prof_begin("cholesky", s);
     for (int kb = 0; kb < npanel; ++kb) {
-      k_chol_diag<<<1, 32, 0, s>>>(N, kb, b.L, b.Linv, st);
+      k_chol_diag<<<1, kDiagThreads, 0, s>>>(N, kb, b.Lh, b.Ll, b.rinv, st);
       const int k0 = kb * kNB, m = (N - k0) < kNB ? N - k0 : kNB;
       const int rest = N - k0 - m;
       if (rest > 0) {
-        k_chol_trsm<<<(rest + 3) / 4, 128, 0, s>>>(N, kb, b.L, b.Linv, st);
+        k_chol_trsm<<<(rest + 7) / 8, 256, 0, s>>>(N, kb, b.Lh, b.Ll, b.rinv, st);
         const int nt = (rest + 15) / 16;
-        k_chol_update<<<nt * (nt + 1) / 2, 256, 0, s>>>(N, kb, b.L, st);
+        k_chol_update<<<nt * (nt + 1) / 2, 256, 0, s>>>(N, kb, b.Lh, b.Ll, st);
       }
     }
-    k_chol_solve<<<1, 1024, sm_solve, s>>>(N, sy.joint, b.L, b.Linv, b.v, dsol, st);
+    k_chol_solve<<<1, 1024, sm_solve, s>>>(N, b.Lh, b.Ll, b.rinv, b.v, nullptr, b.x, st);
+    for (int ref = 0; ref < 2; ++ref) {
+      k_residual<<<(N * 32 + 255) / 256, 256, 0, s>>>(N, b.M, b.v, b.x, b.y, st);
+      k_chol_solve<<<1, 1024, sm_solve, s>>>(N, b.Lh, b.Ll, b.rinv, b.y, b.x, b.x, st);
+    }
+    k_store_solution<<<(N + 255) / 256, 256, 0, s>>>(N, sy.joint, b.x, dsol, st);
     k_lu_solve<<<1, 1024, 0, s>>>(N, sy.joint, b.M, b.v, b.L, b.y, b.piv, dsol, st);
-    prof_end("cholesky", s, 3 * npanel + 2);
+    prof_end("cholesky", s, 3 * npanel + 7);
     prof_begin("chi2_reject", s);
-    chi2<<<p.nreg, 256, sizeof(double) * p.Nb, s>>>(cq);
+    chi2<<<p.nreg, 256, (sizeof(double) + sizeof(float2)) * p.Nb + 16, s>>>(cq);
     k_reject<<<1, 1024, 0, s>>>(p.nreg, p.max_cand, p.cfg.max_iter, p.cfg.reject_nsigma, b.cand,
-                                b.ptr, b.cand_stat, b.chi2, st);
-    prof_end("chi2_reject", s, 2);
+                                b.ptr, b.cand_stat, b.chi2, b.fresh, b.removed, st);
+    k_system_delta<<<(unsigned)((nthr + 255) / 256), 256, sm_asm, s>>>(sy, 1, asm_chunk);
+    prof_end("chi2_reject", s, 3);
   }
   prof_begin("rbad", s);
   if (launch_rbad(p, t, dsol, st, s) != cudaSuccess) return PSFM_ERR_CUDA;

@@ -47,15 +47,13 @@ __global__ void k_median_hist(HistParams P) {
   for (int i = threadIdx.x; i < 2048; i += blockDim.x) h[i] = 0;
   __syncthreads();
   const uint32_t prefix = P.st->sel_prefix;
-  const int64_t n = (int64_t)P.W * P.H;
-  // warp-uniform trip count so that the warp-wide match below sees every lane
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n;
-       base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = base + threadIdx.x;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  // rows strided over the grid; warp-uniform trip count so that the warp-wide match below
+  // sees every lane
+  for (int y = blockIdx.y; y < P.H; y += gridDim.y) {
     bool valid = false;
     uint32_t bin = 0;
-    if (i < n) {
-      const int y = (int)(i / P.W), x = (int)(i - (int64_t)y * P.W);
+    if (x < P.W) {
       const int64_t o = (int64_t)y * P.pitch + x;
       if (!((P.m1[o] | P.m2[o]) & P.badmask)) {
         const float s = P.i1[o] + P.i2[o];
@@ -335,7 +333,7 @@ cudaError_t launch_extract(const Plan& p, DevState* st, const SolveBuffers& b, c
   HistParams hp{ref, img, mask_ref, mask_img, p.W, p.H, p.pitch, p.cfg.badmask, 0, b.hist, st};
   for (int pass = 0; pass < 3; ++pass) {
     hp.pass = pass;
-    k_median_hist<<<4 * 152, 512, 0, s>>>(hp);
+    k_median_hist<<<dim3((p.W + 255) / 256, p.H < 256 ? p.H : 256), 256, 0, s>>>(hp);
     k_median_select<<<1, 1024, 0, s>>>(b.hist, pass, st);
   }
   const int nwords = (p.W + 31) / 32;

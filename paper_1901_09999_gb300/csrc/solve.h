@@ -29,10 +29,16 @@ struct SolveBuffers {
   double* M;  // [Nsys][Nsys]
   double* v;  // [Nsys]
   double* L;  // [Nsys][Nsys] factor
-  double* Linv;  // [Nsys/32][32][32] inverses of the diagonal blocks of L
+  float2* rinv;  // [Nsys/32][32][32] inverses of the diagonal blocks (double-float)
+  float* Lh;     // [Nsys][Nsys] double-float Cholesky factor, high parts
+  float* Ll;     // low parts
+  double* x;     // [Nsys] solution being refined
   double* y;  // [Nsys]
   int32_t* piv;  // [Nsys] LU pivots
   double* gv;    // [nreg][Ns] spatial factors at the stamp centres, 0 when inactive
+  double* gp;    // [nreg][(Ns+1)^2] their pairwise products (index Ns stands for 1)
+  int32_t* fresh;    // [nreg] Gram computed in this iteration
+  int32_t* removed;  // [nreg] stamp rejected in this iteration
 };
 
 void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b);
