@@ -1,12 +1,13 @@
 #!/usr/bin/env python3
 """Benchmark of the PSF-matching hot path: PSF-matched Mpix/s (solve + convolve + variance).
 
-One step is one full subtraction of the full-chip workload through the C ABI call
-``psfm_subtract``: stamp extraction, basis convolution and Gram per stamp, normalisation,
-the FP64 solve with the iterative stamp rejection, r_bad, then the spatially varying
-convolution of the whole chip, the per-patch variance propagation, the mask propagation and
-the covariance pseudo-matrix.  Inputs (4846 x 4868 float32 images, variances and uint16
-masks; about 472 MB) are resident in HBM and larger than L2.
+One step is one batch of full-chip subtractions through the C ABI (``psfm_batch_subtract``;
+``--single`` uses one ``psfm_subtract`` per step): for every chip, stamp extraction, basis
+convolution and Gram per stamp, normalisation, the solve with the iterative stamp rejection,
+r_bad, then the spatially varying convolution of the whole chip, the per-patch variance
+propagation, the mask propagation and the covariance pseudo-matrix.  The default batch is 4
+distinct 4846 x 4868 chips (seeds 2..5) in flight on 4 streams, replayed from a CUDA graph.
+Inputs (472 MB per chip) are resident in HBM and larger than L2.
 
 Prints one JSON line on rank 0.  ``--impl reference`` times the FP64 CPU oracle on bounded
 cut-outs of the same workload instead.
@@ -15,7 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -34,6 +35,7 @@ WORKLOAD = dict(
     spatial_order=2, stamps=300, grid=(15, 20), seed=2)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+PRECISION = {"fp64": 0, "fp32": 1, "f32x2": 4}
 
 
 def parse():
@@ -42,44 +44,53 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--chips", type=int, default=4, help="full chips per step (batched)")
+    ap.add_argument("--streams", type=int, default=4)
+    ap.add_argument("--single", action="store_true", help="one psfm_subtract per step, no batch")
+    ap.add_argument("--exposure", action="store_true",
+                    help="60 uneven chips of one exposure (GPU-generated inputs)")
+    ap.add_argument("--small", action="store_true", help="512x512 plain-method workload")
+    ap.add_argument("--precision", default="f32x2", choices=list(PRECISION))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--small", action="store_true", help="512x512 plain-method workload")
-    ap.add_argument("--precision", default="f32x2", choices=["fp64", "f32x2", "fp32"],
-                    help="arithmetic of the stamp design blocks and Gram matrices")
     return ap.parse_args()
 
 
-PRECISION = {"fp64": 0, "fp32": 1, "f32x2": 4}
-
-
-def workload_specs(small, precision="f32x2"):
+def chip_specs(precision, small=False):
     from paper_1901_09999_gb300 import psfm as P
     from paper_1901_09999_gb300 import synth
     prec = PRECISION[precision]
     if small:
-        b = P.basis_spec((0.7, 1.5, 3.0), (4, 2, 2), 10, 0)
-        c = P.config(badmask=synth.BADMASK, precision=prec)
-    else:
-        b = P.basis_spec(WORKLOAD["basis_sigma"], WORKLOAD["degrees"], 15, 2)
-        c = P.config(badmask=synth.BADMASK, grid_nx=15, grid_ny=20, precision=prec)
-    return b, c
+        return (P.basis_spec((0.7, 1.5, 3.0), (4, 2, 2), 10, 0),
+                P.config(badmask=synth.BADMASK, precision=prec))
+    return (P.basis_spec(WORKLOAD["basis_sigma"], WORKLOAD["degrees"], 15, 2),
+            P.config(badmask=synth.BADMASK, grid_nx=15, grid_ny=20, precision=prec))
 
 
-def make_field(small, seed):
+def _gen_chip(args):
+    seed, small = args
+    sys.path.insert(0, ROOT)
     from paper_1901_09999_gb300 import synth
-    if small:
-        return synth.small_gaussian_field(seed)
-    return synth.full_chip_field(seed)
+    f = synth.small_gaussian_field(seed) if small else synth.full_chip_field(seed)
+    return f.sci, f.ref, f.var_sci, f.var_ref, f.mask_sci, f.mask_ref
+
+
+def gen_chips(n, small):
+    """Generate n seeded chips in parallel worker processes (spawned before any CUDA use)."""
+    seeds = [(WORKLOAD["seed"] + i, small) for i in range(n)]
+    if n == 1:
+        return [_gen_chip(seeds[0])]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(n, os.cpu_count() or 1)) as pool:
+        return pool.map(_gen_chip, seeds)
 
 
 def flops_per_pixel(b):
-    """Algorithmic work per output pixel (image: separable passes plus coefficient
-    evaluation; variance: direct w^2 taps)."""
+    """Algorithmic work per output pixel: image = separable passes plus per-pixel coefficient
+    polynomials, 2w(N_H + N_b) + 2N_b(N_s + 1); variance = direct w^2 taps, 2w^2."""
     from paper_1901_09999_gb300 import psfm as P
     w = 2 * b.half_width + 1
-    nb = P.basis_size(b)
-    ns = P.spatial_size(b)
+    nb, ns = P.basis_size(b), P.spatial_size(b)
     nh = sum(b.degree[g] + 1 for g in range(b.n_gauss))
     return 2 * w * (nh + nb) + 2 * nb * (ns + 1), 2 * w * w
 
@@ -99,9 +110,9 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "200"], stdout=self.f,
-                                         stderr=subprocess.DEVNULL)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-i", str(self.index),
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
@@ -176,8 +187,8 @@ def oracle_sample():
 
 def run_oracle_subprocess(reps):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; r=[bench.oracle_sample() for _ in range(%d)];"
-            "print(json.dumps(r))" % (ROOT, reps))
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "r=[bench.oracle_sample() for _ in range(%d)]; print(json.dumps(r))" % (ROOT, reps))
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
                          cwd=ROOT, timeout=1800)
     if out.returncode != 0:
@@ -185,7 +196,7 @@ def run_oracle_subprocess(reps):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(reps=1):
+def cpu_baseline(reps):
     r = run_oracle_subprocess(reps)
     mpix = sum(a for a, _ in r)
     sec = sum(b for _, b in r)
@@ -195,33 +206,57 @@ def cpu_baseline(reps=1):
                       f"single-threaded BLAS, {sec:.1f} s"}
 
 
-# ----------------------------------------------------------------------------- main
+def reference_arm(args):
+    for _ in range(args.warmup):
+        run_oracle_subprocess(1)
+    r = run_oracle_subprocess(args.steps)
+    mpix = sum(a for a, _ in r)
+    sec = sum(b for _, b in r)
+    val = mpix / sec
+    print(json.dumps({
+        "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * sec / len(r), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference", "config": dict(WORKLOAD, sample="288x288 cut-out per step"),
+        "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(r)} x 288x288 cut-outs, {sec:.1f} s"},
+        "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def exposure_chips(dev, seed=4, n=60, precision="f32x2"):
+    """60 chips of uneven sizes, PSF FWHM 3-8 px, masked 1-20 %, S = 1..3, 49-70 terms, basis
+    widths by the paper's ISIS prescription scaled by the chip's worse seeing (GPU-generated)."""
+    from paper_1901_09999_gb300 import psfm as P
+    from paper_1901_09999_gb300 import synth
+    chips, bases = [], []
+    for c in synth.exposure_chips(seed, n):
+        fmax = max(c["fwhm_ref"], c["fwhm_sci"])
+        sig = synth.isis_prescription_sigmas(fmax)
+        h = int(np.ceil(4.7 * sig[-1]))
+        chips.append(synth.torch_chip_pair(c["seed"], c["W"], c["H"], c["fwhm_ref"],
+                                           c["fwhm_sci"], c["mask_frac"], dev))
+        bases.append(P.basis_spec(sig, c["degrees"], h, c["spatial_order"]))
+    cfg = P.config(badmask=synth.BADMASK, grid_nx=12, grid_ny=12, precision=PRECISION[precision])
+    return chips, bases, cfg
+
 
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-
     if args.impl == "reference":
-        if rank != 0:
-            return 0
-        for _ in range(args.warmup):
-            run_oracle_subprocess(1)
-        r = run_oracle_subprocess(args.steps)
-        mpix = sum(a for a, _ in r)
-        sec = sum(b for _, b in r)
-        val = mpix / sec
-        print(json.dumps({
-            "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": 0, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000 * sec / len(r), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
-            "config": dict(WORKLOAD, sample="288x288 cut-out per step"),
-            "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{len(r)} x 288x288 cut-outs, {sec:.1f} s"},
-            "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        if rank == 0:
+            reference_arm(args)
         return 0
+
+    nchips = 1 if args.single else args.chips
+    host_chips = None
+    if not args.exposure:
+        # numpy generation in spawned workers before the first CUDA call
+        host_chips = gen_chips(nchips, args.small)
 
     import torch
     import torch.distributed as dist
@@ -233,100 +268,136 @@ def main():
     build.build()
     from paper_1901_09999_gb300 import psfm as P
 
-    b, c = workload_specs(args.small, args.precision)
-    field = make_field(args.small, WORKLOAD["seed"] + rank)
-    H, W = field.shape
-
     def put(a):
         if a.dtype == np.uint16:
             a = a.view(np.int16)
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
 
-    t_img, t_ref = put(field.sci), put(field.ref)
-    t_vi, t_vr = put(field.var_sci), put(field.var_ref)
-    t_mi, t_mr = put(field.mask_sci), put(field.mask_ref)
-    out = torch.empty_like(t_img)
-    out_var = torch.empty_like(t_img)
-    out_mask = torch.empty_like(t_mi)
-    shape = P.psfm_shape(W, H, W)
-    need = P.psfm_workspace_size(P.OP_SUBTRACT, shape, b, c)
-    ws = torch.empty(need, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
+    if args.exposure:
+        chips, bases, cfg = exposure_chips(dev, precision=args.precision)
+        workload = dict(workload="exposure_60_uneven_chips_S1-3_49-70terms", chips=len(chips),
+                        mpix=sum(c["img"].numel() for c in chips) / 1e6)
+    else:
+        b, cfg = chip_specs(args.precision, args.small)
+        chips = [dict(img=put(c[0]), ref=put(c[1]), var_img=put(c[2]), var_ref=put(c[3]),
+                      mask_img=put(c[4]), mask_ref=put(c[5])) for c in host_chips]
+        bases = [b] * len(chips)
+        workload = (dict(WORKLOAD) if not args.small else
+                    {"workload": "small_512x512_gaussian_S0_27terms"})
+        workload.update(chips_per_step=len(chips),
+                        seeds=[WORKLOAD["seed"] + i for i in range(len(chips))])
+    del host_chips
+    px_per_step = sum(c["img"].numel() for c in chips)
+    stream = torch.cuda.Stream()
 
-    def step():
-        return P.psfm_subtract(t_img, t_ref, t_vi, t_vr, t_mi, t_mr, b, c, out=out, out_var=out_var,
-                               out_mask=out_mask, workspace=ws, stream=stream)
+    if args.single:
+        c0 = chips[0]
+        outs = dict(out=torch.empty_like(c0["img"]), out_var=torch.empty_like(c0["img"]),
+                    out_mask=torch.empty_like(c0["mask_img"]))
+        shape = P.psfm_shape(c0["img"].shape[1], c0["img"].shape[0], c0["img"].stride(0))
+        ws = torch.empty(P.psfm_workspace_size(P.OP_SUBTRACT, shape, bases[0], cfg),
+                         dtype=torch.uint8, device=dev)
 
-    for _ in range(max(3, args.warmup)):
-        sol = step()[4]
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+        def step():
+            P.psfm_subtract(c0["img"], c0["ref"], c0["var_img"], c0["var_ref"], c0["mask_img"],
+                            c0["mask_ref"], bases[0], cfg, workspace=ws, stream=stream, **outs)
+        batch = None
+    else:
+        batch = P.Batch(chips, bases, cfg, n_streams=args.streams, want_cov=True)
 
-    launches0 = P.psfm_launch_count()
-    P.psfm_profile_enable(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+        def step():
+            batch.run(stream)
+
+    sols = None
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+        if batch is not None:
+            sols = batch.solutions(stream)
         torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            sol = step()[4]
-        e1.record(stream)
-        torch.cuda.synchronize()
-    prof = P.psfm_profile_read()
-    P.psfm_profile_enable(False)
-    launches = P.psfm_launch_count() - launches0
-    ms = e0.elapsed_time(e1)
+        if world > 1:
+            dist.barrier()
+        l0 = P.psfm_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if batch is not None:
+            sols = batch.solutions(stream)
+            launches = batch.kernel_count() * args.steps
+        else:
+            launches = P.psfm_launch_count() - l0
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
-    mpix_total = W * H * world * args.steps / 1e6
-    value = mpix_total / (ms / 1e3)
+    value = px_per_step * world * args.steps / 1e6 / (ms / 1e3)
 
-    # roofline of the dominant kernel (the spatially varying image convolution)
-    f_img, f_var = flops_per_pixel(b)
-    stages = {k: v for k, v in prof.items()}
-    conv_ms, conv_n, _ = stages.get("conv_image", (float("nan"), 1, 1))
-    var_ms, var_n, _ = stages.get("variance", (float("nan"), 1, 1))
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
-    achieved = W * H * f_img / (conv_ms / conv_n / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None, "kernel": "k_conv_image",
-                "kernel_ms": conv_ms / conv_n,
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
-                "variance_kernel": {"achieved": W * H * f_var / (var_ms / var_n / 1e3) / 1e12,
+    # roofline of the dominant kernel, timed with the library's CUDA events on its stream in a
+    # separate (non-graph, unshared) subtraction of chip 0 right after the timed region
+    c0, b0 = chips[0], bases[0]
+    P.psfm_profile_enable(True)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            P.psfm_subtract(c0["img"], c0["ref"], c0["var_img"], c0["var_ref"], c0["mask_img"],
+                            c0["mask_ref"], b0, cfg, stream=stream)
+    torch.cuda.synchronize()
+    prof = P.psfm_profile_read()
+    P.psfm_profile_enable(False)
+    f_img, f_var = flops_per_pixel(b0)
+    npx0 = c0["img"].numel()
+    conv_ms, conv_n, _ = prof.get("conv_image", (float("nan"), 1, 1))
+    var_ms, var_n, _ = prof.get("variance", (float("nan"), 1, 1))
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    achieved = npx0 * f_img / (conv_ms / conv_n / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_conv_image", "kernel_ms": conv_ms / conv_n,
+                "algorithmic_flop_per_px": f_img,
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived; an "
+                             "FMA-chain probe measured 74.7 TFLOP/s)",
+                "variance_kernel": {"achieved": npx0 * f_var / (var_ms / var_n / 1e3) / 1e12,
                                     "ms": var_ms / var_n}}
+    stages = {k: v[0] / v[2] for k, v in prof.items()}
 
-    # end to end through the public API with host buffers
     e2e = None
-    if not args.no_e2e:
-        pin = lambda t: t.cpu().pin_memory()
-        h_in = [pin(t) for t in (t_img, t_ref, t_vi, t_vr, t_mi, t_mr)]
-        h_out = [torch.empty(out.shape, dtype=out.dtype).pin_memory(),
-                 torch.empty(out.shape, dtype=out.dtype).pin_memory(),
-                 torch.empty(out_mask.shape, dtype=out_mask.dtype).pin_memory()]
-        d_in = [t_img, t_ref, t_vi, t_vr, t_mi, t_mr]
-        bi = sum(t.numel() * t.element_size() for t in h_in)
-        bo = sum(t.numel() * t.element_size() for t in h_out)
+    if not args.no_e2e and not args.exposure:
+        keys = ("img", "ref", "var_img", "var_ref", "mask_img", "mask_ref")
+        h_in = [[c[k].cpu().pin_memory() for k in keys] for c in chips]
+        if batch is not None:
+            d_out = [(batch.diff[i], batch.diff_var[i], batch.diff_mask[i])
+                     for i in range(len(chips))]
+        else:
+            d_out = [(outs["out"], outs["out_var"], outs["out_mask"])]
+        h_out = [[torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in o] for o in d_out]
+        bi = sum(t.numel() * t.element_size() for hs in h_in for t in hs)
+        bo = sum(t.numel() * t.element_size() for hs in h_out for t in hs)
 
         def e2e_step():
-            for d, h in zip(d_in, h_in):
-                d.copy_(h, non_blocking=True)
+            for c, hs in zip(chips, h_in):
+                for k, h in zip(keys, hs):
+                    c[k].copy_(h, non_blocking=True)
             step()
-            for h, d in zip(h_out, (out, out_var, out_mask)):
-                h.copy_(d, non_blocking=True)
+            for hs, ds in zip(h_out, d_out):
+                for h, d in zip(hs, ds):
+                    h.copy_(d, non_blocking=True)
 
-        e2e_step()
-        torch.cuda.synchronize()
-        n2 = max(2, args.steps // 2)
-        e0.record(stream)
-        for _ in range(n2):
+        with torch.cuda.stream(stream):
             e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e2e = {"value": W * H * n2 / 1e6 / (e0.elapsed_time(e1) / 1e3), "unit": "Mpix/s",
+            torch.cuda.synchronize()
+            n2 = max(2, args.steps // 2)
+            e0.record(stream)
+            for _ in range(n2):
+                e2e_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        e2e = {"value": px_per_step * n2 / 1e6 / (e0.elapsed_time(e1) / 1e3), "unit": "Mpix/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
     if rank != 0:
@@ -339,19 +410,26 @@ def main():
             cpu = cpu_baseline(8)
         except Exception as e:  # the oracle is a reported baseline only
             cpu = {"error": str(e)[-300:]}
+    sol_info = None
+    if sols is not None:
+        sol_info = [{"n_used": s.n_used, "n_iter": s.n_iter, "b0": s.b0, "r_bad": s.r_bad}
+                    for s in sols[:4]]
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD if not args.small else {"workload": "small_512x512_gaussian_S0_27terms"},
-                       l2="inputs (472 MB) larger than L2, no flush",
-                       precision=f"stamp design+Gram {args.precision}, FP64 normal equations, FP32 image/variance passes",
+        "config": dict(workload, l2="inputs larger than L2 (472 MB per chip), no flush",
+                       precision=f"stamp design+Gram {args.precision}, normal equations "
+                                 "double-float Cholesky + FP64 refinement, FP32 image/variance",
+                       batching=("none" if args.single else
+                                 f"{len(chips)} chips on {args.streams} streams, CUDA graph replay"),
                        parallelism=f"replicas x{world}"),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clk.summary(), "stages_ms": {k: v[0] / args.steps for k, v in stages.items()},
-        "solution": {"n_used": sol.n_used, "n_iter": sol.n_iter, "b0": sol.b0, "r_bad": sol.r_bad},
+        "clocks": clk.summary(), "single_chip_stages_ms": stages, "solutions": sol_info,
     }
     print(json.dumps(line))
+    if batch is not None:
+        batch.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

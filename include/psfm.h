@@ -243,6 +243,38 @@ psfm_status psfm_stack(int32_t n, const float* const* imgs, const float* const* 
                        double* cov_out, int32_t cov_out_w, psfm_solution* sols,
                        void* workspace, size_t ws_bytes, psfm_stream stream);
 
+/* Batched subtraction (Sec. 3, Sec. 4 applied chip by chip; the batching itself has no
+ * counterpart in the paper).  A batch is n chips, each with its own shape, basis (size, degrees,
+ * spatial order) and buffers; the configuration is shared.  psfm_batch_create lays out one
+ * caller workspace (psfm_batch_workspace_size bytes, 256-byte aligned) for all chips, uploads
+ * their tables once and creates n_streams CUDA streams (1..32) on which chips run
+ * concurrently.  The batch object is host memory owned by the library until
+ * psfm_batch_destroy.
+ * psfm_batch_subtract enqueues every chip's psfm_subtract work (extractor, rejection loop,
+ * image, variance, mask, pseudo-matrix of width 2w-1 when cov_outs[i] is set) without any host
+ * synchronisation.  On a non-default stream the first call is captured into a CUDA graph and
+ * later calls with the same buffer pointers replay it; on the legacy default stream the work
+ * is enqueued directly.  Array arguments are host arrays of n device pointers; diff_vars,
+ * diff_masks and cov_outs may be NULL.  Errors raised on the device are reported by
+ * psfm_batch_solutions, which synchronises `stream` and fills n host solutions (sols may be
+ * NULL) and returns the first chip's non-OK status.  Concurrent calls on one batch race. */
+typedef struct psfm_batch psfm_batch;
+size_t psfm_batch_workspace_size(int32_t n, const psfm_shape* shapes,
+                                 const psfm_basis_spec* bases, const psfm_config* cfg);
+psfm_status psfm_batch_create(int32_t n, const psfm_shape* shapes, const psfm_basis_spec* bases,
+                              const psfm_config* cfg, int32_t n_streams, void* workspace,
+                              size_t ws_bytes, psfm_batch** out);
+psfm_status psfm_batch_subtract(psfm_batch* b, const float* const* imgs, const float* const* refs,
+                                const float* const* var_imgs, const float* const* var_refs,
+                                const uint16_t* const* mask_imgs,
+                                const uint16_t* const* mask_refs, float* const* diffs,
+                                float* const* diff_vars, uint16_t* const* diff_masks,
+                                double* const* cov_outs, psfm_stream stream);
+psfm_status psfm_batch_solutions(psfm_batch* b, psfm_solution* sols, psfm_stream stream);
+/* Kernels one execution of the batch launches (counted when it was enqueued or captured). */
+long long psfm_batch_kernel_count(const psfm_batch* b);
+void psfm_batch_destroy(psfm_batch* b);
+
 /* psfm_convolve without a workspace (no counterpart in the paper: this is an integration
  * aid).  For callers that cannot allocate device memory or hand over a workspace -- for
  * example a plugin running inside another framework's CUDA graph capture, where allocation

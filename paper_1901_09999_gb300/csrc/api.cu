@@ -7,24 +7,13 @@
 #include <cstring>
 #include <vector>
 
+#include "host.h"
 #include "psfm_internal.h"
 #include "solve.h"
 
 using namespace psfm;
 
-namespace {
-
-constexpr int kMaxCovIn = 129;
-
-// Layout of the head of the workspace: [DevState][dsol][tables], uploaded in one copy.
-struct Head {
-  DevState* st = nullptr;
-  double* dsol = nullptr;
-  char* tables = nullptr;
-  size_t bytes = 0;
-  size_t offs[6];
-  std::vector<char> blob;
-};
+namespace psfm {
 
 size_t head_layout(const Plan& p, Head& h) {
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -247,9 +236,6 @@ psfm_status run_stack_impl(int n, const float* const* imgs, const float* const* 
   return cudaStreamSynchronize(st) == cudaSuccess ? PSFM_OK : PSFM_ERR_CUDA;
 }
 
-}  // namespace
-
-namespace psfm {
 psfm_status run_stack(int n, const float* const* imgs, const float* const* vars,
                       const uint16_t* const* masks, psfm_shape shape,
                       const double* const* src_xyf, const int32_t* n_src, double target_fwhm,
@@ -261,6 +247,7 @@ psfm_status run_stack(int n, const float* const* imgs, const float* const* vars,
                         out, out_var, out_mask, out_count, cov_out, cov_out_w, sols, ws,
                         ws_bytes, s);
 }
+
 }  // namespace psfm
 
 extern "C" {

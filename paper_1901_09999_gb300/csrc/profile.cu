@@ -45,10 +45,19 @@ thread_local cudaEvent_t t_begin = nullptr;
 
 }  // namespace
 
+bool capturing(cudaStream_t s);
+
+// Work enqueued while a stream is being captured into a graph is not timed (its events would
+// belong to the graph), only counted.
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
 void prof_begin(const char* name, cudaStream_t s) {
   (void)name;
-  if (!g_on) return;
   t_begin = nullptr;
+  if (!g_on || capturing(s)) return;
   if (cudaEventCreate(&t_begin) == cudaSuccess) cudaEventRecord(t_begin, s);
 }
 

@@ -474,3 +474,95 @@ def psfm_profile_read() -> dict:
         if lib.psfm_profile_entry(i, name, 64, C.byref(ms), C.byref(nl), C.byref(nc)) == 0:
             out[name.value.decode()] = (ms.value, nl.value, nc.value)
     return out
+
+
+# ------------------------------------------------------------------------ batches of chips
+
+def _batch_types(lib):
+    vp, i32, sz = C.c_void_p, C.c_int32, C.c_size_t
+    P = C.POINTER
+    lib.psfm_batch_workspace_size.argtypes = [i32, P(psfm_shape), P(psfm_basis_spec), P(psfm_config)]
+    lib.psfm_batch_workspace_size.restype = sz
+    lib.psfm_batch_create.argtypes = [i32, P(psfm_shape), P(psfm_basis_spec), P(psfm_config), i32,
+                                      vp, sz, P(vp)]
+    lib.psfm_batch_create.restype = i32
+    lib.psfm_batch_subtract.argtypes = [vp] + [P(vp)] * 10 + [vp]
+    lib.psfm_batch_subtract.restype = i32
+    lib.psfm_batch_solutions.argtypes = [vp, P(psfm_solution), vp]
+    lib.psfm_batch_solutions.restype = i32
+    lib.psfm_batch_kernel_count.argtypes = [vp]
+    lib.psfm_batch_kernel_count.restype = C.c_longlong
+    lib.psfm_batch_destroy.argtypes = [vp]
+    lib.psfm_batch_destroy.restype = None
+
+
+class Batch:
+    """Many chips subtracted by one call (C: psfm_batch_*).  ``chips`` is a list of dicts with
+    the CUDA tensors img, ref, var_img, var_ref, mask_img, mask_ref; ``bases`` one
+    psfm_basis_spec per chip.  Outputs are allocated here; run() enqueues (and on a
+    non-default stream captures / replays a CUDA graph), solutions() synchronises."""
+
+    def __init__(self, chips, bases, cfg, n_streams=4, want_cov=False):
+        torch = _torch()
+        self.lib = load()
+        _batch_types(self.lib)
+        self.n = len(chips)
+        self.chips = chips
+        self.bases = (psfm_basis_spec * self.n)(*bases)
+        self.cfg = cfg
+        shapes = [_shape_of(c["img"], c["ref"], c["var_img"], c["var_ref"], c["mask_img"],
+                            c["mask_ref"]) for c in chips]
+        self.shapes = (psfm_shape * self.n)(*shapes)
+        need = int(self.lib.psfm_batch_workspace_size(self.n, self.shapes, self.bases, C.byref(cfg)))
+        if need == 0:
+            raise PsfmError(1, "psfm_batch_workspace_size")
+        dev = chips[0]["img"].device
+        self.ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        self.h = C.c_void_p()
+        st = self.lib.psfm_batch_create(self.n, self.shapes, self.bases, C.byref(cfg), n_streams,
+                                        _ptr(self.ws), need, C.byref(self.h))
+        if st != PSFM_OK:
+            raise PsfmError(st, "psfm_batch_create")
+        self.diff = [_like(c["img"]) for c in chips]
+        self.diff_var = [_like(c["img"]) for c in chips]
+        self.diff_mask = [_like(c["mask_img"]) for c in chips]
+        self.cov = [torch.empty((cov_width(b, 1, 1),) * 2, dtype=torch.float64, device=dev)
+                    for b in bases] if want_cov else None
+
+    def _arr(self, ts):
+        return (C.c_void_p * self.n)(*[None if t is None else t.data_ptr() for t in ts])
+
+    def run(self, stream=None):
+        c = self.chips
+        a = [self._arr([x[k] for x in c]) for k in ("img", "ref", "var_img", "var_ref",
+                                                     "mask_img", "mask_ref")]
+        st = self.lib.psfm_batch_subtract(self.h, *a, self._arr(self.diff), self._arr(self.diff_var),
+                                          self._arr(self.diff_mask),
+                                          self._arr(self.cov) if self.cov else None,
+                                          _stream(stream))
+        if st != PSFM_OK:
+            raise PsfmError(st, "psfm_batch_subtract")
+
+    def kernel_count(self):
+        return int(self.lib.psfm_batch_kernel_count(self.h))
+
+    def solutions(self, stream=None):
+        sols = [Solution(basis_size(b) * spatial_size(b), _ncand(b, self.cfg, 0)) for b in self.bases]
+        arr = (psfm_solution * self.n)(*[s.c for s in sols])
+        st = self.lib.psfm_batch_solutions(self.h, arr, _stream(stream))
+        for s, c in zip(sols, arr):
+            s.c = c
+        if st != PSFM_OK:
+            raise PsfmError(st, "psfm_batch_solutions")
+        return sols
+
+    def close(self):
+        if self.h:
+            self.lib.psfm_batch_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

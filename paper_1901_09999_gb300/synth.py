@@ -364,3 +364,69 @@ def skycell_warps(seed: int = 5, n_warps: int = 16, size: int = 6000, n_stars: i
         warps.append(dict(image=img.astype(np.float32), var=np.maximum(img, 1.0).astype(np.float32),
                           mask=m, fwhm=fw, masked_frac=float(np.mean(m != 0))))
     return warps, np.stack([xs, ys, fl], 1)
+
+
+# --------------------------------------------------------------------------------------
+# Fast seeded generation on the GPU for large throughput workloads (torch; no method code)
+# --------------------------------------------------------------------------------------
+
+def torch_chip_pair(seed: int, W: int, H: int, fwhm_ref: float, fwhm_sci: float,
+                    mask_frac: float, device, stars_per_mpix: float = 100.0,
+                    sky: float = 500.0):
+    """Reference / science pair of circular-Gaussian star fields rendered on the GPU.
+
+    Stars at uniform sub-pixel positions (bilinear deposit, then a separable Gaussian blur),
+    flux log-uniform in [1e3, 1e5] e-, sky plus Poisson noise, variance = image, and defect
+    blocks (shared by both images) covering about ``mask_frac``.  Returns a dict of CUDA tensors
+    (img, ref, var_img, var_ref, mask_img, mask_ref) with the masks as int16."""
+    import torch
+    import torch.nn.functional as F
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    n = max(20, int(stars_per_mpix * W * H / 1e6))
+    xs = torch.rand(n, generator=g, device=device, dtype=torch.float64) * (W - 1)
+    ys = torch.rand(n, generator=g, device=device, dtype=torch.float64) * (H - 1)
+    fl = torch.exp(torch.rand(n, generator=g, device=device, dtype=torch.float64) *
+                   (math.log(1e5) - math.log(1e3)) + math.log(1e3))
+
+    def render(fwhm):
+        img = torch.zeros(H * W, device=device, dtype=torch.float64)
+        x0, y0 = xs.floor(), ys.floor()
+        fx, fy = xs - x0, ys - y0
+        for dx, dy, wgt in ((0, 0, (1 - fx) * (1 - fy)), (1, 0, fx * (1 - fy)),
+                            (0, 1, (1 - fx) * fy), (1, 1, fx * fy)):
+            xi = (x0 + dx).clamp(0, W - 1).long()
+            yi = (y0 + dy).clamp(0, H - 1).long()
+            img.index_add_(0, yi * W + xi, fl * wgt)
+        sig = fwhm_to_sigma(fwhm)
+        r = int(math.ceil(5 * sig))
+        t = torch.arange(-r, r + 1, device=device, dtype=torch.float64)
+        k = torch.exp(-t * t / (2 * sig * sig))
+        k = (k / k.sum()).float()
+        im = img.float().view(1, 1, H, W)
+        im = F.conv2d(F.pad(im, (r, r, 0, 0)), k.view(1, 1, 1, -1))
+        im = F.conv2d(F.pad(im, (0, 0, r, r)), k.view(1, 1, -1, 1))
+        return im.view(H, W) + sky
+
+    ref = torch.poisson(render(fwhm_ref), generator=g)
+    sci = torch.poisson(render(fwhm_sci), generator=g)
+    m = torch.zeros((H, W), dtype=torch.int16, device=device)
+    target = int(mask_frac * W * H)
+    covered = 0
+    rng = np.random.default_rng(int(seed))
+    while covered < target:
+        bw, bh = int(rng.integers(10, 80)), int(rng.integers(10, 80))
+        bx, by = int(rng.integers(0, max(1, W - bw))), int(rng.integers(0, max(1, H - bh)))
+        m[by:by + bh, bx:bx + bw] = MASK_BAD
+        covered += bw * bh
+    ref = ref.masked_fill(m != 0, 0.0)
+    sci = sci.masked_fill(m != 0, 0.0)
+    return dict(img=sci.contiguous(), ref=ref.contiguous(), var_img=sci.clone(),
+                var_ref=ref.clone(), mask_img=m, mask_ref=m.clone())
+
+
+def isis_prescription_sigmas(fwhm_max: float):
+    """Gaussian widths of the paper's recommended ISIS basis (Sec. 3.1): FWHM 2.9, 4.8, 8.2 px
+    scaled linearly by fwhm_max / 9, the scale clamped to [0.7, 1.2]; returned as sigmas."""
+    scale = min(1.2, max(0.7, fwhm_max / 9.0))
+    return tuple(fwhm_to_sigma(f * scale) for f in (2.9, 4.8, 8.2))
