@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--precision", default="f32x2", choices=list(PRECISION))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     return ap.parse_args()
 
 
@@ -151,27 +152,34 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- CPU oracle
 
 _ORACLE_INPUTS = None
+ORACLE_CUT = 288
 
 
-def oracle_inputs():
-    """A 288 x 288 cut-out around the centre of the full-chip workload (generated once)."""
-    global _ORACLE_INPUTS
-    if _ORACLE_INPUTS is None:
-        from paper_1901_09999_gb300 import synth
+def write_oracle_inputs(path, chip=None):
+    """Save a 288 x 288 cut-out around the centre of a full chip (generated from the workload's
+    seed unless given as the 6 host arrays sci, ref, var_sci, var_ref, mask_sci, mask_ref)."""
+    from paper_1901_09999_gb300 import synth
+    if chip is None:
         f = synth.full_chip_field(WORKLOAD["seed"])
-        n = 288
-        y0, x0 = (f.shape[0] - n) // 2, (f.shape[1] - n) // 2
-        cut = lambda a: np.ascontiguousarray(a[y0:y0 + n, x0:x0 + n])
-        _ORACLE_INPUTS = tuple(map(cut, (f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci)))
-    return _ORACLE_INPUTS
+        chip = (f.sci, f.ref, f.var_sci, f.var_ref, f.mask_sci, f.mask_ref)
+    sci, ref, var_sci, var_ref, mask_sci, mask_ref = chip
+    n = ORACLE_CUT
+    y0, x0 = (sci.shape[0] - n) // 2, (sci.shape[1] - n) // 2
+    cut = lambda a: np.ascontiguousarray(a[y0:y0 + n, x0:x0 + n])
+    np.savez(path, I1=cut(ref), I2=cut(sci), V1=cut(var_ref), V2=cut(var_sci), m1=cut(mask_ref),
+             m2=cut(mask_sci))
 
 
-def oracle_sample():
+def oracle_sample(path):
     """Time the FP64 oracle (solve + convolve + variance + mask + covariance) on the cut-out
     with the full-chip basis (S = 2, 49 terms) and a 2 x 2 stamp grid."""
+    global _ORACLE_INPUTS
     from oracle import psfm_oracle as O
     from paper_1901_09999_gb300 import synth
-    I1, I2, V1, V2, m1, m2 = oracle_inputs()
+    if _ORACLE_INPUTS is None:
+        z = np.load(path)
+        _ORACLE_INPUTS = tuple(z[k] for k in ("I1", "I2", "V1", "V2", "m1", "m2"))
+    I1, I2, V1, V2, m1, m2 = _ORACLE_INPUTS
     n = I1.shape[0]
     ob = O.Basis(WORKLOAD["basis_sigma"], WORKLOAD["degrees"], 15, 2)
     oc = O.Config(grid_nx=2, grid_ny=2, badmask=synth.BADMASK)
@@ -185,41 +193,68 @@ def oracle_sample():
     return n * n / 1e6, dt
 
 
-def run_oracle_subprocess(reps):
+def run_oracle_parallel(reps, cores, path):
+    """Run the oracle sample ``reps`` times in each of ``cores`` concurrent single-threaded
+    processes; returns (per-process [(Mpix, s)] lists, wall seconds)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "r=[bench.oracle_sample() for _ in range(%d)]; print(json.dumps(r))" % (ROOT, reps))
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                         cwd=ROOT, timeout=1800)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+            "r=[bench.oracle_sample(%r) for _ in range(%d)]; print(json.dumps(r))"
+            % (ROOT, path, reps))
+    t = time.perf_counter()
+    procs = [subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, cwd=ROOT) for _ in range(cores)]
+    res = []
+    for pr in procs:
+        out, err = pr.communicate(timeout=1800)
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    return res, time.perf_counter() - t
 
 
-def cpu_baseline(reps):
-    r = run_oracle_subprocess(reps)
-    mpix = sum(a for a, _ in r)
-    sec = sum(b for _, b in r)
-    return {"value": mpix / sec, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(r)} x 288x288 cut-out of the full-chip workload (S=2, 49 terms, "
-                      f"2x2 stamp grid), solve+convolve+variance+mask+covariance, FP64 numpy, "
-                      f"single-threaded BLAS, {sec:.1f} s"}
+def oracle_rate(res):
+    """Aggregate throughput of concurrent processes: sum of each one's Mpix / busy seconds."""
+    return sum(sum(a for a, _ in r) / sum(b for _, b in r) for r in res)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(reps, path, cores):
+    res, wall = run_oracle_parallel(reps, cores, path)
+    busy = sum(b for r in res for _, b in r)
+    return {"value": oracle_rate(res), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} x {ORACLE_CUT}x{ORACLE_CUT} centre cut-out of the first full chip per "
+                      f"process, {cores} concurrent single-threaded processes (S=2, 49 terms, 2x2 "
+                      f"stamp grid), solve+convolve+variance+mask+covariance, FP64 numpy; "
+                      f"{busy:.1f} CPU-s in {wall:.1f} s wall"}
 
 
 def reference_arm(args):
-    for _ in range(args.warmup):
-        run_oracle_subprocess(1)
-    r = run_oracle_subprocess(args.steps)
-    mpix = sum(a for a, _ in r)
-    sec = sum(b for _, b in r)
-    val = mpix / sec
+    import tempfile
+    cores = host_cores()
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "oracle_cut.npz")
+        write_oracle_inputs(path)
+        for _ in range(args.warmup):
+            run_oracle_parallel(1, cores, path)
+        res, wall = run_oracle_parallel(args.steps, cores, path)
+    val = oracle_rate(res)
+    busy = sum(b for r in res for _, b in r)
     print(json.dumps({
         "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": 0, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1000 * sec / len(r), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "impl": "reference", "config": dict(WORKLOAD, sample="288x288 cut-out per step"),
-        "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{len(r)} x 288x288 cut-outs, {sec:.1f} s"},
+        "impl": "reference",
+        "config": dict(WORKLOAD, sample=f"{ORACLE_CUT}x{ORACLE_CUT} centre cut-out per process "
+                                        f"per step, {cores} processes"),
+        "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} x {ORACLE_CUT}x{ORACLE_CUT} cut-outs in each of "
+                                   f"{cores} single-threaded processes, {busy:.1f} CPU-s"},
         "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -286,6 +321,7 @@ def main():
                     {"workload": "small_512x512_gaussian_S0_27terms"})
         workload.update(chips_per_step=len(chips),
                         seeds=[WORKLOAD["seed"] + i for i in range(len(chips))])
+    oracle_chip = host_chips[0] if (host_chips and not args.small) else None
     del host_chips
     px_per_step = sum(c["img"].numel() for c in chips)
     stream = torch.cuda.Stream()
@@ -366,6 +402,37 @@ def main():
                                     "ms": var_ms / var_n}}
     stages = {k: v[0] / v[2] for k, v in prof.items()}
 
+    # the plain FP32 GPU path on the same chips: one unbatched psfm_subtract per chip with FP32
+    # stamp design and Gram, no streams or graph
+    plain = None
+    if not args.no_plain and not args.single:
+        _, cfg32 = chip_specs("fp32", args.small)
+        outs32 = [dict(out=P._like(c["img"]), out_var=P._like(c["img"]),
+                       out_mask=P._like(c["mask_img"])) for c in chips]
+        ws32 = torch.empty(max(P.psfm_workspace_size(
+            P.OP_SUBTRACT, P.psfm_shape(c["img"].shape[1], c["img"].shape[0], c["img"].stride(0)),
+            b, cfg32) for c, b in zip(chips, bases)), dtype=torch.uint8, device=dev)
+
+        def plain_pass():
+            for c, b, o in zip(chips, bases, outs32):
+                P.psfm_subtract(c["img"], c["ref"], c["var_img"], c["var_ref"], c["mask_img"],
+                                c["mask_ref"], b, cfg32, workspace=ws32, stream=stream, **o)
+
+        with torch.cuda.stream(stream):
+            plain_pass()
+            torch.cuda.synchronize()
+            n3 = max(1, min(3, args.steps))
+            e0.record(stream)
+            for _ in range(n3):
+                plain_pass()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / n3
+        plain = {"value": px_per_step / 1e6 / (pms / 1e3), "unit": "Mpix/s", "ms_per_step": pms,
+                 "what": "same chips, one unbatched psfm_subtract each, FP32 stamp design+Gram",
+                 "batched_speedup": value / (px_per_step / 1e6 / (pms / 1e3))}
+        del outs32, ws32
+
     e2e = None
     if not args.no_e2e and not args.exposure:
         keys = ("img", "ref", "var_img", "var_ref", "mask_img", "mask_ref")
@@ -406,8 +473,12 @@ def main():
         return 0
     cpu = None
     if not args.no_cpu_baseline:
+        import tempfile
         try:
-            cpu = cpu_baseline(8)
+            with tempfile.TemporaryDirectory() as d:
+                path = os.path.join(d, "oracle_cut.npz")
+                write_oracle_inputs(path, oracle_chip)
+                cpu = cpu_baseline(4, path, host_cores())
         except Exception as e:  # the oracle is a reported baseline only
             cpu = {"error": str(e)[-300:]}
     sol_info = None
@@ -425,6 +496,7 @@ def main():
                                  f"{len(chips)} chips on {args.streams} streams, CUDA graph replay"),
                        parallelism=f"replicas x{world}"),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "plain_fp32": plain,
         "clocks": clk.summary(), "single_chip_stages_ms": stages, "solutions": sol_info,
     }
     print(json.dumps(line))

@@ -247,9 +247,10 @@ psfm_status psfm_stack(int32_t n, const float* const* imgs, const float* const* 
  * counterpart in the paper).  A batch is n chips, each with its own shape, basis (size, degrees,
  * spatial order) and buffers; the configuration is shared.  psfm_batch_create lays out one
  * caller workspace (psfm_batch_workspace_size bytes, 256-byte aligned) for all chips, uploads
- * their tables once and creates n_streams CUDA streams (1..32) on which chips run
- * concurrently.  The batch object is host memory owned by the library until
- * psfm_batch_destroy.
+ * their tables once and creates n_streams (1..32) pairs of CUDA streams on which chips run
+ * concurrently: chip i is solved on the high-priority stream of pair i % n_streams and its
+ * image, variance, mask and pseudo-matrix passes then run on that pair's low-priority stream.
+ * The batch object is host memory owned by the library until psfm_batch_destroy.
  * psfm_batch_subtract enqueues every chip's psfm_subtract work (extractor, rejection loop,
  * image, variance, mask, pseudo-matrix of width 2w-1 when cov_outs[i] is set) without any host
  * synchronisation.  On a non-default stream the first call is captured into a CUDA graph and

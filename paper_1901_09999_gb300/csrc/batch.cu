@@ -4,6 +4,12 @@
 // CUDA graph on the first call so that later calls with the same buffers replay it with a
 // single launch.
 //
+// Each stream slot is a pair: solves run on a high-priority stream and the image, variance,
+// mask and pseudo-matrix passes on a low-priority one, so that the small, latency-bound solve
+// kernels get SMs as soon as any convolution CTA retires instead of queueing behind whole
+// convolution grids.  The graph is instantiated with per-node priorities, which capture
+// takes from the streams.
+//
 // Per chip the work is exactly psfm_subtract's (extractor, rejection loop, r_bad, image,
 // variance, mask, pseudo-matrix), with the solution kept on the device; the per-chip tables
 // are uploaded once, at creation, and every execution resets only the device state block.
@@ -20,8 +26,9 @@ struct psfm_batch {
   std::vector<psfm::Head> heads;
   std::vector<psfm::ApplyBuffers> ab;
   std::vector<psfm::SolveBuffers> sb;
-  std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> done;
+  std::vector<cudaStream_t> streams;     // solve streams (high priority)
+  std::vector<cudaStream_t> streams_lo;  // apply streams (low priority)
+  std::vector<cudaEvent_t> done, done_lo, solved;
   cudaEvent_t fork = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -67,19 +74,22 @@ size_t layout(int n, const psfm_shape* shapes, const psfm_basis_spec* bases,
   return ws.used;
 }
 
-psfm_status enqueue_chip(psfm_batch* b, int i, cudaStream_t s, const float* img, const float* ref,
-                         const float* var_img, const float* var_ref, const uint16_t* mask_img,
-                         const uint16_t* mask_ref, float* diff, float* diff_var,
-                         uint16_t* diff_mask, double* cov_out) {
+psfm_status enqueue_chip(psfm_batch* b, int i, cudaStream_t s, cudaStream_t s_lo,
+                         const float* img, const float* ref, const float* var_img,
+                         const float* var_ref, const uint16_t* mask_img, const uint16_t* mask_ref,
+                         float* diff, float* diff_var, uint16_t* diff_mask, double* cov_out) {
   const Plan& p = b->plans[i];
   const Head& h = b->heads[i];
   if (cudaMemsetAsync(h.st, 0, sizeof(DevState), s) != cudaSuccess) return PSFM_ERR_CUDA;
   psfm_status st = run_solve(p, b->ab[i].tab, h.st, h.dsol, b->sb[i], img, ref, var_img, var_ref,
                              mask_img, mask_ref, nullptr, s);
   if (st != PSFM_OK) return st;
+  if (cudaEventRecord(b->solved[i], s) != cudaSuccess ||
+      cudaStreamWaitEvent(s_lo, b->solved[i], 0) != cudaSuccess)
+    return PSFM_ERR_CUDA;
   const int cw = 2 * p.w - 1;
   return run_apply(p, h, b->ab[i], ref, var_ref, mask_ref, img, var_img, mask_img, nullptr, 1,
-                   nullptr, 1, diff, diff_var, diff_mask, cov_out, cw, cov_out != nullptr, s);
+                   nullptr, 1, diff, diff_var, diff_mask, cov_out, cw, cov_out != nullptr, s_lo);
 }
 
 }  // namespace
@@ -120,16 +130,35 @@ psfm_status psfm_batch_create(int32_t n, const psfm_shape* shapes, const psfm_ba
     delete b;
     return PSFM_ERR_CUDA;
   }
+  int prio_lo = 0, prio_hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+    psfm_batch_destroy(b);
+    return PSFM_ERR_CUDA;
+  }
   for (int k = 0; k < n_streams; ++k) {
-    cudaStream_t s;
-    cudaEvent_t e;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    cudaStream_t s = nullptr, s_lo = nullptr;
+    cudaEvent_t e = nullptr, e_lo = nullptr;
+    const bool ok =
+        cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
+        cudaStreamCreateWithPriority(&s_lo, cudaStreamNonBlocking, prio_lo) == cudaSuccess &&
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&e_lo, cudaEventDisableTiming) == cudaSuccess;
+    if (s) b->streams.push_back(s);
+    if (s_lo) b->streams_lo.push_back(s_lo);
+    if (e) b->done.push_back(e);
+    if (e_lo) b->done_lo.push_back(e_lo);
+    if (!ok) {
       psfm_batch_destroy(b);
       return PSFM_ERR_CUDA;
     }
-    b->streams.push_back(s);
-    b->done.push_back(e);
+  }
+  for (int i = 0; i < n; ++i) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      psfm_batch_destroy(b);
+      return PSFM_ERR_CUDA;
+    }
+    b->solved.push_back(e);
   }
   *out = b;
   return PSFM_OK;
@@ -140,7 +169,10 @@ void psfm_batch_destroy(psfm_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (auto s : b->streams) cudaStreamDestroy(s);
+  for (auto s : b->streams_lo) cudaStreamDestroy(s);
   for (auto e : b->done) cudaEventDestroy(e);
+  for (auto e : b->done_lo) cudaEventDestroy(e);
+  for (auto e : b->solved) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   delete b;
 }
@@ -182,14 +214,20 @@ psfm_status psfm_batch_subtract(psfm_batch* b, const float* const* imgs, const f
   if (cudaEventRecord(b->fork, origin) != cudaSuccess) st = PSFM_ERR_CUDA;
   const int K = (int)b->streams.size();
   for (int k = 0; k < K && st == PSFM_OK; ++k)
-    if (cudaStreamWaitEvent(b->streams[k], b->fork, 0) != cudaSuccess) st = PSFM_ERR_CUDA;
+    if (cudaStreamWaitEvent(b->streams[k], b->fork, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(b->streams_lo[k], b->fork, 0) != cudaSuccess)
+      st = PSFM_ERR_CUDA;
   for (int i = 0; i < n && st == PSFM_OK; ++i)
-    st = enqueue_chip(b, i, b->streams[i % K], imgs[i], refs[i], var_imgs[i], var_refs[i],
-                      mask_imgs[i], mask_refs[i], diffs[i], diff_vars ? diff_vars[i] : nullptr,
-                      diff_masks ? diff_masks[i] : nullptr, cov_outs ? cov_outs[i] : nullptr);
+    st = enqueue_chip(b, i, b->streams[i % K], b->streams_lo[i % K], imgs[i], refs[i],
+                      var_imgs[i], var_refs[i], mask_imgs[i], mask_refs[i], diffs[i],
+                      diff_vars ? diff_vars[i] : nullptr, diff_masks ? diff_masks[i] : nullptr,
+                      cov_outs ? cov_outs[i] : nullptr);
   for (int k = 0; k < K; ++k) {
-    if (cudaEventRecord(b->done[k], b->streams[k]) != cudaSuccess) st = PSFM_ERR_CUDA;
-    if (cudaStreamWaitEvent(origin, b->done[k], 0) != cudaSuccess) st = PSFM_ERR_CUDA;
+    if (cudaEventRecord(b->done[k], b->streams[k]) != cudaSuccess ||
+        cudaEventRecord(b->done_lo[k], b->streams_lo[k]) != cudaSuccess ||
+        cudaStreamWaitEvent(origin, b->done[k], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(origin, b->done_lo[k], 0) != cudaSuccess)
+      st = PSFM_ERR_CUDA;
   }
   b->kernels_per_exec = psfm_launch_count() - l0;
   if (!capture) return st;
@@ -200,7 +238,7 @@ psfm_status psfm_batch_subtract(psfm_batch* b, const float* const* imgs, const f
     return st != PSFM_OK ? st : PSFM_ERR_CUDA;
   }
   cudaGraphExec_t ex = nullptr;
-  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+  if (cudaGraphInstantiate(&ex, g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
     cudaGraphDestroy(g);
     return PSFM_ERR_CUDA;
   }

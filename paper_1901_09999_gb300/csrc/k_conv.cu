@@ -45,27 +45,39 @@ __device__ __forceinline__ int spatial_index(int l, int m, int S) {
   return l * (S + 1) - (l * (l - 1)) / 2 + m;
 }
 
-// Polynomial sum_m yt^m (sum_l c[m][l] xt^l) with c laid out [m][l], (S+1)^2 entries.
-__device__ __forceinline__ void xpoly(const float* c, int S, float xt, float out[4]) {
-  const int S1 = S + 1;
+// Adds c_k(x, y_i) acc[i] to out[i] for the 8 rows of a thread, with the term's coefficient
+// polynomial c_k = sum_{l+m<=SS} a[m][l] xt^l yt^m evaluated by Horner (x first, then y).
+template <int SS>
+__device__ __forceinline__ void add_term(const float* a, float xt, const float yt[8],
+                                         const float acc[8], float out[8]) {
+  constexpr int S1 = SS + 1;
+  float cm[SS + 1];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    float acc = 0.f;
-    if (m <= S) {
+  for (int m = 0; m <= SS; ++m) {
+    float t = 0.f;
 #pragma unroll
-      for (int l = 3; l >= 0; --l)
-        if (l + m <= S) acc = fmaf(acc, xt, c[m * S1 + l]);
-    }
-    out[m] = acc;
+    for (int l = SS - m; l >= 0; --l) t = fmaf(t, xt, a[m * S1 + l]);
+    cm[m] = t;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    float c = cm[SS];
+#pragma unroll
+    for (int m = SS - 1; m >= 0; --m) c = fmaf(c, yt[i], cm[m]);
+    out[i] = fmaf(c, acc[i], out[i]);
   }
 }
 
-__device__ __forceinline__ float ypoly(const float cm[4], int S, float yt) {
-  float acc = 0.f;
-#pragma unroll
-  for (int m = 3; m >= 0; --m)
-    if (m <= S) acc = fmaf(acc, yt, cm[m]);
-  return acc;
+// The spatial order is uniform over the launch: one branch per term selects the unrolled
+// polynomial of that order.
+__device__ __forceinline__ void add_term_s(int S, const float* a, float xt, const float yt[8],
+                                           const float acc[8], float out[8]) {
+  switch (S) {
+    case 0: add_term<0>(a, xt, yt, acc, out); break;
+    case 1: add_term<1>(a, xt, yt, acc, out); break;
+    case 2: add_term<2>(a, xt, yt, acc, out); break;
+    default: add_term<3>(a, xt, yt, acc, out); break;
+  }
 }
 
 template <int HW>
@@ -187,23 +199,21 @@ __global__ void __launch_bounds__(256, 2) k_conv_image(ConvParams P) {
             }
           }
         }
-        float cm[4];
-        xpoly(alpha + (kgp + q) * S1 * S1, S, xt, cm);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) out[i] = fmaf(ypoly(cm, S, yt[i]), acc[i], out[i]);
+        add_term_s(S, alpha + (kgp + q) * S1 * S1, xt, yt, acc, out);
       }
     }
     __syncthreads();
   }
 
-  float cb[4];
-  xpoly(beta, S, xt, cb);
+  float rc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) rc[i] = Rs[(wi * 8 + i + HW) * RS + lane + HW];
+  add_term_s(S, beta, xt, yt, rc, out);
   const float d0 = (float)P.dsol[1];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int gy = y0 + wi * 8 + i;
-    const float r = Rs[(wi * 8 + i + HW) * RS + lane + HW];
-    float o = fmaf(ypoly(cb, S, yt[i]), r, out[i]) + d0;
+    float o = out[i] + d0;
     if (gx < P.g.W && gy < P.g.H) {
       const int64_t off = (int64_t)gy * P.g.pitch + gx;
       if (P.img) o = P.img[off] - o;

@@ -28,6 +28,16 @@ namespace {
 
 __device__ __forceinline__ void raise_error(DevState* st, int code) { atomicCAS(&st->error, 0, code); }
 
+// Whether a block skips its work because the loop has finished or an error was raised, by an
+// earlier kernel or by another block of this launch.  Read once by one thread so that the
+// decision is uniform across the block's barriers.
+__device__ __forceinline__ bool block_skip(const DevState* st) {
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = (st->error || st->done) ? 1 : 0;
+  __syncthreads();
+  return s_skip != 0;
+}
+
 __device__ __forceinline__ bool region_active(const int32_t* ptr, const int32_t* cand, int r,
                                               int max_cand, int* cx, int* cy) {
   const int j = ptr[r];
@@ -60,6 +70,8 @@ struct StampParams {
   void* C;  // [nreg][Nb][P] of T (float or double, by precision mode)
   double* G;
   double* Gt;
+  double* Gpart;        // [nreg][kGramSplit][Nc][Nc] partial Grams (double-float mode)
+  int32_t* gram_count;  // [nreg] partials finished, reset by the block that combines them
   double* footsum;
   DevState* st;
 };
@@ -76,7 +88,7 @@ __global__ void __launch_bounds__(256) k_stamp_design(StampParams P) {
   extern __shared__ __align__(16) unsigned char sh_raw[];
   T* sh = reinterpret_cast<T*>(sh_raw);
   const int r = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
-  if (P.st->error || P.st->done) return;
+  if (block_skip(P.st)) return;
   int cx, cy;
   if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return;
   if (P.have[r] == P.ptr[r]) return;
@@ -215,17 +227,21 @@ __device__ __forceinline__ df df_norm(df a) {
 
 __device__ __forceinline__ double df_to_d(df a) { return (double)a.hi + (double)a.lo; }
 
-// grid (nreg, ng): basis-convolved footprint of one Gaussian's terms in double-float.  The
-// reference pixels are exact FP32; the 1-D factors are split into FP32 pairs.
+// grid (nreg, N_H): the basis-convolved footprint of the terms of one horizontal plane (g, p),
+// that is B_{g,p,q} (x) R for q = 0..d_g - p, in double-float.  The reference pixels are exact
+// FP32; the 1-D factors are split into FP32 pairs.  One block per plane spreads a stamp over
+// N_H blocks, so a handful of replaced stamps still fill many SMs.
 __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
   extern __shared__ __align__(16) unsigned char sh_raw[];
-  const int r = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
-  if (P.st->error || P.st->done) return;
+  const int r = blockIdx.x, pl = blockIdx.y, tid = threadIdx.x;
+  if (block_skip(P.st)) return;
   int cx, cy;
   if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return;
   if (P.have[r] == P.ptr[r]) return;
+  int g = 0;
+  while (g + 1 < P.b.ng && pl >= P.b.plane_base[g + 1]) ++g;
   const int h = P.b.h, W = P.b.w, foot = P.foot, sw = P.sw;
-  const int dg = P.b.deg[g], pb = P.b.plane_base[g];
+  const int dg = P.b.deg[g], pb = P.b.plane_base[g], p = pl - pb;
   float* F = reinterpret_cast<float*>(sh_raw);   // foot x foot
   float* Hh = F + foot * foot;                    // foot x sw
   float* Hl = Hh + foot * sw;
@@ -247,7 +263,7 @@ __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
       const int64_t o = (int64_t)gy * P.g.pitch + gx;
       const uint16_t a = P.m1[o] & P.badmask, b = P.m2[o] & P.badmask;
       if (!a) v = P.i1[o];
-      if (g == 0 && !a && !b) {
+      if (pl == 0 && !a && !b) {
         f1 += v;
         f2 += P.i2[o];
         nf += 1.0;
@@ -255,7 +271,7 @@ __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
     }
     F[i] = v;
   }
-  if (g == 0) {
+  if (pl == 0) {
     __shared__ double red[3][8];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -282,48 +298,51 @@ __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
     }
   }
   __syncthreads();
-  for (int p = 0; p <= dg; ++p) {
+  {
     const float* ph = wh + p * W;
-    const float* pl = wl + p * W;
+    const float* pw = wl + p * W;
     for (int i = tid; i < foot * sw; i += 256) {
       const int rr = i / sw, px = i - rr * sw;
       const float* src = F + rr * foot + px + 2 * h;
       df a = {0.f, 0.f};
-      for (int t = 0; t < W; ++t) df_fma_f(a, src[-t], df{ph[t], pl[t]});
+      for (int t = 0; t < W; ++t) df_fma_f(a, src[-t], df{ph[t], pw[t]});
       a = df_norm(a);
       Hh[i] = a.hi;
       Hl[i] = a.lo;
     }
-    __syncthreads();
-    const int kgp = P.b.kbase[g] + p * (dg + 1) - (p * (p - 1)) / 2;
-    for (int q = 0; q <= dg - p; ++q) {
-      const float* qh = wh + q * W;
-      const float* ql = wl + q * W;
-      float2* out = reinterpret_cast<float2*>(P.C) + ((int64_t)r * P.b.Nb + kgp + q) * P.P;
-      for (int i = tid; i < P.P; i += 256) {
-        const int py = i / sw, px = i - py * sw;
-        const int base = (py + 2 * h) * sw + px;
-        df a = {0.f, 0.f};
-        for (int t = 0; t < W; ++t)
-          df_fma(a, df{Hh[base - t * sw], Hl[base - t * sw]}, df{qh[t], ql[t]});
-        a = df_norm(a);
-        out[i] = make_float2(a.hi, a.lo);
-      }
+  }
+  __syncthreads();
+  const int kgp = P.b.kbase[g] + p * (dg + 1) - (p * (p - 1)) / 2;
+  for (int q = 0; q <= dg - p; ++q) {
+    const float* qh = wh + q * W;
+    const float* ql = wl + q * W;
+    float2* out = reinterpret_cast<float2*>(P.C) + ((int64_t)r * P.b.Nb + kgp + q) * P.P;
+    for (int i = tid; i < P.P; i += 256) {
+      const int py = i / sw, px = i - py * sw;
+      const int base = (py + 2 * h) * sw + px;
+      df a = {0.f, 0.f};
+      for (int t = 0; t < W; ++t)
+        df_fma(a, df{Hh[base - t * sw], Hl[base - t * sw]}, df{qh[t], ql[t]});
+      a = df_norm(a);
+      out[i] = make_float2(a.hi, a.lo);
     }
-    __syncthreads();
   }
 }
 
-// grid (nreg), 512 threads: weighted Gram of the augmented block in double-float.  Each
-// thread owns a 4 x 4 block of the Gram and one of `nsl` interleaved pixel slices of every
-// 64-pixel chunk; the weighted columns w * A are formed once per chunk in shared memory.
-// Chunk partial sums go to per-slice FP64 accumulators, reduced in a fixed order at the end.
+// grid (nreg, kGramSplit), 512 threads: weighted Gram of the augmented block in double-float.
+// Block (r, j) takes the 64-pixel chunks j, j + kGramSplit, ... of stamp r.  Each thread owns
+// a 4 x 4 block of the Gram and one of `nsl` interleaved pixel slices of every chunk; the
+// weighted columns w * A are formed once per chunk in shared memory.  Chunk partial sums go
+// to per-slice double-float accumulators, then each block writes its FP64 partial Gram; the
+// last block of a stamp to finish (counted with an atomic) adds the partials in split order,
+// so the result does not depend on which block finishes last, and forms the transformed Gram.
 constexpr int kGramChunk = 64;
 constexpr int kGramThreads = 512;
 __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
   extern __shared__ double shd[];
-  const int r = blockIdx.x, tid = threadIdx.x;
-  if (P.st->error || P.st->done) return;
+  __shared__ int s_last;
+  const int r = blockIdx.x, split = blockIdx.y, tid = threadIdx.x;
+  if (block_skip(P.st)) return;
   int cx, cy;
   if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return;
   if (P.have[r] == P.ptr[r]) return;
@@ -340,7 +359,7 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
   float* wl = wh + kGramChunk;
   for (int i = tid; i < nsl * npair * 16; i += kGramThreads) acc[i] = make_float2(0.f, 0.f);
   const float2* Cr = reinterpret_cast<const float2*>(P.C) + (int64_t)r * Nb * P.P;
-  for (int base = 0; base < P.P; base += kGramChunk) {
+  for (int base = split * kGramChunk; base < P.P; base += kGramSplit * kGramChunk) {
     __syncthreads();
     if (tid < kGramChunk) {
       const int pix = base + tid;
@@ -422,7 +441,7 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
     }
   }
   __syncthreads();
-  double* Gr = P.G + (int64_t)r * Nc * Nc;
+  double* Gp = P.Gpart + ((int64_t)r * kGramSplit + split) * Nc * Nc;
   for (int q = tid; q < npair * 16; q += kGramThreads) {
     const int pq = q / 16, e = (q / 4) % 4, f = q % 4;
     double v = 0.0;
@@ -438,9 +457,23 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
     const int bj2 = bi2 + rem2;
     const int i = bi2 * 4 + e, j = bj2 * 4 + f;
     if (i < Nc && j < Nc) {
-      Gr[i * Nc + j] = v;
-      Gr[j * Nc + i] = v;
+      Gp[i * Nc + j] = v;
+      Gp[j * Nc + i] = v;
     }
+  }
+  // publish the partial, then let the last block of this stamp combine them
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&P.gram_count[r], 1) == kGramSplit - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double* Gr = P.G + (int64_t)r * Nc * Nc;
+  const double* Gp0 = P.Gpart + (int64_t)r * kGramSplit * Nc * Nc;
+  for (int q = tid; q < Nc * Nc; q += kGramThreads) {
+    double v = 0.0;
+    for (int k = 0; k < kGramSplit; ++k) v += __ldcg(Gp0 + (int64_t)k * Nc * Nc + q);
+    Gr[q] = v;
   }
   __syncthreads();
   double* Gtr = P.Gt + (int64_t)r * Nc * Nc;
@@ -457,6 +490,7 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
   }
   __syncthreads();
   if (tid == 0) {
+    P.gram_count[r] = 0;
     P.have[r] = P.ptr[r];
     P.fresh[r] = 1;
   }
@@ -468,7 +502,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_stamp_gram(StampParams P) {
   extern __shared__ double shd[];
   const int r = blockIdx.x, tid = threadIdx.x;
-  if (P.st->error || P.st->done) return;
+  if (block_skip(P.st)) return;
   int cx, cy;
   if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return;
   if (P.have[r] == P.ptr[r]) return;
@@ -1235,7 +1269,7 @@ __global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
   __shared__ double red[2][8];
   __shared__ double s_delta;
   const int r = blockIdx.x, tid = threadIdx.x;
-  if (P.st->error || P.st->done) return;
+  if (block_skip(P.st)) return;
   int cx, cy;
   if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return;
   const int Nb = P.b.Nb, Ns = P.b.Ns;
@@ -1307,6 +1341,9 @@ __global__ void __launch_bounds__(1024) k_reject(int nreg, int max_cand, int max
   __shared__ double sh[33];
   __shared__ int s_finish;
   if (st->error || st->done) return;
+  // every thread reads the iteration count before the first barrier; thread 0 advances it
+  // after the last one
+  const int it = st->iter;
   double n = 0.0, sum = 0.0;
   for (int r = threadIdx.x; r < nreg; r += blockDim.x) {
     fresh[r] = 0;
@@ -1328,7 +1365,6 @@ __global__ void __launch_bounds__(1024) k_reject(int nreg, int max_cand, int max
   }
   ss = block_sum(ss, sh);
   const double sd = sqrt(ss / n);
-  const int it = st->iter;
   bool finish = it == max_iter - 1;
   double nrej = 0.0;
   if (!finish) {
@@ -1393,6 +1429,8 @@ void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b) {
   b.C = ws.take<double>((size_t)p.nreg * p.Nb * p.P);
   b.G = ws.take<double>((size_t)p.nreg * p.Nc * p.Nc);
   b.Gt = ws.take<double>((size_t)p.nreg * p.Nc * p.Nc);
+  b.Gpart = ws.take<double>((size_t)p.nreg * kGramSplit * p.Nc * p.Nc);
+  b.gram_count = ws.take<int32_t>(p.nreg);
   b.foot = ws.take<double>((size_t)p.nreg * 4);
   b.chi2 = ws.take<double>(p.nreg);
   b.M = ws.take<double>((size_t)p.Nsys * p.Nsys);
@@ -1450,6 +1488,8 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   sp.C = b.C;
   sp.G = b.G;
   sp.Gt = b.Gt;
+  sp.Gpart = b.Gpart;
+  sp.gram_count = b.gram_count;
   sp.footsum = b.foot;
   sp.st = st;
 
@@ -1524,12 +1564,14 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   if (cudaMemsetAsync(b.Gt, 0, sizeof(double) * (size_t)p.nreg * p.Nc * p.Nc, s) != cudaSuccess ||
       cudaMemsetAsync(b.M, 0, sizeof(double) * (size_t)p.Nsys * p.Nsys, s) != cudaSuccess ||
       cudaMemsetAsync(b.fresh, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess ||
-      cudaMemsetAsync(b.removed, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess)
+      cudaMemsetAsync(b.removed, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess ||
+      cudaMemsetAsync(b.gram_count, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess)
     return PSFM_ERR_CUDA;
+  const bool dfm = prec == PSFM_PREC_F32X2;
   for (int it = 0; it < p.cfg.max_iter; ++it) {
     prof_begin("stamps", s);
-    design<<<dim3(p.nreg, p.ng), 256, sm_design, s>>>(sp);
-    gram<<<p.nreg, prec == PSFM_PREC_F32X2 ? kGramThreads : 256, sm_gram, s>>>(sp);
+    design<<<dim3(p.nreg, dfm ? p.NH : p.ng), 256, sm_design, s>>>(sp);
+    gram<<<dim3(p.nreg, dfm ? kGramSplit : 1), dfm ? kGramThreads : 256, sm_gram, s>>>(sp);
     prof_end("stamps", s, 2);
     prof_begin("system", s);
     k_norm<<<1, 1024, 0, s>>>(sy);

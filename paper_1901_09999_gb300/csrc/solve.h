@@ -6,6 +6,9 @@
 
 namespace psfm {
 
+// Blocks that share one stamp's Gram (pixel chunks split between them).
+constexpr int kGramSplit = 4;
+
 struct SolveBuffers {
   // extractor (Sec. 3.3)
   uint32_t* hist;     // [3][2048] radix-select histograms of the detection image
@@ -23,6 +26,8 @@ struct SolveBuffers {
   void* C;       // [nreg][Nb][P] basis-convolved masked reference at the stamp pixels (float or double)
   double* G;     // [nreg][Nc][Nc] weighted Gram of (basis columns, R, 1, I2)
   double* Gt;    // [nreg][Nc][Nc] the same with basis columns psi_k C_k - s_k R
+  double* Gpart;        // [nreg][kGramSplit][Nc][Nc] partial Grams over pixel chunks
+  int32_t* gram_count;  // [nreg] partial Grams finished for the stamp being built
   double* foot;  // [nreg][4] footprint sums F1, F2, n, unused
   double* chi2;  // [nreg] chi^2 of the active stamp
   // normal equations

@@ -328,13 +328,15 @@ def chip_field(chip: dict, n_stars_per_mpix: float = 100.0, sky: float = 500.0) 
 
 
 def skycell_warps(seed: int = 5, n_warps: int = 16, size: int = 6000, n_stars: int = 6000,
-                  sky: float = 500.0):
+                  sky: float = 500.0, gap_range=(300, 700), block_range=(50, 600),
+                  masked_range=(0.05, 0.40)):
     """Inputs of the stacking workload: warps of one skycell with uneven coverage.
 
     Returns (warps, sources): a list of dicts with image, variance, mask and the warp's PSF
     FWHM, and the (x, y, flux) source list shared by all warps.  Each warp's PSF is a
     Gaussian-core Moffat mixture with FWHM in [3.5, 7]; masked fraction 5-40% from chip-gap
-    bands and defect blocks.
+    bands and defect blocks (``gap_range``, ``block_range`` and ``masked_range`` shrink them
+    for small test versions).
     """
     rng = np.random.default_rng(seed)
     xs, ys = rng.uniform(0, size - 1, n_stars), rng.uniform(0, size - 1, n_stars)
@@ -350,14 +352,14 @@ def skycell_warps(seed: int = 5, n_warps: int = 16, size: int = 6000, n_stars: i
                 add_moffat(img, x, y, f * frac_moffat, fw, 3.0)
         img = rng.poisson(img).astype(np.float64)
         m = np.zeros((size, size), np.uint16)
-        target = float(rng.uniform(0.05, 0.40))
+        target = float(rng.uniform(*masked_range))
         # chip-gap bands
-        gap = int(rng.integers(300, 700))
+        gap = int(rng.integers(*gap_range))
         off = int(rng.integers(0, gap))
         for g0 in range(off, size, gap):
             m[:, g0:g0 + 12] |= MASK_BAD
         while float(np.mean(m != 0)) < target:
-            bw, bh = int(rng.integers(50, 600)), int(rng.integers(50, 600))
+            bw, bh = int(rng.integers(*block_range)), int(rng.integers(*block_range))
             bx, by = int(rng.integers(0, size - bw)), int(rng.integers(0, size - bh))
             m[by:by + bh, bx:bx + bw] |= MASK_BAD
         img[m != 0] = 0.0
