@@ -33,9 +33,13 @@ WORKLOAD = dict(
     workload="full_chip_4846x4868_moffat_S2_49terms_300stamps",
     W=4846, H=4868, basis_sigma=(0.8, 1.6, 3.2), degrees=(6, 4, 2), kernel=31,
     spatial_order=2, stamps=300, grid=(15, 20), seed=2)
+# DRAM bytes (read + write) of one k_conv_image launch on the full-chip workload, from the ncu
+# capture summarised in profiles/k_conv_image_k_variance_full_chip.md; valid for the kernel
+# as captured there.
+CONV_TRAFFIC_FULL_CHIP = 234.80192e6 + 75.25248e6
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-PRECISION = {"fp64": 0, "fp32": 1, "f32x2": 4}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3, "f32x2": 4}
 
 
 def parse():
@@ -50,6 +54,7 @@ def parse():
     ap.add_argument("--exposure", action="store_true",
                     help="60 uneven chips of one exposure (GPU-generated inputs)")
     ap.add_argument("--small", action="store_true", help="512x512 plain-method workload")
+    ap.add_argument("--stack", action="store_true", help="16-warp 6000x6000 stacking workload")
     ap.add_argument("--precision", default="f32x2", choices=list(PRECISION))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -277,6 +282,83 @@ def exposure_chips(dev, seed=4, n=60, precision="f32x2"):
     return chips, bases, cfg
 
 
+STACK = dict(workload="stack_16_warps_6000x6000_target_fwhm7.5_S1", warps=16, size=6000,
+             sources=6000, target_fwhm=7.5, spatial_order=1, grid=(12, 12), seed=5)
+
+
+def run_stack(args, world, local):
+    """Config 5: PSF-homogenised stack of 16 warps of one 6000 x 6000 skycell (psfm_stack: each
+    warp matched to a Gaussian target of FWHM 7.5 px, convolved with its variance, mask and
+    pseudo-matrix, then the inverse-variance weighted coadd).  Mpix/s counts input pixels."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1901_09999_gb300 import build
+    build.build()
+    from paper_1901_09999_gb300 import psfm as P
+    from paper_1901_09999_gb300 import synth
+    n, size = STACK["warps"], STACK["size"]
+    warps, src = synth.torch_skycell_warps(STACK["seed"], n, size, STACK["sources"], dev)
+    sig = synth.isis_prescription_sigmas(STACK["target_fwhm"])
+    h = int(np.ceil(4.7 * sig[-1]))
+    b = P.basis_spec(sig, (6, 4, 2), h, STACK["spatial_order"])
+    cfg = P.config(badmask=synth.BADMASK, grid_nx=STACK["grid"][0], grid_ny=STACK["grid"][1],
+                   precision=PRECISION[args.precision])
+    imgs = [w["image"] for w in warps]
+    vars_ = [w["var"] for w in warps]
+    masks = [w["mask"] for w in warps]
+    stream = torch.cuda.Stream()
+    shape = P.psfm_shape(size, size, size)
+    ws = torch.empty(P.psfm_workspace_size(P.OP_STACK, shape, b, cfg, len(src)), dtype=torch.uint8,
+                     device=dev)
+
+    def step():
+        return P.psfm_stack(imgs, vars_, masks, [src] * n, STACK["target_fwhm"], [b] * n, cfg,
+                            workspace=ws, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            out = step()
+        torch.cuda.synchronize()
+        l0 = P.psfm_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                out = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = P.psfm_launch_count() - l0
+        P.psfm_profile_enable(True)
+        step()
+        torch.cuda.synchronize()
+        prof = P.psfm_profile_read()
+        P.psfm_profile_enable(False)
+    mpix_in = n * size * size / 1e6
+    f_img, _ = flops_per_pixel(b)
+    conv_ms, conv_n, _ = prof.get("conv_image", (float("nan"), 1, 1))
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    achieved = size * size * f_img / (conv_ms / conv_n / 1e3) / 1e12
+    cnt = out[3].cpu().numpy()
+    print(json.dumps({
+        "metric": METRIC, "value": mpix_in * args.steps / (ms / 1e3), "unit": "Mpix/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(STACK, h=h, basis_sigma=list(sig), degrees=[6, 4, 2],
+                       precision=args.precision, counts="input pixels",
+                       output_mpix=size * size / 1e6,
+                       coverage_mean=float(cnt.mean()), l2="inputs larger than L2"),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_conv_image",
+                     "kernel_ms": conv_ms / conv_n},
+        "gpu_launches": launches, "clocks": clk.summary(),
+        "stages_ms": {k: v[0] for k, v in prof.items()}}))
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -286,6 +368,9 @@ def main():
         if rank == 0:
             reference_arm(args)
         return 0
+
+    if args.stack:
+        return run_stack(args, world, local)
 
     nchips = 1 if args.single else args.chips
     host_chips = None
@@ -393,7 +478,9 @@ def main():
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     achieved = npx0 * f_img / (conv_ms / conv_n / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": (CONV_TRAFFIC_FULL_CHIP if (not args.small and not args.exposure)
+                            else None),
                 "kernel": "k_conv_image", "kernel_ms": conv_ms / conv_n,
                 "algorithmic_flop_per_px": f_img,
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived; an "

@@ -95,8 +95,9 @@ typedef struct {
  * always assembled and solved in FP64; the image, variance and mask passes are FP32). */
 #define PSFM_PREC_FP64 0     /* design and Gram in FP64 (slow on this GPU's FP64 pipes) */
 #define PSFM_PREC_FP32 1     /* FP32 design and products, FP64 sums over 32-pixel chunks */
-#define PSFM_PREC_TF32 2     /* reserved: Gram on tensor cores in TF32 */
-#define PSFM_PREC_BF16X3 3   /* reserved: Gram on tensor cores, 3 x BF16 split products */
+#define PSFM_PREC_TF32 2     /* FP32 design; Gram on the tensor cores, TF32 products, FP32 sums */
+#define PSFM_PREC_BF16X3 3   /* FP32 design; Gram on the tensor cores from a BF16 hi/lo split,
+                                3 products (hi*hi + hi*lo + lo*hi), FP32 sums */
 #define PSFM_PREC_F32X2 4    /* design and Gram in double-float (FP32 pairs, ~48 bits) */
 
 /* Options; psfm_config_default() fills the defaults noted in brackets. */
@@ -296,6 +297,24 @@ psfm_status psfm_convolve_noalloc(const float* ref, const float* var_ref,
                                   psfm_shape shape, const psfm_basis_spec* basis,
                                   const psfm_config* cfg, const psfm_solution* sol, float* out,
                                   float* out_var, uint16_t* out_mask, psfm_stream stream);
+
+/* Weighted Gram of column blocks: the normal-equation block C^T W C of one stamp (Eq. 5-6,
+ * the Gram accumulation of Sec. 3.5), exposed on its own for the precision study.  For each
+ * block b < n_blocks:
+ *   gram[b][i][j] = sum_p weights[b][p] * cols[b][i][p] * cols[b][j][p].
+ * cols: device [n_blocks][n_cols][n_pix] float; weights: device [n_blocks][n_pix] float;
+ * gram: device [n_blocks][n_cols][n_cols] double, written symmetric.  precision:
+ *   PSFM_PREC_FP64   FP64 products and sums (the reference; workspace unused, may be NULL);
+ *   PSFM_PREC_TF32   tensor cores, TF32 products, FP32 accumulation, n_cols <= 128;
+ *   PSFM_PREC_BF16X3 tensor cores, BF16 hi/lo split, three products, FP32 accumulation,
+ *                    n_cols <= 128;
+ * others return PSFM_ERR_UNSUPPORTED.  The tensor-core modes need PSFM_GRAM_WORKSPACE bytes of
+ * 256-byte-aligned device workspace (a status word) and synchronise `stream` to report a
+ * device-side PSFM_ERR_TIMEOUT; the FP64 mode is asynchronous. */
+#define PSFM_GRAM_WORKSPACE 256
+psfm_status psfm_gram(int32_t n_blocks, int32_t n_cols, int32_t n_pix, const float* cols,
+                      const float* weights, int32_t precision, double* gram, void* workspace,
+                      size_t ws_bytes, psfm_stream stream);
 
 /* Instrumentation (no counterpart in the paper).  psfm_profile_enable(1) clears the stage
  * table and starts recording a CUDA event pair around every stage the library enqueues

@@ -540,10 +540,23 @@ def convolve_image(I1, m1, sol: Solution, badmask, I2=None):
     return out
 
 
+def _masked_window(img, m, badmask, x, y, h):
+    """(2h+1)^2 window of img centred on (x, y) with masked and off-image pixels zero, and the
+    window's own centre coordinates (h, h)."""
+    H, W = img.shape
+    out = np.zeros((2 * h + 1, 2 * h + 1))
+    ya, yb, xa, xb = max(0, y - h), min(H, y + h + 1), max(0, x - h), min(W, x + h + 1)
+    sub = np.asarray(img[ya:yb, xa:xb], np.float64)
+    ok = (m[ya:yb, xa:xb].astype(np.int64) & badmask) == 0
+    out[ya - (y - h):yb - (y - h), xa - (x - h):xb - (x - h)] = np.where(ok, sub, 0.0)
+    return out
+
+
 def convolve_pixel(I1, m1, sol: Solution, badmask, x, y):
     """Eq. 12 at one output pixel with the kernel realised there (plus d0)."""
-    R = masked_ref(I1, m1, badmask)
-    return conv_pixel(R, realise_kernel(sol, x, y), x, y) + sol.d0
+    h = sol.basis.h
+    R = _masked_window(I1, m1, badmask, x, y, h)
+    return conv_pixel(R, realise_kernel(sol, x, y), h, h) + sol.d0
 
 
 def tile_centres(n, tile):
@@ -627,6 +640,23 @@ def variance_image(V1, m1, sol: Solution, badmask, tile=64, C_in=None, V2=None):
     return out
 
 
+def variance_pixel(V1, m1, sol: Solution, badmask, x, y, tile=64, C_in=None, V2=None):
+    """Eq. 13 at one output pixel: f_t sum_{u,v} K_t(u, v)^2 V1(x-u, y-v) with K_t realised at
+    the centre of the fixed tile that contains (x, y) (same tiles as ``variance_image``)."""
+    H, W = V1.shape
+    xa = (x // tile) * tile
+    ya = (y // tile) * tile
+    xc = (xa + min(W, xa + tile) - 1) / 2.0
+    yc = (ya + min(H, ya + tile) - 1) / 2.0
+    K = realise_kernel(sol, xc, yc)
+    f = 1.0 if C_in is None else covariance_factor(K, C_in)
+    h = sol.basis.h
+    v = f * conv_pixel(_masked_window(V1, m1, badmask, x, y, h), K * K, h, h)
+    if V2 is not None:
+        v += float(V2[y, x])
+    return v
+
+
 def r_bad(sol: Solution, bad_frac=0.2):
     """Box radius of CONV.BAD (Sec. 3.4): smallest r in [0, h] such that the sum of K^2 outside
     the box max(|u|, |v|) <= r is at most ``bad_frac`` of the total, K realised at the image
@@ -670,6 +700,33 @@ def mask_image(m1, sol: Solution, cfg: Config, m2=None, rb=None):
     out = np.where(nb, out | cfg.conv_bad, out)
     out = np.where(~nb & npoor, out | cfg.conv_poor, out)
     return out.astype(np.uint16)
+
+
+def mask_pixel(m1, sol: Solution, cfg: Config, x, y, m2=None, rb=None):
+    """Output mask of one pixel (Sec. 3.4), by the same rule as ``mask_image``: CONV.BAD when a
+    badmask pixel of m1 or the image edge lies within Chebyshev distance r_bad, else CONV.POOR
+    when one lies within h."""
+    H, W = m1.shape
+    h = sol.basis.h
+    if rb is None:
+        rb = r_bad(sol, cfg.bad_frac)
+    near_bad = near_poor = False
+    for dy in range(-h, h + 1):
+        for dx in range(-h, h + 1):
+            yy, xx = y + dy, x + dx
+            masked = not (0 <= yy < H and 0 <= xx < W) or (int(m1[yy, xx]) & cfg.badmask) != 0
+            if masked:
+                near_poor = True
+                if max(abs(dx), abs(dy)) <= rb:
+                    near_bad = True
+    out = int(m1[y, x])
+    if m2 is not None:
+        out |= int(m2[y, x])
+    if near_bad:
+        out |= cfg.conv_bad
+    elif near_poor:
+        out |= cfg.conv_poor
+    return out
 
 
 def pseudo_matrix(sol: Solution, cfg: Config, C_in=None):

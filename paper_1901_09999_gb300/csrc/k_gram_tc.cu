@@ -1,0 +1,448 @@
+// Weighted Gram of the stamp design blocks on the 5th-generation tensor cores (Eq. 5-6:
+// M_s = C_s^T W_s C_s over the stamp pixels, W = 1 / (V1 + V2)), in the two reduced-precision
+// forms of the precision study: TF32 products, and BF16 products of a hi/lo split
+// (a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi), both accumulated in FP32 in tensor memory.
+//
+// One CTA of 128 threads per stamp.  The augmented columns (basis columns C_k, the masked
+// reference R, the constant 1 and I2) form A (M = 128 rows, Nc of them used, K = pixels) and
+// the weighted columns W A form B (N = 64 or 128 rows); D = A B^T is the Gram.  Pixels are
+// staged 32 at a time into a double-buffered shared-memory tile in the canonical K-major
+// layout without swizzle (8-row x 16-byte core matrices), one thread issues the MMAs, and
+// tcgen05.commit arrives on the buffer's mbarrier when they have consumed it.  Every wait is
+// bounded: a wait that runs out records PSFM_ERR_TIMEOUT and the CTA still frees its tensor
+// memory before it returns.
+#include <cuda_bf16.h>
+
+#include "psfm_internal.h"
+#include "solve.h"
+#include "stamp.h"
+
+namespace psfm {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kTcM = 128;   // rows of A (TMEM lanes)
+constexpr int kTcKC = 32;   // pixels per staged chunk
+constexpr uint32_t kTcSpinLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: start address, leading (K-direction) and stride
+// (M/N-direction) byte offsets between core matrices, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+         ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format, both K-major, N, M.
+__device__ __forceinline__ uint32_t instr_desc(uint32_t ab_format, int n, int m) {
+  return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait for the phase with the given parity; false if it ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < kTcSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+template <int KIND>  // 0: kind::tf32, 1: kind::f16 (BF16 operands)
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  if (KIND == 0)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (row, k) of a K-major operand tile with kTcKC columns, built from
+// 8-row x 16-byte core matrices stored row group by row group: LBO = 128 B (next core matrix
+// along K), SBO = (kTcKC * esz / 16) * 128 B (next group of 8 rows).
+template <int ESZ>
+__device__ __forceinline__ uint32_t tile_off(int row, int k) {
+  constexpr int per = 16 / ESZ;  // elements per core-matrix row
+  return (uint32_t)(((row >> 3) * (kTcKC / per) + k / per) * 128 + (row & 7) * 16 + (k % per) * ESZ);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// Column source of the stamp Grams inside the solve: basis columns from the FP32 design
+// block, then R (masked), 1 and I2 read from the images at the stamp pixels, weights
+// 1 / (V1 + V2) (0 at masked or off-image pixels).  After the Gram it forms the transformed
+// Gram and marks the stamp's block as cached.
+struct StampSource {
+  StampParams P;
+  int r, cx, cy;
+  __device__ bool open(int blk) {
+    r = blk;
+    if (P.st->error || P.st->done) return false;
+    if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return false;
+    return P.have[r] != P.ptr[r];
+  }
+  __device__ int ncols() const { return P.Nc; }
+  __device__ int npix() const { return P.P; }
+  __device__ bool pixel(int pix, int64_t* o) const {
+    const int py = pix / P.sw, px = pix - py * P.sw;
+    const int gx = cx - P.s + px, gy = cy - P.s + py;
+    if (gx < 0 || gx >= P.g.W || gy < 0 || gy >= P.g.H) return false;
+    *o = (int64_t)gy * P.g.pitch + gx;
+    return true;
+  }
+  __device__ float weight(int pix) const {
+    int64_t o;
+    if (pix >= P.P || !pixel(pix, &o) || ((P.m1[o] | P.m2[o]) & P.badmask)) return 0.f;
+    const float a = P.i1[o], b = P.i2[o];
+    const double wd = 1.0 / ((double)P.v1[o] + (double)P.v2[o]);
+    if (!isfinite(a) || !isfinite(b) || !isfinite(wd)) raise_error(P.st, PSFM_ERR_NONFINITE);
+    return (float)wd;
+  }
+  __device__ float value(int c, int pix) const {
+    if (pix >= P.P) return 0.f;
+    const int Nb = P.b.Nb;
+    if (c < Nb) return reinterpret_cast<const float*>(P.C)[((int64_t)r * Nb + c) * P.P + pix];
+    int64_t o;
+    if (!pixel(pix, &o)) return 0.f;
+    if (c == Nb) return (P.m1[o] & P.badmask) ? 0.f : P.i1[o];
+    if (c == Nb + 1) return 1.f;
+    return P.i2[o];
+  }
+  __device__ double* gram() const { return P.G + (int64_t)r * P.Nc * P.Nc; }
+  __device__ void fail(int code) const { atomicCAS(&P.st->error, 0, code); }
+  __device__ void finish(int tid, int nthreads) const {
+    const int Nc = P.Nc, Nb = P.b.Nb, cR = Nb;
+    const double* Gr = gram();
+    double* Gtr = P.Gt + (int64_t)r * Nc * Nc;
+    for (int q = tid; q < Nc * Nc; q += nthreads) {
+      const int i = q / Nc, j = q - i * Nc;
+      const double ai = i < Nb ? P.psi[i] : 1.0, bi3 = i < Nb ? P.sk[i] : 0.0;
+      const double aj = j < Nb ? P.psi[j] : 1.0, bj3 = j < Nb ? P.sk[j] : 0.0;
+      double e = ai * aj * Gr[i * Nc + j];
+      if (bj3 != 0.0) e -= ai * bj3 * Gr[i * Nc + cR];
+      if (bi3 != 0.0) e -= bi3 * aj * Gr[cR * Nc + j];
+      if (bi3 != 0.0 && bj3 != 0.0) e += bi3 * bj3 * Gr[cR * Nc + cR];
+      Gtr[q] = e;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      P.have[r] = P.ptr[r];
+      P.fresh[r] = 1;
+    }
+  }
+};
+
+// Column source of psfm_gram: caller blocks cols [blk][c][pix] and weights [blk][pix].
+struct PlainSource {
+  const float* cols;
+  const float* w;
+  double* G;
+  int32_t* status;
+  int n_cols, n_pix, r;
+  __device__ bool open(int blk) {
+    r = blk;
+    return true;
+  }
+  __device__ int ncols() const { return n_cols; }
+  __device__ int npix() const { return n_pix; }
+  __device__ float weight(int pix) const {
+    return pix < n_pix ? w[(int64_t)r * n_pix + pix] : 0.f;
+  }
+  __device__ float value(int c, int pix) const {
+    return pix < n_pix ? cols[((int64_t)r * n_cols + c) * n_pix + pix] : 0.f;
+  }
+  __device__ double* gram() const { return G + (int64_t)r * n_cols * n_cols; }
+  __device__ void fail(int code) const { atomicCAS(status, 0, code); }
+  __device__ void finish(int, int) const {}
+};
+
+// MODE 0: TF32; MODE 1: BF16 hi/lo split with three products.  One block of 128 threads per
+// column block (stamp).
+template <int MODE, class Src>
+__global__ void __launch_bounds__(kTcThreads) k_gram_tc(Src src, int n_tile) {
+  constexpr int ESZ = MODE == 0 ? 4 : 2;
+  constexpr int NOPS = MODE == 0 ? 1 : 2;  // operand planes: value, or hi and lo
+  extern __shared__ __align__(1024) unsigned char tc_sh[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ float wsm[kTcKC];
+  __shared__ int s_ok, s_last, s_open;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // block-uniform early exit (finished loop, error, inactive region or cached Gram)
+  if (tid == 0) s_open = src.open(blockIdx.x) ? 1 : 0;
+  __syncthreads();
+  if (!s_open) return;
+  if (tid != 0) src.open(blockIdx.x);
+  const int Nc = src.ncols(), npix = src.npix();
+  const uint32_t a_bytes = kTcM * kTcKC * ESZ, b_bytes = (uint32_t)n_tile * kTcKC * ESZ;
+  const uint32_t stage_bytes = NOPS * (a_bytes + b_bytes);
+  // stage s: [A planes][B planes]
+  auto a_plane = [&](int s, int o) { return tc_sh + s * stage_bytes + o * a_bytes; };
+  auto b_plane = [&](int s, int o) {
+    return tc_sh + s * stage_bytes + NOPS * a_bytes + o * b_bytes;
+  };
+  // rows >= Nc stay zero for the whole kernel
+  for (uint32_t i = tid; i < 2 * stage_bytes / 4; i += kTcThreads)
+    reinterpret_cast<uint32_t*>(tc_sh)[i] = 0u;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_ok = 1;
+    s_last = -1;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(n_tile)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t idesc = instr_desc(MODE == 0 ? 2u : 1u, n_tile, kTcM);
+  const uint32_t sbo = (kTcKC * ESZ / 16) * 128;
+  const int kstep = MODE == 0 ? 8 : 16;  // K of one MMA
+  const int nchunk = (npix + kTcKC - 1) / kTcKC;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int s = ch & 1;
+    // the MMAs that read this buffer two chunks ago must be done before it is rewritten
+    if (ch >= 2 && !mbar_wait(&bars[s], ((ch - 2) >> 1) & 1) && tid == 0) s_ok = 0;
+    __syncthreads();
+    if (!s_ok) break;
+    const int base = ch * kTcKC;
+    if (tid < kTcKC) wsm[tid] = src.weight(base + tid);
+    __syncthreads();
+    for (int i = tid; i < Nc * kTcKC; i += kTcThreads) {
+      const int c = i / kTcKC, j = i - c * kTcKC;
+      const float v = src.value(c, base + j);
+      const float b = wsm[j] * v;
+      const uint32_t oa = tile_off<ESZ>(c, j);
+      if (MODE == 0) {
+        *reinterpret_cast<float*>(a_plane(s, 0) + oa) = v;
+        *reinterpret_cast<float*>(b_plane(s, 0) + oa) = b;
+      } else {
+        const float vh = __bfloat162float(__float2bfloat16_rn(v));
+        const float bh = __bfloat162float(__float2bfloat16_rn(b));
+        *reinterpret_cast<uint16_t*>(a_plane(s, 0) + oa) = bf16_bits(vh);
+        *reinterpret_cast<uint16_t*>(a_plane(s, 1) + oa) = bf16_bits(v - vh);
+        *reinterpret_cast<uint16_t*>(b_plane(s, 0) + oa) = bf16_bits(bh);
+        *reinterpret_cast<uint16_t*>(b_plane(s, 1) + oa) = bf16_bits(b - bh);
+      }
+    }
+    // make the generic-proxy stores visible to the tensor cores' reads
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      for (int k0 = 0; k0 < kTcKC; k0 += kstep) {
+        const uint32_t koff = (uint32_t)(k0 / (16 / ESZ)) * 128;
+        const uint64_t ah = smem_desc(smem_u32(a_plane(s, 0)) + koff, 128, sbo);
+        const uint64_t bh = smem_desc(smem_u32(b_plane(s, 0)) + koff, 128, sbo);
+        tc_mma<MODE>(tmem, ah, bh, idesc, (ch > 0 || k0 > 0) ? 1u : 0u);
+        if (MODE == 1) {
+          const uint64_t al = smem_desc(smem_u32(a_plane(s, 1)) + koff, 128, sbo);
+          const uint64_t bl = smem_desc(smem_u32(b_plane(s, 1)) + koff, 128, sbo);
+          tc_mma<MODE>(tmem, ah, bl, idesc, 1u);
+          tc_mma<MODE>(tmem, al, bh, idesc, 1u);
+        }
+      }
+      tc_commit(&bars[s]);
+      s_last = ch;
+    }
+  }
+  __syncthreads();
+  // the last commit covers every MMA issued before it; after a timeout this still waits
+  // (bounded) for the MMAs in flight before the tensor memory is freed
+  const int last = s_last;
+  const bool drained = last < 0 || mbar_wait(&bars[last & 1], (last >> 1) & 1);
+  __syncthreads();
+  if (!drained && tid == 0) s_ok = 0;
+  __syncthreads();
+  tc_fence_after();
+  const bool ok = s_ok != 0 && last == nchunk - 1;
+  double* Gr = src.gram();
+  if (ok) {
+    const int row = warp * 32 + lane;  // TMEM lane = row of D
+    for (int c0 = 0; c0 < n_tile; c0 += 16) {
+      float v[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int col = c0 + e;
+        if (row < Nc && col <= row) {
+          Gr[row * Nc + col] = (double)v[e];
+          Gr[col * Nc + row] = (double)v[e];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(n_tile)
+                 : "memory");
+  if (!ok) {
+    if (tid == 0) src.fail(PSFM_ERR_TIMEOUT);
+    return;
+  }
+  __syncthreads();
+  src.finish(tid, kTcThreads);
+}
+
+}  // namespace
+
+size_t gram_tc_smem(int mode, int n_tile) {
+  const size_t esz = mode == 0 ? 4 : 2, nops = mode == 0 ? 1 : 2;
+  return 2 * nops * (size_t)(kTcM + n_tile) * kTcKC * esz;
+}
+
+template <class Src>
+cudaError_t launch_gram_tc_src(int mode, const Src& src, int nblk, int n_cols, cudaStream_t s) {
+  const int n_tile = n_cols <= 64 ? 64 : 128;
+  const size_t smem = gram_tc_smem(mode, n_tile);
+  cudaError_t e;
+  if (mode == 0) {
+    e = cudaFuncSetAttribute(k_gram_tc<0, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gram_tc<0, Src><<<nblk, kTcThreads, smem, s>>>(src, n_tile);
+  } else {
+    e = cudaFuncSetAttribute(k_gram_tc<1, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gram_tc<1, Src><<<nblk, kTcThreads, smem, s>>>(src, n_tile);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tc(int mode, const StampParams& sp, int nreg, cudaStream_t s) {
+  StampSource src;
+  src.P = sp;
+  return launch_gram_tc_src(mode, src, nreg, sp.Nc, s);
+}
+
+cudaError_t launch_gram_tc_plain(int mode, const float* cols, const float* w, int n_blocks,
+                                 int n_cols, int n_pix, double* G, int32_t* status,
+                                 cudaStream_t s) {
+  PlainSource src;
+  src.cols = cols;
+  src.w = w;
+  src.G = G;
+  src.status = status;
+  src.n_cols = n_cols;
+  src.n_pix = n_pix;
+  return launch_gram_tc_src(mode, src, n_blocks, n_cols, s);
+}
+
+}  // namespace psfm
+
+namespace psfm {
+namespace {
+
+// FP64 reference Gram of psfm_gram: one thread per (i, j <= i), FP64 products and sums in
+// pixel order.
+__global__ void k_gram_fp64(const float* cols, const float* w, int n_cols, int n_pix,
+                            double* G) {
+  const int b = blockIdx.y;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = q / n_cols, j = q - i * n_cols;
+  if (i >= n_cols || j > i) return;
+  const float* ci = cols + ((int64_t)b * n_cols + i) * n_pix;
+  const float* cj = cols + ((int64_t)b * n_cols + j) * n_pix;
+  const float* wb = w + (int64_t)b * n_pix;
+  double s = 0.0;
+  for (int p = 0; p < n_pix; ++p) s = fma((double)wb[p] * (double)ci[p], (double)cj[p], s);
+  double* Gb = G + (int64_t)b * n_cols * n_cols;
+  Gb[i * n_cols + j] = s;
+  Gb[j * n_cols + i] = s;
+}
+
+}  // namespace
+}  // namespace psfm
+
+extern "C" psfm_status psfm_gram(int32_t n_blocks, int32_t n_cols, int32_t n_pix,
+                                 const float* cols, const float* weights, int32_t precision,
+                                 double* gram, void* workspace, size_t ws_bytes,
+                                 psfm_stream stream) {
+  if (n_blocks < 0 || n_cols < 1 || n_pix < 1 || !cols || !weights || !gram)
+    return n_blocks == 0 ? PSFM_OK : PSFM_ERR_BAD_ARG;
+  if (n_blocks == 0) return PSFM_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (precision == PSFM_PREC_FP64) {
+    const int64_t nt = (int64_t)n_cols * n_cols;
+    dim3 grid((unsigned)((nt + 255) / 256), (unsigned)n_blocks);
+    psfm::k_gram_fp64<<<grid, 256, 0, s>>>(cols, weights, n_cols, n_pix, gram);
+    return cudaGetLastError() == cudaSuccess ? PSFM_OK : PSFM_ERR_CUDA;
+  }
+  if (precision != PSFM_PREC_TF32 && precision != PSFM_PREC_BF16X3) return PSFM_ERR_UNSUPPORTED;
+  if (n_cols > 128) return PSFM_ERR_UNSUPPORTED;
+  if (!workspace || ws_bytes < PSFM_GRAM_WORKSPACE ||
+      (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return PSFM_ERR_WORKSPACE;
+  int32_t* status = static_cast<int32_t*>(workspace);
+  if (cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) return PSFM_ERR_CUDA;
+  if (psfm::launch_gram_tc_plain(precision == PSFM_PREC_TF32 ? 0 : 1, cols, weights, n_blocks,
+                                 n_cols, n_pix, gram, status, s) != cudaSuccess)
+    return PSFM_ERR_CUDA;
+  int32_t h = 0;
+  if (cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return PSFM_ERR_CUDA;
+  return h;
+}

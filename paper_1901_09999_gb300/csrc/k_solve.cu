@@ -22,59 +22,13 @@
 
 #include "psfm_internal.h"
 #include "solve.h"
+#include "stamp.h"
 
 namespace psfm {
+
+cudaError_t launch_gram_tc(int mode, const StampParams& sp, int nreg, cudaStream_t s);
+
 namespace {
-
-__device__ __forceinline__ void raise_error(DevState* st, int code) { atomicCAS(&st->error, 0, code); }
-
-// Whether a block skips its work because the loop has finished or an error was raised, by an
-// earlier kernel or by another block of this launch.  Read once by one thread so that the
-// decision is uniform across the block's barriers.
-__device__ __forceinline__ bool block_skip(const DevState* st) {
-  __shared__ int s_skip;
-  if (threadIdx.x == 0) s_skip = (st->error || st->done) ? 1 : 0;
-  __syncthreads();
-  return s_skip != 0;
-}
-
-__device__ __forceinline__ bool region_active(const int32_t* ptr, const int32_t* cand, int r,
-                                              int max_cand, int* cx, int* cy) {
-  const int j = ptr[r];
-  if (j >= max_cand) return false;
-  const int64_t c = (int64_t)r * max_cand + j;
-  *cx = cand[2 * c];
-  *cy = cand[2 * c + 1];
-  return *cx >= 0;
-}
-
-struct StampParams {
-  BasisDev b;
-  ImgGeom g;
-  const float* i1;
-  const float* i2;
-  const float* v1;
-  const float* v2;
-  const uint16_t* m1;
-  const uint16_t* m2;
-  uint16_t badmask;
-  int s, sw, P, foot, max_cand, Nc;
-  const float* f1d;     // [NH][wpad]
-  const double* f1d64;  // [NH][w]
-  const double* psi;
-  const double* sk;
-  const int32_t* cand;
-  const int32_t* ptr;
-  int32_t* have;
-  int32_t* fresh;  // [nreg] Gram recomputed in this iteration (added to M by k_system_delta)
-  void* C;  // [nreg][Nb][P] of T (float or double, by precision mode)
-  double* G;
-  double* Gt;
-  double* Gpart;        // [nreg][kGramSplit][Nc][Nc] partial Grams (double-float mode)
-  int32_t* gram_count;  // [nreg] partials finished, reset by the block that combines them
-  double* footsum;
-  DevState* st;
-};
 
 template <typename T>
 __device__ __forceinline__ T tap(const StampParams& P, int plane, int t) {
@@ -1537,6 +1491,8 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
     sm_gram = sizeof(float2) * nsl * npair * 16 + sizeof(float) * (4 * nblk * 4 * kGramChunk + 2 * kGramChunk);
   }
   if (sm_design > 200 * 1024 || sm_gram > 200 * 1024) return PSFM_ERR_UNSUPPORTED;
+  // TF32 / BF16X3: FP32 design blocks, the Gram on the tensor cores (k_gram_tc.cu)
+  const bool tcm = prec == PSFM_PREC_TF32 || prec == PSFM_PREC_BF16X3;
   auto design = prec == PSFM_PREC_FP64 ? k_stamp_design<double>
                 : prec == PSFM_PREC_F32X2 ? k_stamp_design_df : k_stamp_design<float>;
   auto gram = prec == PSFM_PREC_FP64 ? k_stamp_gram<double>
@@ -1571,7 +1527,12 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   for (int it = 0; it < p.cfg.max_iter; ++it) {
     prof_begin("stamps", s);
     design<<<dim3(p.nreg, dfm ? p.NH : p.ng), 256, sm_design, s>>>(sp);
-    gram<<<dim3(p.nreg, dfm ? kGramSplit : 1), dfm ? kGramThreads : 256, sm_gram, s>>>(sp);
+    if (tcm) {
+      if (launch_gram_tc(prec == PSFM_PREC_TF32 ? 0 : 1, sp, p.nreg, s) != cudaSuccess)
+        return PSFM_ERR_CUDA;
+    } else {
+      gram<<<dim3(p.nreg, dfm ? kGramSplit : 1), dfm ? kGramThreads : 256, sm_gram, s>>>(sp);
+    }
     prof_end("stamps", s, 2);
     prof_begin("system", s);
     k_norm<<<1, 1024, 0, s>>>(sy);

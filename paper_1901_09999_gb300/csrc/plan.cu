@@ -115,11 +115,9 @@ psfm_status make_plan(Plan& p, psfm_shape shape, const psfm_basis_spec* b, const
   if (c->norm_mode != PSFM_NORM_SEPARATE && c->norm_mode != PSFM_NORM_JOINT)
     return PSFM_ERR_BAD_ARG;
   if (c->precision != PSFM_PREC_FP64 && c->precision != PSFM_PREC_FP32 &&
-      c->precision != PSFM_PREC_F32X2) {
-    if (c->precision == PSFM_PREC_TF32 || c->precision == PSFM_PREC_BF16X3)
-      return PSFM_ERR_UNSUPPORTED;
+      c->precision != PSFM_PREC_F32X2 && c->precision != PSFM_PREC_TF32 &&
+      c->precision != PSFM_PREC_BF16X3)
     return PSFM_ERR_BAD_ARG;
-  }
   if (!(c->thresh_nsigma >= 0.0) || !(c->reject_nsigma > 0.0) || !(c->soften_alpha >= 0.0) ||
       !(c->bad_frac >= 0.0 && c->bad_frac <= 1.0))
     return PSFM_ERR_BAD_ARG;
@@ -139,6 +137,9 @@ psfm_status make_plan(Plan& p, psfm_shape shape, const psfm_basis_spec* b, const
   }
   p.Nsys = p.ncoef + (c->norm_mode == PSFM_NORM_JOINT ? 2 : 0);
   p.Nc = p.Nb + 3;
+  // the tensor-core Gram holds the augmented block in one 128-lane accumulator tile
+  if ((c->precision == PSFM_PREC_TF32 || c->precision == PSFM_PREC_BF16X3) && p.Nc > 128)
+    return PSFM_ERR_UNSUPPORTED;
   return PSFM_OK;
 }
 

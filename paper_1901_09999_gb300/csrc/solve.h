@@ -48,6 +48,13 @@ struct SolveBuffers {
 
 void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b);
 
+// Tensor-core weighted Gram of caller column blocks (TF32 mode 0, BF16 hi/lo mode 1):
+// G[b] = cols[b] diag(w[b]) cols[b]^T, cols [n_blocks][n_cols][n_pix], n_cols <= 128; a wait
+// that runs out writes PSFM_ERR_TIMEOUT to *status.
+cudaError_t launch_gram_tc_plain(int mode, const float* cols, const float* w, int n_blocks,
+                                 int n_cols, int n_pix, double* G, int32_t* status,
+                                 cudaStream_t s);
+
 // Enqueue the whole solve (extractor or caller stamps, rejection loop, r_bad).
 psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* dsol,
                       const SolveBuffers& b, const float* img, const float* ref,

@@ -437,6 +437,30 @@ def psfm_stack(imgs, vars_, masks, sources, target_fwhm, bases, cfg, want_cov=Tr
     return out, out_var, out_mask, out_count, cov, sols
 
 
+def psfm_gram(cols, weights, precision, stream=None):
+    """Weighted Gram of column blocks (C: psfm_gram).  ``cols`` (n_blocks, n_cols, n_pix) and
+    ``weights`` (n_blocks, n_pix) are contiguous float32 CUDA tensors; returns the
+    (n_blocks, n_cols, n_cols) float64 Gram."""
+    torch = _torch()
+    lib = load()
+    lib.psfm_gram.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                              C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+    lib.psfm_gram.restype = C.c_int32
+    if cols.dtype != torch.float32 or weights.dtype != torch.float32:
+        raise ValueError("cols and weights must be float32")
+    cols, weights = cols.contiguous(), weights.contiguous()
+    nb, nc, npix = cols.shape
+    if tuple(weights.shape) != (nb, npix):
+        raise ValueError("weights must be (n_blocks, n_pix)")
+    G = torch.empty((nb, nc, nc), dtype=torch.float64, device=cols.device)
+    ws = torch.empty(256, dtype=torch.uint8, device=cols.device)
+    st = lib.psfm_gram(nb, nc, npix, _ptr(cols), _ptr(weights), int(precision), _ptr(G), _ptr(ws),
+                       256, _stream(stream))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_gram")
+    return G
+
+
 # ------------------------------------------------------------------------ instrumentation
 
 def _prof_types(lib):

@@ -432,3 +432,66 @@ def isis_prescription_sigmas(fwhm_max: float):
     scaled linearly by fwhm_max / 9, the scale clamped to [0.7, 1.2]; returned as sigmas."""
     scale = min(1.2, max(0.7, fwhm_max / 9.0))
     return tuple(fwhm_to_sigma(f * scale) for f in (2.9, 4.8, 8.2))
+
+
+def torch_skycell_warps(seed: int, n_warps: int, size: int, n_src: int, device,
+                        sky: float = 500.0, masked_range=(0.05, 0.40)):
+    """Stacking inputs rendered on the GPU: ``n_warps`` warps of one ``size`` x ``size``
+    skycell sharing a source list (uniform positions, flux log-uniform in [1e3, 1e5] e-).  Each
+    warp's PSF is a core Gaussian plus a wing Gaussian of twice the width carrying a random
+    fraction (0-30 %) of the flux, core FWHM U[3.5, 7] px; sky plus Poisson noise, variance =
+    image; chip-gap bands (12 px every 300-700 px) and defect blocks bring the masked fraction
+    to U[masked_range].  Returns (warps, sources): warps are dicts of CUDA tensors image, var,
+    mask (int16) with the warp's fwhm; sources an (n, 3) float64 numpy array (x, y, flux)."""
+    import torch
+    import torch.nn.functional as F
+    rng = np.random.default_rng(int(seed))
+    xs = rng.uniform(0, size - 1, n_src)
+    ys = rng.uniform(0, size - 1, n_src)
+    fl = _log_uniform(rng, 1e3, 1e5, n_src)
+    sources = np.stack([xs, ys, fl], 1)
+    tx = torch.from_numpy(xs).to(device)
+    ty = torch.from_numpy(ys).to(device)
+    tf = torch.from_numpy(fl).to(device)
+    x0, y0 = tx.floor(), ty.floor()
+    fx, fy = tx - x0, ty - y0
+    point = torch.zeros(size * size, device=device, dtype=torch.float64)
+    for dx, dy, wgt in ((0, 0, (1 - fx) * (1 - fy)), (1, 0, fx * (1 - fy)),
+                        (0, 1, (1 - fx) * fy), (1, 1, fx * fy)):
+        xi = (x0 + dx).clamp(0, size - 1).long()
+        yi = (y0 + dy).clamp(0, size - 1).long()
+        point.index_add_(0, yi * size + xi, tf * wgt)
+    point = point.float().view(1, 1, size, size)
+
+    def blur(sig):
+        r = int(math.ceil(5 * sig))
+        t = torch.arange(-r, r + 1, device=device, dtype=torch.float64)
+        k = torch.exp(-t * t / (2 * sig * sig))
+        k = (k / k.sum()).float()
+        im = F.conv2d(F.pad(point, (r, r, 0, 0)), k.view(1, 1, 1, -1))
+        return F.conv2d(F.pad(im, (0, 0, r, r)), k.view(1, 1, -1, 1)).view(size, size)
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    warps = []
+    for _ in range(n_warps):
+        fw = float(rng.uniform(3.5, 7.0))
+        wing = float(rng.uniform(0.0, 0.3))
+        sig = fwhm_to_sigma(fw)
+        img = (1 - wing) * blur(sig) + wing * blur(2 * sig) + sky
+        img = torch.poisson(img.double(), generator=g).float()
+        m = torch.zeros((size, size), dtype=torch.int16, device=device)
+        gap = int(rng.integers(300, 700))
+        for g0 in range(int(rng.integers(0, gap)), size, gap):
+            m[:, g0:g0 + 12] = MASK_BAD
+        target = float(rng.uniform(*masked_range))
+        covered = float((m != 0).float().mean())
+        while covered < target:
+            bw, bh = int(rng.integers(50, 600)), int(rng.integers(50, 600))
+            bx, by = int(rng.integers(0, size - bw)), int(rng.integers(0, size - bh))
+            m[by:by + bh, bx:bx + bw] = MASK_BAD
+            covered = float((m != 0).float().mean())
+        img = img.masked_fill(m != 0, 0.0)
+        warps.append(dict(image=img.contiguous(), var=img.clamp_min(1.0).contiguous(), mask=m,
+                          fwhm=fw))
+    return warps, sources

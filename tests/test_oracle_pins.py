@@ -463,3 +463,29 @@ def test_render_target_flux_and_stack_of_equal_inputs():
     num = 2 * w * O1
     assert np.allclose(num / (2 * w), O1)
     assert np.allclose((2 * w * w * V1) / (2 * w) ** 2, V1 / 2)
+
+
+def test_per_pixel_forms_match_whole_image_forms():
+    """The one-pixel forms used for sampled full-size parity equal the whole-image forms
+    (Eq. 12 image, Eq. 13 variance with per-tile kernels, Sec. 3.4 masks), including edges,
+    masks, ragged tiles and a spatially varying kernel."""
+    W, H = 83, 70
+    sol = _fixed_solution(W, H, S=1, seed=3)
+    rng = np.random.default_rng(4)
+    V = rng.uniform(1.0, 9.0, (H, W)).astype(np.float32)
+    V2 = rng.uniform(1.0, 9.0, (H, W)).astype(np.float32)
+    m = np.zeros((H, W), np.uint16)
+    m[rng.random((H, W)) < 0.01] = 1
+    m2 = np.zeros((H, W), np.uint16)
+    m2[5, 7] = 4
+    cfg = O.Config(badmask=0xFF)
+    Vimg = O.variance_image(V, m, sol, 0xFF, 32, V2=V2)
+    Mimg = O.mask_image(m, sol, cfg, m2)
+    Oimg = O.convolve_image(V, m, sol, 0xFF)
+    for y in range(0, H, 3):
+        for x in range(0, W, 4):
+            assert abs(O.convolve_pixel(V, m, sol, 0xFF, x, y) - Oimg[y, x]) <= \
+                1e-12 * np.abs(V).max()
+            assert abs(O.variance_pixel(V, m, sol, 0xFF, x, y, 32, V2=V2) - Vimg[y, x]) <= \
+                1e-12 * Vimg[y, x]
+            assert O.mask_pixel(m, sol, cfg, x, y, m2) == Mimg[y, x]
