@@ -114,16 +114,8 @@ __global__ void __launch_bounds__(256, 2) k_conv_image(ConvParams P) {
     beta[tid] = (float)v;
   }
   // masked reference tile with halo; zero padding to the row stride
-  for (int i = tid; i < RR * RS; i += 256) {
-    const int r = i / RS, c = i - r * RS;
-    const int gx = x0 - HW + c, gy = y0 - HW + r;
-    float v = 0.f;
-    if (c < TX + 2 * HW && gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
-      const int64_t o = (int64_t)gy * P.g.pitch + gx;
-      if (!(P.mref[o] & P.badmask)) v = P.ref[o];
-    }
-    Rs[i] = v;
-  }
+  stage_masked_tile<8>(P.ref, P.mref, P.badmask, P.g.W, P.g.H, P.g.pitch, x0 - HW, y0 - HW, RR,
+                       TX + 2 * HW, RS, Rs, tid, 256);
   __syncthreads();
 
   const int lane = tid & 31, wi = tid >> 5;

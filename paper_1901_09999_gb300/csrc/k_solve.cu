@@ -252,33 +252,72 @@ __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
     }
   }
   __syncthreads();
+  // horizontal pass: each thread takes 4 neighbouring outputs of one footprint row and slides
+  // a 4-value register window along the taps (one shared-memory load per tap instead of four);
+  // each output still sums its taps in order t = 0..W-1
   {
     const float* ph = wh + p * W;
     const float* pw = wl + p * W;
-    for (int i = tid; i < foot * sw; i += 256) {
-      const int rr = i / sw, px = i - rr * sw;
-      const float* src = F + rr * foot + px + 2 * h;
-      df a = {0.f, 0.f};
-      for (int t = 0; t < W; ++t) df_fma_f(a, src[-t], df{ph[t], pw[t]});
-      a = df_norm(a);
-      Hh[i] = a.hi;
-      Hl[i] = a.lo;
+    const int ncg = (sw + 3) / 4;
+    for (int it = tid; it < foot * ncg; it += 256) {
+      const int rr = it / ncg, px0 = (it - rr * ncg) * 4;
+      const float* row = F + rr * foot;
+      float x0 = row[min(px0 + 2 * h, foot - 1)], x1 = row[min(px0 + 1 + 2 * h, foot - 1)];
+      float x2 = row[min(px0 + 2 + 2 * h, foot - 1)], x3 = row[min(px0 + 3 + 2 * h, foot - 1)];
+      df a0 = {0.f, 0.f}, a1 = a0, a2 = a0, a3 = a0;
+      for (int t = 0; t < W; ++t) {
+        const df w = {ph[t], pw[t]};
+        df_fma_f(a0, x0, w);
+        df_fma_f(a1, x1, w);
+        df_fma_f(a2, x2, w);
+        df_fma_f(a3, x3, w);
+        x3 = x2;
+        x2 = x1;
+        x1 = x0;
+        if (t + 1 < W) x0 = row[px0 + 2 * h - t - 1];
+      }
+      const df o[4] = {df_norm(a0), df_norm(a1), df_norm(a2), df_norm(a3)};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (px0 + j < sw) {
+          Hh[rr * sw + px0 + j] = o[j].hi;
+          Hl[rr * sw + px0 + j] = o[j].lo;
+        }
     }
   }
   __syncthreads();
+  // vertical passes: each thread takes 4 neighbouring rows of one column, with the same
+  // sliding window over the horizontal-pass rows
   const int kgp = P.b.kbase[g] + p * (dg + 1) - (p * (p - 1)) / 2;
+  const int nrg = (sw + 3) / 4;
   for (int q = 0; q <= dg - p; ++q) {
     const float* qh = wh + q * W;
     const float* ql = wl + q * W;
     float2* out = reinterpret_cast<float2*>(P.C) + ((int64_t)r * P.b.Nb + kgp + q) * P.P;
-    for (int i = tid; i < P.P; i += 256) {
-      const int py = i / sw, px = i - py * sw;
-      const int base = (py + 2 * h) * sw + px;
-      df a = {0.f, 0.f};
-      for (int t = 0; t < W; ++t)
-        df_fma(a, df{Hh[base - t * sw], Hl[base - t * sw]}, df{qh[t], ql[t]});
-      a = df_norm(a);
-      out[i] = make_float2(a.hi, a.lo);
+    for (int it = tid; it < sw * nrg; it += 256) {
+      const int rg = it / sw, px = it - rg * sw, py0 = rg * 4;
+      auto ld = [&](int row) {
+        const int o = min(row, foot - 1) * sw + px;
+        return df{Hh[o], Hl[o]};
+      };
+      df y0 = ld(py0 + 2 * h), y1 = ld(py0 + 1 + 2 * h), y2 = ld(py0 + 2 + 2 * h);
+      df y3 = ld(py0 + 3 + 2 * h);
+      df a0 = {0.f, 0.f}, a1 = a0, a2 = a0, a3 = a0;
+      for (int t = 0; t < W; ++t) {
+        const df w = {qh[t], ql[t]};
+        df_fma(a0, y0, w);
+        df_fma(a1, y1, w);
+        df_fma(a2, y2, w);
+        df_fma(a3, y3, w);
+        y3 = y2;
+        y2 = y1;
+        y1 = y0;
+        if (t + 1 < W) y0 = ld(py0 + 2 * h - t - 1);
+      }
+      const df o[4] = {df_norm(a0), df_norm(a1), df_norm(a2), df_norm(a3)};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (py0 + j < sw) out[(py0 + j) * sw + px] = make_float2(o[j].hi, o[j].lo);
     }
   }
 }
@@ -291,6 +330,9 @@ __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
 // last block of a stamp to finish (counted with an atomic) adds the partials in split order,
 // so the result does not depend on which block finishes last, and forms the transformed Gram.
 constexpr int kGramChunk = 64;
+// row stride of the staged columns: one float of padding puts the rows that the threads of a
+// warp read (different columns, same pixel) in different shared-memory banks
+constexpr int kGramLd = kGramChunk + 1;
 constexpr int kGramThreads = 512;
 __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
   extern __shared__ double shd[];
@@ -306,10 +348,10 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
   const int ncr = nblk * 4;                                        // padded column count
   float2* acc = reinterpret_cast<float2*>(shd);                   // [nsl][npair][16] df
   float* Ah = reinterpret_cast<float*>(acc + (size_t)nsl * npair * 16);  // [ncr][chunk]
-  float* Al = Ah + ncr * kGramChunk;
-  float* Bh = Al + ncr * kGramChunk;                               // w * A
-  float* Bl = Bh + ncr * kGramChunk;
-  float* wh = Bl + ncr * kGramChunk;                               // [chunk] weights
+  float* Al = Ah + ncr * kGramLd;
+  float* Bh = Al + ncr * kGramLd;                                  // w * A
+  float* Bl = Bh + ncr * kGramLd;
+  float* wh = Bl + ncr * kGramLd;                                  // [chunk] weights
   float* wl = wh + kGramChunk;
   for (int i = tid; i < nsl * npair * 16; i += kGramThreads) acc[i] = make_float2(0.f, 0.f);
   const float2* Cr = reinterpret_cast<const float2*>(P.C) + (int64_t)r * Nb * P.P;
@@ -355,10 +397,10 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
         }
       }
       const df b = df_mul(df{wh[j], wl[j]}, v);
-      Ah[i] = v.hi;
-      Al[i] = v.lo;
-      Bh[i] = b.hi;
-      Bl[i] = b.lo;
+      Ah[c * kGramLd + j] = v.hi;
+      Al[c * kGramLd + j] = v.lo;
+      Bh[c * kGramLd + j] = b.hi;
+      Bl[c * kGramLd + j] = b.lo;
     }
     __syncthreads();
     for (int pp = tid; pp < npair * nsl; pp += kGramThreads) {
@@ -376,8 +418,8 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
         df a[4], b[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          a[e] = df{Ah[(bi * 4 + e) * kGramChunk + j], Al[(bi * 4 + e) * kGramChunk + j]};
-          b[e] = df{Bh[(bj * 4 + e) * kGramChunk + j], Bl[(bj * 4 + e) * kGramChunk + j]};
+          a[e] = df{Ah[(bi * 4 + e) * kGramLd + j], Al[(bi * 4 + e) * kGramLd + j]};
+          b[e] = df{Bh[(bj * 4 + e) * kGramLd + j], Bl[(bj * 4 + e) * kGramLd + j]};
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e)
@@ -735,18 +777,34 @@ __global__ void __launch_bounds__(256) k_system_delta(SysParams P, int mode, int
   const int pidx = (si < 0 ? Ns : si) * N1 + (sj < 0 ? Ns : sj);
   double acc = 0.0;
   const int64_t gij = (int64_t)ai * Nc + aj;
+  int* list = reinterpret_cast<int*>(gsh + (size_t)chunk * N1 * N1);  // [chunk]
+  __shared__ int s_nf;
   for (int r0 = 0; r0 < P.nreg; r0 += chunk) {
     const int nr = min(chunk, P.nreg - r0);
     __syncthreads();
-    for (int q = threadIdx.x; q < nr * N1 * N1; q += blockDim.x)
-      gsh[q] = flag[r0 + q / (N1 * N1)] ? P.gp[(int64_t)r0 * N1 * N1 + q] : 0.0;
+    // warp 0 lists the flagged regions of this chunk in ascending order
+    if (threadIdx.x < 32) {
+      int base = 0;
+      for (int j0 = 0; j0 < nr; j0 += 32) {
+        const int j = j0 + threadIdx.x;
+        const bool f = j < nr && flag[r0 + j];
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (f) list[base + __popc(bal & ((1u << threadIdx.x) - 1u))] = j;
+        base += __popc(bal);
+      }
+      if (threadIdx.x == 0) s_nf = base;
+    }
+    __syncthreads();
+    const int nf = s_nf;
+    for (int q = threadIdx.x; q < nf * N1 * N1; q += blockDim.x) {
+      const int f = q / (N1 * N1);
+      gsh[q] = P.gp[(int64_t)(r0 + list[f]) * N1 * N1 + (q - f * N1 * N1)];
+    }
     __syncthreads();
     if (mine) {
       const double* Gr = P.Gt + (int64_t)r0 * Nc * Nc + gij;
-      for (int r = 0; r < nr; ++r) {
-        if (!flag[r0 + r]) continue;
-        acc = fma(gsh[r * N1 * N1 + pidx], Gr[(int64_t)r * Nc * Nc], acc);
-      }
+      for (int f = 0; f < nf; ++f)
+        acc = fma(gsh[f * N1 * N1 + pidx], Gr[(int64_t)list[f] * Nc * Nc], acc);
     }
   }
   if (!mine) return;
@@ -817,17 +875,18 @@ __device__ __forceinline__ df df_shfl(df a, int src) {
   return df{__shfl_sync(0xffffffffu, a.hi, src), __shfl_sync(0xffffffffu, a.lo, src)};
 }
 
-// Diagonal block, 128 threads with the block in shared memory: column-by-column Cholesky
-// (pivot, scale, rank-1 update of the trailing block, each phase across the CTA), then the
-// inverse of the block by the same column sweep.  The inverse turns the panel solve and the
+// Diagonal block by one warp with the block in shared memory: lane i owns row i of the factor
+// and column i of the inverse.  Column-by-column Cholesky (lane j takes the pivot, a shuffle
+// spreads its reciprocal square root, every lane below scales its entry and updates its own
+// row of the trailing block), then the inverse by the same sweep, each lane on its own column
+// with no exchange at all.  Only warp barriers.  The inverse turns the panel solve and the
 // triangular solves into dot products with no sequential chain.
-constexpr int kDiagThreads = 128;
+constexpr int kDiagThreads = 32;
 __global__ void __launch_bounds__(kDiagThreads) k_chol_diag(int n, int kb, float* Lh, float* Ll,
                                                             float2* Linv_all, DevState* st) {
   __shared__ float2 A[kNB][kNB + 1];
   __shared__ float2 X[kNB][kNB + 1];
   __shared__ float2 rp[kNB];
-  __shared__ int s_fail;
   if (st->error || st->done || st->chol_fail) return;
   const int k0 = kb * kNB, m = min(kNB, n - k0), tid = threadIdx.x;
   for (int q = tid; q < kNB * kNB; q += kDiagThreads) {
@@ -842,62 +901,53 @@ __global__ void __launch_bounds__(kDiagThreads) k_chol_diag(int n, int kb, float
     A[r][c] = v;
     X[r][c] = make_float2(r == c ? 1.f : 0.f, 0.f);
   }
-  if (tid == 0) s_fail = 0;
-  __syncthreads();
+  __syncwarp();
   for (int j = 0; j < kNB; ++j) {
-    // pivot and column scaling inside warp 0 (lane j computes the pivot, a shuffle spreads it)
-    if (tid < 32) {
-      df d = {A[j][j].x, A[j][j].y};
-      df r = {0.f, 0.f};
-      if (tid == j) {
-        if (!(d.hi > 0.f) || !isfinite(d.hi)) s_fail = 1;
-        r = df_rsqrt(d);
-        const df l = df_mul(d, r);
-        A[j][j] = make_float2(l.hi, l.lo);
-        rp[j] = make_float2(r.hi, r.lo);
-      }
-      r = df_shfl(r, j);
-      if (tid > j) {
-        const df a = df_mul(df{A[tid][j].x, A[tid][j].y}, r);
-        A[tid][j] = make_float2(a.hi, a.lo);
-      }
+    df r = {0.f, 0.f};
+    bool bad = false;
+    if (tid == j) {
+      const df d = {A[j][j].x, A[j][j].y};
+      bad = !(d.hi > 0.f) || !isfinite(d.hi);
+      r = df_rsqrt(d);
+      const df l = df_mul(d, r);
+      A[j][j] = make_float2(l.hi, l.lo);
+      rp[j] = make_float2(r.hi, r.lo);
     }
-    __syncthreads();
-    if (s_fail) break;
-    const int rem = kNB - j - 1;
-    for (int q = tid; q < rem * rem; q += kDiagThreads) {
-      const int i = j + 1 + q / rem, c = j + 1 + q % rem;
-      if (c <= i) {
-        df a = {A[i][c].x, A[i][c].y};
-        df_fma(a, df_neg(df{A[i][j].x, A[i][j].y}), df{A[c][j].x, A[c][j].y});
+    if (__any_sync(0xffffffffu, bad)) {
+      if (tid == 0) st->chol_fail = 1;
+      return;
+    }
+    r = df_shfl(r, j);
+    if (tid > j) {
+      const df a = df_mul(df{A[tid][j].x, A[tid][j].y}, r);
+      A[tid][j] = make_float2(a.hi, a.lo);
+    }
+    __syncwarp();
+    if (tid > j) {
+      const df lij = df_neg(df{A[tid][j].x, A[tid][j].y});
+      for (int c = j + 1; c <= tid; ++c) {
+        df a = {A[tid][c].x, A[tid][c].y};
+        df_fma(a, lij, df{A[c][j].x, A[c][j].y});
         a = df_norm(a);
-        A[i][c] = make_float2(a.hi, a.lo);
+        A[tid][c] = make_float2(a.hi, a.lo);
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
-  if (s_fail) {
-    if (tid == 0) st->chol_fail = 1;
-    return;
-  }
-  // inverse: for t = 0..: row t of X scaled by 1/L_tt, then X[i][:] -= L[i][t] X[t][:]
+  // inverse: for t = 0..: X[t][c] scaled by 1/L_tt, then X[i][c] -= L[i][t] X[t][c]; lane c
+  // owns column c
   for (int t = 0; t < kNB; ++t) {
-    if (tid < kNB) {
-      // 1 / L_tt is the pivot's reciprocal square root kept from the factorisation
-      const df x = df_mul(df{X[t][tid].x, X[t][tid].y}, df{rp[t].x, rp[t].y});
-      X[t][tid] = make_float2(x.hi, x.lo);
-    }
-    __syncthreads();
-    const int rem = kNB - t - 1;
-    for (int q = tid; q < rem * kNB; q += kDiagThreads) {
-      const int i = t + 1 + q / kNB, c = q % kNB;
-      df x = {X[i][c].x, X[i][c].y};
-      df_fma(x, df_neg(df{A[i][t].x, A[i][t].y}), df{X[t][c].x, X[t][c].y});
+    // 1 / L_tt is the pivot's reciprocal square root kept from the factorisation
+    const df xt = df_mul(df{X[t][tid].x, X[t][tid].y}, df{rp[t].x, rp[t].y});
+    X[t][tid] = make_float2(xt.hi, xt.lo);
+    for (int i = t + 1; i < kNB; ++i) {
+      df x = {X[i][tid].x, X[i][tid].y};
+      df_fma(x, df_neg(df{A[i][t].x, A[i][t].y}), xt);
       x = df_norm(x);
-      X[i][c] = make_float2(x.hi, x.lo);
+      X[i][tid] = make_float2(x.hi, x.lo);
     }
-    __syncthreads();
   }
+  __syncwarp();
   float2* Linv = Linv_all + (int64_t)kb * kNB * kNB;
   for (int q = tid; q < kNB * kNB; q += kDiagThreads) {
     const int r = q / kNB, c = q % kNB;
@@ -1178,32 +1228,48 @@ __global__ void __launch_bounds__(1024) k_lu_solve(int N, int joint, const doubl
   }
 }
 
-__device__ __forceinline__ double cval(float v) { return (double)v; }
-__device__ __forceinline__ double cval(double v) { return v; }
-__device__ __forceinline__ double cval(float2 v) { return (double)v.x + (double)v.y; }
-
 // sum_k a_k C_k(pix): FP64 products for FP32 / FP64 design blocks, double-float products on
 // the FP32 pipes for double-float blocks.
-__device__ __forceinline__ double basis_model(const double* ak, const float2*, const float* C,
-                                              int Nb, int P, int pix) {
-  double m = 0.0;
-  for (int k = 0; k < Nb; ++k) m += ak[k] * (double)C[(int64_t)k * P + pix];
-  return m;
-}
-__device__ __forceinline__ double basis_model(const double* ak, const float2*, const double* C,
-                                              int Nb, int P, int pix) {
-  double m = 0.0;
-  for (int k = 0; k < Nb; ++k) m += ak[k] * C[(int64_t)k * P + pix];
-  return m;
-}
-__device__ __forceinline__ double basis_model(const double*, const float2* akf, const float2* C,
-                                              int Nb, int P, int pix) {
-  df m = {0.f, 0.f};
+// sum_k a_k psi_k C_k at 4 stamp pixels at once (independent loads and accumulators; each
+// pixel still sums its terms in order k = 0..Nb-1).  pix < 0 marks an unused slot.
+__device__ __forceinline__ void basis_model4(const double* ak, const float2*, const float* C,
+                                             int Nb, int P, const int pix[4], double m[4]) {
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int k = 0; k < Nb; ++k) {
-    const float2 c = C[(int64_t)k * P + pix];
-    df_fma(m, df{akf[k].x, akf[k].y}, df{c.x, c.y});
+    const double a = ak[k];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (pix[j] >= 0) acc[j] += a * (double)C[(int64_t)k * P + pix[j]];
   }
-  return df_to_d(df_norm(m));
+#pragma unroll
+  for (int j = 0; j < 4; ++j) m[j] = acc[j];
+}
+__device__ __forceinline__ void basis_model4(const double* ak, const float2*, const double* C,
+                                             int Nb, int P, const int pix[4], double m[4]) {
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < Nb; ++k) {
+    const double a = ak[k];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (pix[j] >= 0) acc[j] += a * C[(int64_t)k * P + pix[j]];
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) m[j] = acc[j];
+}
+__device__ __forceinline__ void basis_model4(const double*, const float2* akf, const float2* C,
+                                             int Nb, int P, const int pix[4], double m[4]) {
+  df acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int k = 0; k < Nb; ++k) {
+    const df a = {akf[k].x, akf[k].y};
+    float2 c[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      c[j] = pix[j] >= 0 ? C[(int64_t)k * P + pix[j]] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) df_fma(acc[j], a, df{c[j].x, c[j].y});
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) m[j] = df_to_d(df_norm(acc[j]));
 }
 
 struct Chi2Params {
@@ -1252,18 +1318,36 @@ __global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
   const double delta = s_delta, d0 = Q.dsol[1];
   const T* Cr = reinterpret_cast<const T*>(P.C) + (int64_t)r * Nb * P.P;
   double q = 0.0, n = 0.0;
-  for (int pix = tid; pix < P.P; pix += 256) {
-    const int py = pix / P.sw, px = pix - py * P.sw;
-    const int gx = cx - P.s + px, gy = cy - P.s + py;
-    if (gx < 0 || gx >= P.g.W || gy < 0 || gy >= P.g.H) continue;
-    const int64_t o = (int64_t)gy * P.g.pitch + gx;
-    if ((P.m1[o] | P.m2[o]) & P.badmask) continue;
-    const double R = P.i1[o], I2 = P.i2[o];
-    const double model = delta * R + d0 + basis_model(ak, akf, Cr, Nb, P.P, pix);
-    const double res = I2 - model;
-    const double den = ((double)P.v1[o] + (double)P.v2[o]) + Q.alpha * fabs(I2);
-    q += res * res / den;
-    n += 1.0;
+  // 4 pixels per thread at a time, so that their design-column loads overlap
+  for (int base = tid; base < P.P; base += 4 * 256) {
+    int pix[4];
+    int64_t off[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      pix[j] = -1;
+      const int pp = base + 256 * j;
+      if (pp >= P.P) continue;
+      const int py = pp / P.sw, px = pp - py * P.sw;
+      const int gx = cx - P.s + px, gy = cy - P.s + py;
+      if (gx < 0 || gx >= P.g.W || gy < 0 || gy >= P.g.H) continue;
+      const int64_t o = (int64_t)gy * P.g.pitch + gx;
+      if ((P.m1[o] | P.m2[o]) & P.badmask) continue;
+      pix[j] = pp;
+      off[j] = o;
+    }
+    double mod[4];
+    basis_model4(ak, akf, Cr, Nb, P.P, pix, mod);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (pix[j] < 0) continue;
+      const int64_t o = off[j];
+      const double R = P.i1[o], I2 = P.i2[o];
+      const double model = delta * R + d0 + mod[j];
+      const double res = I2 - model;
+      const double den = ((double)P.v1[o] + (double)P.v2[o]) + Q.alpha * fabs(I2);
+      q += res * res / den;
+      n += 1.0;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -1488,7 +1572,7 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
     sm_design = sizeof(float) * ((size_t)p.foot * p.foot + 2 * (size_t)p.foot * p.sw +
                                  2 * (size_t)(p.dmax + 1) * p.w);
     const int nsl = kGramThreads / npair > 1 ? kGramThreads / npair : 1;
-    sm_gram = sizeof(float2) * nsl * npair * 16 + sizeof(float) * (4 * nblk * 4 * kGramChunk + 2 * kGramChunk);
+    sm_gram = sizeof(float2) * nsl * npair * 16 + sizeof(float) * (4 * nblk * 4 * kGramLd + 2 * kGramChunk);
   }
   if (sm_design > 200 * 1024 || sm_gram > 200 * 1024) return PSFM_ERR_UNSUPPORTED;
   // TF32 / BF16X3: FP32 design blocks, the Gram on the tensor cores (k_gram_tc.cu)
@@ -1508,7 +1592,7 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   const int64_t nthr = (int64_t)N * N;
   const int N1 = p.Ns + 1;
   const int asm_chunk = (40 * 1024) / (N1 * N1 * (int)sizeof(double));
-  const size_t sm_asm = sizeof(double) * (size_t)asm_chunk * N1 * N1;
+  const size_t sm_asm = (sizeof(double) * N1 * N1 + sizeof(int)) * (size_t)asm_chunk;
   const int npanel = (N + kNB - 1) / kNB;
   const size_t sm_solve = sizeof(float2) * ((size_t)N + 33 * 33 + 32);
   if (sm_solve > 200 * 1024) return PSFM_ERR_UNSUPPORTED;

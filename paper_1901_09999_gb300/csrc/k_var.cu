@@ -115,16 +115,8 @@ __global__ void __launch_bounds__(256) k_variance(VarParams P) {
     K2[u * P.b.wpad + v] = 0.f;
   }
   // masked variance tile with halo
-  for (int i = tid; i < VR * VS; i += 256) {
-    const int r = i / VS, c = i - r * VS;
-    const int gx = x0 - HW + c, gy = y0 - HW + r;
-    float v = 0.f;
-    if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
-      const int64_t o = (int64_t)gy * P.g.pitch + gx;
-      if (!(P.mref[o] & P.badmask)) v = P.var_ref[o];
-    }
-    Vs[i] = v;
-  }
+  stage_masked_tile<8>(P.var_ref, P.mref, P.badmask, P.g.W, P.g.H, P.g.pitch, x0 - HW, y0 - HW,
+                       VR, VS, VS, Vs, tid, 256);
   __syncthreads();
   // covariance factor of K_t (Sec. 4.3): sum_d C(d) sum_a K(a) K(a-d) / sum K^2
   if (P.cov_in) {

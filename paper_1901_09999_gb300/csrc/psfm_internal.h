@@ -125,6 +125,45 @@ struct ApplyBuffers {
 
 BasisDev basis_dev(const Plan& p);
 
+#ifdef __CUDACC__
+// Stage the rows x ld tile whose top-left image pixel is (gx0, gy0) into shared memory: the
+// image value where the pixel is inside the image, in the first `cols` columns and not
+// flagged in `badmask`, else 0.  Each thread keeps G elements' global loads in flight
+// together, so the tile arrives in a few memory latencies instead of one per element.
+template <int G>
+__device__ __forceinline__ void stage_masked_tile(const float* img, const uint16_t* mask,
+                                                  uint16_t badmask, int W, int H,
+                                                  int64_t pitch, int gx0, int gy0, int rows,
+                                                  int cols, int ld, float* dst, int tid,
+                                                  int nthreads) {
+  const int n = rows * ld;
+  for (int i0 = tid; i0 < n; i0 += G * nthreads) {
+    float v[G];
+    uint16_t m[G];
+    bool ok[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int i = i0 + g * nthreads;
+      const int r = i / ld, c = i - r * ld;
+      const int gx = gx0 + c, gy = gy0 + r;
+      ok[g] = i < n && c < cols && gx >= 0 && gx < W && gy >= 0 && gy < H;
+      v[g] = 0.f;
+      m[g] = 0;
+      if (ok[g]) {
+        const int64_t o = (int64_t)gy * pitch + gx;
+        v[g] = img[o];
+        m[g] = mask[o];
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int i = i0 + g * nthreads;
+      if (i < n) dst[i] = (ok[g] && !(m[g] & badmask)) ? v[g] : 0.f;
+    }
+  }
+}
+#endif
+
 // Stage timing (CUDA events on the launching stream when profiling is on) and launch count.
 void prof_begin(const char* name, cudaStream_t s);
 void prof_end(const char* name, cudaStream_t s, int n_launches);
