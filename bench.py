@@ -36,7 +36,7 @@ WORKLOAD = dict(
 # DRAM bytes (read + write) of one k_conv_image launch on the full-chip workload, from the ncu
 # capture summarised in profiles/k_conv_image_k_variance_full_chip.md; valid for the kernel
 # as captured there.
-CONV_TRAFFIC_FULL_CHIP = 234.80192e6 + 75.25248e6
+CONV_TRAFFIC_FULL_CHIP = 236.08192e6 + 75.049984e6
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3, "f32x2": 4}
@@ -524,35 +524,93 @@ def main():
     if not args.no_e2e and not args.exposure:
         keys = ("img", "ref", "var_img", "var_ref", "mask_img", "mask_ref")
         h_in = [[c[k].cpu().pin_memory() for k in keys] for c in chips]
-        if batch is not None:
-            d_out = [(batch.diff[i], batch.diff_var[i], batch.diff_mask[i])
-                     for i in range(len(chips))]
-        else:
-            d_out = [(outs["out"], outs["out_var"], outs["out_mask"])]
-        h_out = [[torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in o] for o in d_out]
         bi = sum(t.numel() * t.element_size() for hs in h_in for t in hs)
-        bo = sum(t.numel() * t.element_size() for hs in h_out for t in hs)
+        if batch is not None:
+            # two device buffer sets, each with its own batch graph: while one step computes,
+            # the copy stream uploads the next step's inputs into the other set and reads the
+            # previous step's outputs back
+            chips2 = [{k: torch.empty_like(c[k]) for k in keys} for c in chips]
+            batch2 = P.Batch(chips2, bases, cfg, n_streams=args.streams, want_cov=True)
+            sets = [(chips, batch), (chips2, batch2)]
+            h_out = [[[torch.empty(t.shape, dtype=t.dtype).pin_memory()
+                       for t in (b.diff[i], b.diff_var[i], b.diff_mask[i])]
+                      for i in range(len(chips))] for _, b in sets]
+            bo = sum(t.numel() * t.element_size() for hs in h_out[0] for t in hs)
+            copy = torch.cuda.Stream()
+            ev_up = [torch.cuda.Event(), torch.cuda.Event()]
+            ev_comp = [torch.cuda.Event(), torch.cuda.Event()]
+            ev_down = [torch.cuda.Event(), torch.cuda.Event()]
 
-        def e2e_step():
-            for c, hs in zip(chips, h_in):
-                for k, h in zip(keys, hs):
-                    c[k].copy_(h, non_blocking=True)
-            step()
-            for hs, ds in zip(h_out, d_out):
-                for h, d in zip(hs, ds):
-                    h.copy_(d, non_blocking=True)
+            def upload(si):
+                for c, hs in zip(sets[si][0], h_in):
+                    for k, hh in zip(keys, hs):
+                        c[k].copy_(hh, non_blocking=True)
+                ev_up[si].record(copy)
 
-        with torch.cuda.stream(stream):
-            e2e_step()
+            def download(si):
+                b = sets[si][1]
+                for i, hs in enumerate(h_out[si]):
+                    for hh, d in zip(hs, (b.diff[i], b.diff_var[i], b.diff_mask[i])):
+                        hh.copy_(d, non_blocking=True)
+                ev_down[si].record(copy)
+
+            def e2e_run(n, start_event=None):
+                with torch.cuda.stream(copy):
+                    if start_event is not None:
+                        copy.wait_event(start_event)
+                    upload(0)
+                for k in range(n):
+                    si = k % 2
+                    stream.wait_event(ev_up[si])
+                    sets[si][1].run(stream)
+                    ev_comp[si].record(stream)
+                    with torch.cuda.stream(copy):
+                        if k + 1 < n:
+                            if k >= 1:
+                                copy.wait_event(ev_comp[1 - si])
+                            upload(1 - si)
+                        copy.wait_event(ev_comp[si])
+                        download(si)
+                stream.wait_event(ev_down[(n - 1) % 2])
+
+            e2e_run(2)  # captures the second graph
             torch.cuda.synchronize()
-            n2 = max(2, args.steps // 2)
+            n2 = max(2, args.steps)
             e0.record(stream)
-            for _ in range(n2):
-                e2e_step()
+            e2e_run(n2, e0)
             e1.record(stream)
             torch.cuda.synchronize()
-        e2e = {"value": px_per_step * n2 / 1e6 / (e0.elapsed_time(e1) / 1e3), "unit": "Mpix/s",
-               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+            e2e_ms = e0.elapsed_time(e1)
+            batch2.close()
+            del chips2
+        else:
+            d_out = [(outs["out"], outs["out_var"], outs["out_mask"])]
+            h_out = [[torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in o] for o in d_out]
+            bo = sum(t.numel() * t.element_size() for hs in h_out for t in hs)
+
+            def e2e_step():
+                for c, hs in zip(chips, h_in):
+                    for k, hh in zip(keys, hs):
+                        c[k].copy_(hh, non_blocking=True)
+                step()
+                for hs, ds in zip(h_out, d_out):
+                    for hh, d in zip(hs, ds):
+                        hh.copy_(d, non_blocking=True)
+
+            with torch.cuda.stream(stream):
+                e2e_step()
+                torch.cuda.synchronize()
+                n2 = max(2, args.steps // 2)
+                e0.record(stream)
+                for _ in range(n2):
+                    e2e_step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+            e2e_ms = e0.elapsed_time(e1)
+        e2e = {"value": px_per_step * n2 / 1e6 / (e2e_ms / 1e3), "unit": "Mpix/s",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+               "overlap": "copies of one step overlap the compute of the next (two buffer sets)"
+                          if batch is not None else "none"}
 
     if rank != 0:
         if world > 1:

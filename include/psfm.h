@@ -144,7 +144,24 @@ typedef struct {
   double chi2_mean;      /* mean chi^2 over the final stamps (Sec. 3.6) */
   double chi2_rms;       /* population std of chi^2 over the final stamps */
   float median;          /* background of the detection image I1 + I2 */
+  /* Quality diagnostics (Sec. 3.7), from the kernel K realised at the image centre in FP64
+   * (u, v the kernel offsets, sums over the (2h+1)^2 box): */
+  double kernel_sum;     /* sum K */
+  double mom_x, mom_y;   /* first moments sum u K / sum K, sum v K / sum K */
+  double mom_xx, mom_yy, mom_xy;  /* central second moments, e.g. sum (u - mom_x)^2 K / sum K */
+  double deconv_max;     /* max over r = 0..h of sum_{u^2+v^2 <= r^2} K / sum K (> 1: deconvolution) */
+  int32_t quality_flags; /* PSFM_QUALITY_* bits: the paper's recommended cuts */
 } psfm_solution;
+
+/* Quality cuts recommended for flagging bad subtractions (Sec. 3.7).  The two deviation
+ * cuts are applied to chi2_mean and chi2_rms as defined above (softened chi^2 with
+ * sigma^2 = V1 + V2), the reading taken of the paper's normalised deviations. */
+#define PSFM_QUALITY_FEW_STAMPS 1  /* n_used < 3 */
+#define PSFM_QUALITY_MEAN_DEV 2    /* chi2_mean > 0.5 */
+#define PSFM_QUALITY_RMS_DEV 4     /* chi2_rms > 0.3 */
+#define PSFM_QUALITY_MOMENT1 8     /* |mom_x| > 0.5 or |mom_y| > 0.5 */
+#define PSFM_QUALITY_MOMENT2 16    /* mom_xx < 0 or mom_yy < 0 */
+#define PSFM_QUALITY_DECONV 32     /* deconv_max > 1.03 */
 
 /* Fill `cfg` with the defaults listed in psfm_config. */
 void psfm_config_default(psfm_config* cfg);

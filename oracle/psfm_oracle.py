@@ -673,6 +673,51 @@ def r_bad(sol: Solution, bad_frac=0.2):
     return h
 
 
+QUALITY_FEW_STAMPS, QUALITY_MEAN_DEV, QUALITY_RMS_DEV = 1, 2, 4
+QUALITY_MOMENT1, QUALITY_MOMENT2, QUALITY_DECONV = 8, 16, 32
+
+
+def kernel_quality(K):
+    """Diagnostics of one realised kernel K[v+h, u+h] (Sec. 3.7): its sum, first moments
+    (sum u K / sum K, sum v K / sum K), central second moments, and the deconvolution measure:
+    the kernel sum enclosed within radius r (u^2 + v^2 <= r^2) relative to the total, at its
+    maximum over r = 0..h."""
+    h = (K.shape[0] - 1) // 2
+    U, V = np.meshgrid(np.arange(-h, h + 1, dtype=np.float64),
+                       np.arange(-h, h + 1, dtype=np.float64))
+    ks = float(K.sum())
+    mx, my = float((U * K).sum()) / ks, float((V * K).sum()) / ks
+    mxx = float(((U - mx) ** 2 * K).sum()) / ks
+    myy = float(((V - my) ** 2 * K).sum()) / ks
+    mxy = float(((U - mx) * (V - my) * K).sum()) / ks
+    r2 = U * U + V * V
+    deconv = max(float(K[r2 <= r * r].sum()) / ks for r in range(h + 1))
+    return dict(kernel_sum=ks, mom_x=mx, mom_y=my, mom_xx=mxx, mom_yy=myy, mom_xy=mxy,
+                deconv_max=deconv)
+
+
+def quality(sol: Solution, n_used, chi2_mean, chi2_rms):
+    """Quality record of a solution (Sec. 3.7): ``kernel_quality`` of the kernel realised at the
+    image centre plus the paper's recommended cuts as flags (reading: the normalised mean and
+    r.m.s. deviations are the mean and population std of the stamps' softened chi^2)."""
+    q = kernel_quality(realise_kernel(sol, (sol.W - 1) / 2.0, (sol.H - 1) / 2.0))
+    f = 0
+    if n_used < 3:
+        f |= QUALITY_FEW_STAMPS
+    if chi2_mean > 0.5:
+        f |= QUALITY_MEAN_DEV
+    if chi2_rms > 0.3:
+        f |= QUALITY_RMS_DEV
+    if abs(q["mom_x"]) > 0.5 or abs(q["mom_y"]) > 0.5:
+        f |= QUALITY_MOMENT1
+    if q["mom_xx"] < 0 or q["mom_yy"] < 0:
+        f |= QUALITY_MOMENT2
+    if q["deconv_max"] > 1.03:
+        f |= QUALITY_DECONV
+    q["flags"] = f
+    return q
+
+
 def mask_image(m1, sol: Solution, cfg: Config, m2=None, rb=None):
     """Output mask (Sec. 3.4): m1 (| m2 for a difference) plus CONV.BAD where a masked pixel of
     the convolved image, or the image edge, lies within Chebyshev distance r_bad, else

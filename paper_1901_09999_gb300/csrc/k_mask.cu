@@ -108,6 +108,8 @@ __global__ void k_rbad(BasisDev b, const double* f1d64, const double* psi, const
   double* colgp = sh;            // [NH][W]
   double* K2 = colgp + b.NH * W; // [W*W]
   double* part = K2 + W * W;     // [h+2]
+  double* Kc = part + 2 * h + 3; // [W*W] the kernel itself (after the [h+1] ring sums)
+  double* encl = Kc + W * W;     // [h+1] kernel sum within radius r
   const int tid = threadIdx.x;
   if (st->error) return;
   for (int i = tid; i < b.NH * W; i += blockDim.x) {
@@ -134,6 +136,7 @@ __global__ void k_rbad(BasisDev b, const double* f1d64, const double* psi, const
     for (int pl = 0; pl < b.NH; ++pl) kv += f1d64[pl * W + u] * colgp[pl * W + v];
     if (u == h && v == h) kv += part[h + 1];
     K2[i] = kv * kv;
+    Kc[i] = kv;
   }
   __syncthreads();
   // energy per Chebyshev ring, then outside(r) = sum of the rings beyond r
@@ -162,6 +165,61 @@ __global__ void k_rbad(BasisDev b, const double* f1d64, const double* psi, const
       }
     st->r_bad = rb;
   }
+  // quality diagnostics (Sec. 3.7): moments and enclosed kernel sums; every sum is taken in a
+  // fixed order (per-thread strided partials, xor-shuffle trees, warps in order)
+  __shared__ double wpart[8][6];
+  double m[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // K, uK, vK, uuK, vvK, uvK
+  for (int i = tid; i < W * W; i += blockDim.x) {
+    const double v = (double)(i / W - h), u = (double)(i % W - h), k = Kc[i];
+    m[0] += k;
+    m[1] += u * k;
+    m[2] += v * k;
+    m[3] += u * u * k;
+    m[4] += v * v * k;
+    m[5] += u * v * k;
+  }
+  const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    for (int o = 16; o > 0; o >>= 1) m[j] += __shfl_xor_sync(0xffffffffu, m[j], o);
+    if (lane == 0) wpart[wid][j] = m[j];
+  }
+  // enclosed sums: warp w takes radii r = w, w + nw, ...
+  for (int r = wid; r <= h; r += nw) {
+    double e = 0.0;
+    for (int i = lane; i < W * W; i += 32) {
+      const int v = i / W - h, u = i % W - h;
+      if (u * u + v * v <= r * r) e += Kc[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0) encl[r] = e;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < nw; ++w)
+      for (int j = 0; j < 6; ++j) t[j] += wpart[w][j];
+    const double ks = t[0];
+    const double mx = t[1] / ks, my = t[2] / ks;
+    const double mxx = t[3] / ks - mx * mx, myy = t[4] / ks - my * my, mxy = t[5] / ks - mx * my;
+    double dmax = -INFINITY;
+    for (int r = 0; r <= h; ++r) dmax = fmax(dmax, encl[r] / ks);
+    st->q_ksum = ks;
+    st->q_mx = mx;
+    st->q_my = my;
+    st->q_mxx = mxx;
+    st->q_myy = myy;
+    st->q_mxy = mxy;
+    st->q_deconv = dmax;
+    int f = 0;
+    if (st->n_active < 3) f |= PSFM_QUALITY_FEW_STAMPS;
+    if (st->chi2_mean > 0.5) f |= PSFM_QUALITY_MEAN_DEV;
+    if (st->chi2_rms > 0.3) f |= PSFM_QUALITY_RMS_DEV;
+    if (fabs(mx) > 0.5 || fabs(my) > 0.5) f |= PSFM_QUALITY_MOMENT1;
+    if (mxx < 0.0 || myy < 0.0) f |= PSFM_QUALITY_MOMENT2;
+    if (dmax > 1.03) f |= PSFM_QUALITY_DECONV;
+    st->q_flags = f;
+  }
 }
 
 }  // namespace
@@ -183,7 +241,8 @@ cudaError_t launch_mask(const Plan& p, const ApplyBuffers& b, const uint16_t* mr
 
 cudaError_t launch_rbad(const Plan& p, const DevTables& t, const double* dsol, DevState* ds,
                         cudaStream_t st) {
-  const size_t smem = sizeof(double) * ((size_t)p.NH * p.w + (size_t)p.w * p.w + 2 * p.h + 3);
+  const size_t smem =
+      sizeof(double) * ((size_t)p.NH * p.w + 2 * (size_t)p.w * p.w + 3 * (size_t)p.h + 4);
   cudaError_t e = cudaFuncSetAttribute(k_rbad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

@@ -875,18 +875,17 @@ __device__ __forceinline__ df df_shfl(df a, int src) {
   return df{__shfl_sync(0xffffffffu, a.hi, src), __shfl_sync(0xffffffffu, a.lo, src)};
 }
 
-// Diagonal block by one warp with the block in shared memory: lane i owns row i of the factor
-// and column i of the inverse.  Column-by-column Cholesky (lane j takes the pivot, a shuffle
-// spreads its reciprocal square root, every lane below scales its entry and updates its own
-// row of the trailing block), then the inverse by the same sweep, each lane on its own column
-// with no exchange at all.  Only warp barriers.  The inverse turns the panel solve and the
+// Diagonal block, 128 threads with the block in shared memory: column-by-column Cholesky
+// (pivot, scale, rank-1 update of the trailing block, each phase across the CTA), then the
+// inverse of the block by the same column sweep.  The inverse turns the panel solve and the
 // triangular solves into dot products with no sequential chain.
-constexpr int kDiagThreads = 32;
+constexpr int kDiagThreads = 128;
 __global__ void __launch_bounds__(kDiagThreads) k_chol_diag(int n, int kb, float* Lh, float* Ll,
                                                             float2* Linv_all, DevState* st) {
   __shared__ float2 A[kNB][kNB + 1];
   __shared__ float2 X[kNB][kNB + 1];
   __shared__ float2 rp[kNB];
+  __shared__ int s_fail;
   if (st->error || st->done || st->chol_fail) return;
   const int k0 = kb * kNB, m = min(kNB, n - k0), tid = threadIdx.x;
   for (int q = tid; q < kNB * kNB; q += kDiagThreads) {
@@ -901,53 +900,62 @@ __global__ void __launch_bounds__(kDiagThreads) k_chol_diag(int n, int kb, float
     A[r][c] = v;
     X[r][c] = make_float2(r == c ? 1.f : 0.f, 0.f);
   }
-  __syncwarp();
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
   for (int j = 0; j < kNB; ++j) {
-    df r = {0.f, 0.f};
-    bool bad = false;
-    if (tid == j) {
-      const df d = {A[j][j].x, A[j][j].y};
-      bad = !(d.hi > 0.f) || !isfinite(d.hi);
-      r = df_rsqrt(d);
-      const df l = df_mul(d, r);
-      A[j][j] = make_float2(l.hi, l.lo);
-      rp[j] = make_float2(r.hi, r.lo);
-    }
-    if (__any_sync(0xffffffffu, bad)) {
-      if (tid == 0) st->chol_fail = 1;
-      return;
-    }
-    r = df_shfl(r, j);
-    if (tid > j) {
-      const df a = df_mul(df{A[tid][j].x, A[tid][j].y}, r);
-      A[tid][j] = make_float2(a.hi, a.lo);
-    }
-    __syncwarp();
-    if (tid > j) {
-      const df lij = df_neg(df{A[tid][j].x, A[tid][j].y});
-      for (int c = j + 1; c <= tid; ++c) {
-        df a = {A[tid][c].x, A[tid][c].y};
-        df_fma(a, lij, df{A[c][j].x, A[c][j].y});
-        a = df_norm(a);
-        A[tid][c] = make_float2(a.hi, a.lo);
+    // pivot and column scaling inside warp 0 (lane j computes the pivot, a shuffle spreads it)
+    if (tid < 32) {
+      df d = {A[j][j].x, A[j][j].y};
+      df r = {0.f, 0.f};
+      if (tid == j) {
+        if (!(d.hi > 0.f) || !isfinite(d.hi)) s_fail = 1;
+        r = df_rsqrt(d);
+        const df l = df_mul(d, r);
+        A[j][j] = make_float2(l.hi, l.lo);
+        rp[j] = make_float2(r.hi, r.lo);
+      }
+      r = df_shfl(r, j);
+      if (tid > j) {
+        const df a = df_mul(df{A[tid][j].x, A[tid][j].y}, r);
+        A[tid][j] = make_float2(a.hi, a.lo);
       }
     }
-    __syncwarp();
-  }
-  // inverse: for t = 0..: X[t][c] scaled by 1/L_tt, then X[i][c] -= L[i][t] X[t][c]; lane c
-  // owns column c
-  for (int t = 0; t < kNB; ++t) {
-    // 1 / L_tt is the pivot's reciprocal square root kept from the factorisation
-    const df xt = df_mul(df{X[t][tid].x, X[t][tid].y}, df{rp[t].x, rp[t].y});
-    X[t][tid] = make_float2(xt.hi, xt.lo);
-    for (int i = t + 1; i < kNB; ++i) {
-      df x = {X[i][tid].x, X[i][tid].y};
-      df_fma(x, df_neg(df{A[i][t].x, A[i][t].y}), xt);
-      x = df_norm(x);
-      X[i][tid] = make_float2(x.hi, x.lo);
+    __syncthreads();
+    if (s_fail) break;
+    const int rem = kNB - j - 1;
+    for (int q = tid; q < rem * rem; q += kDiagThreads) {
+      const int i = j + 1 + q / rem, c = j + 1 + q % rem;
+      if (c <= i) {
+        df a = {A[i][c].x, A[i][c].y};
+        df_fma(a, df_neg(df{A[i][j].x, A[i][j].y}), df{A[c][j].x, A[c][j].y});
+        a = df_norm(a);
+        A[i][c] = make_float2(a.hi, a.lo);
+      }
     }
+    __syncthreads();
   }
-  __syncwarp();
+  if (s_fail) {
+    if (tid == 0) st->chol_fail = 1;
+    return;
+  }
+  // inverse: for t = 0..: row t of X scaled by 1/L_tt, then X[i][:] -= L[i][t] X[t][:]
+  for (int t = 0; t < kNB; ++t) {
+    if (tid < kNB) {
+      // 1 / L_tt is the pivot's reciprocal square root kept from the factorisation
+      const df x = df_mul(df{X[t][tid].x, X[t][tid].y}, df{rp[t].x, rp[t].y});
+      X[t][tid] = make_float2(x.hi, x.lo);
+    }
+    __syncthreads();
+    const int rem = kNB - t - 1;
+    for (int q = tid; q < rem * kNB; q += kDiagThreads) {
+      const int i = t + 1 + q / kNB, c = q % kNB;
+      df x = {X[i][c].x, X[i][c].y};
+      df_fma(x, df_neg(df{A[i][t].x, A[i][t].y}), df{X[t][c].x, X[t][c].y});
+      x = df_norm(x);
+      X[i][c] = make_float2(x.hi, x.lo);
+    }
+    __syncthreads();
+  }
   float2* Linv = Linv_all + (int64_t)kb * kNB * kNB;
   for (int q = tid; q < kNB * kNB; q += kDiagThreads) {
     const int r = q / kNB, c = q % kNB;
@@ -1706,6 +1714,14 @@ psfm_status fetch_solution(const Plan& p, const DevState* st, const double* dsol
   out->r_bad = h.r_bad;
   out->chi2_mean = h.chi2_mean;
   out->chi2_rms = h.chi2_rms;
+  out->kernel_sum = h.q_ksum;
+  out->mom_x = h.q_mx;
+  out->mom_y = h.q_my;
+  out->mom_xx = h.q_mxx;
+  out->mom_yy = h.q_myy;
+  out->mom_xy = h.q_mxy;
+  out->deconv_max = h.q_deconv;
+  out->quality_flags = h.q_flags;
   {
     const uint32_t k = h.median_key;
     const uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;

@@ -44,6 +44,10 @@ struct DevState {
   uint32_t sel_prefix;  // radix-select state
   int32_t sel_rank;
   int32_t sel_pad;
+  // quality diagnostics of the solution (Sec. 3.7), kernel realised at the image centre
+  int32_t q_flags;
+  int32_t q_pad;
+  double q_ksum, q_mx, q_my, q_mxx, q_myy, q_mxy, q_deconv;
 };
 
 // Host-side plan: everything derived from (shape, basis, config).

@@ -26,6 +26,8 @@ OP_SOLVE, OP_CONVOLVE, OP_SUBTRACT, OP_STACK = 1, 2, 3, 4
 NORM_SEPARATE, NORM_JOINT = 0, 1
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16X3, PREC_F32X2 = 0, 1, 2, 3, 4
 CAND_UNUSED, CAND_USED, CAND_REJECTED = 0, 1, 2
+(QUALITY_FEW_STAMPS, QUALITY_MEAN_DEV, QUALITY_RMS_DEV, QUALITY_MOMENT1, QUALITY_MOMENT2,
+ QUALITY_DECONV) = 1, 2, 4, 8, 16, 32
 MAX_GAUSS = 4
 
 
@@ -65,7 +67,10 @@ class psfm_solution(C.Structure):
                 ("cand_capacity", C.c_int32), ("cand", C.POINTER(psfm_stamp)),
                 ("cand_status", C.POINTER(C.c_int32)), ("chi2", C.POINTER(C.c_double)),
                 ("n_used", C.c_int32), ("n_iter", C.c_int32), ("r_bad", C.c_int32),
-                ("chi2_mean", C.c_double), ("chi2_rms", C.c_double), ("median", C.c_float)]
+                ("chi2_mean", C.c_double), ("chi2_rms", C.c_double), ("median", C.c_float),
+                ("kernel_sum", C.c_double), ("mom_x", C.c_double), ("mom_y", C.c_double),
+                ("mom_xx", C.c_double), ("mom_yy", C.c_double), ("mom_xy", C.c_double),
+                ("deconv_max", C.c_double), ("quality_flags", C.c_int32)]
 
 
 _lib = None
@@ -273,6 +278,14 @@ class Solution:
     @property
     def median(self):
         return self.c.median
+
+    def quality(self) -> dict:
+        """Quality diagnostics of the solution (Sec. 3.7) and the PSFM_QUALITY_* flags."""
+        c = self.c
+        return dict(n_used=c.n_used, chi2_mean=c.chi2_mean, chi2_rms=c.chi2_rms,
+                    kernel_sum=c.kernel_sum, mom_x=c.mom_x, mom_y=c.mom_y, mom_xx=c.mom_xx,
+                    mom_yy=c.mom_yy, mom_xy=c.mom_xy, deconv_max=c.deconv_max,
+                    flags=c.quality_flags)
 
     def candidates(self):
         n = self.c.n_regions * self.c.max_cand

@@ -124,6 +124,14 @@ def test_full_chip_batch_matches_oracle(dev, chip):
         assert de <= IMG_TOL_SIGMA, de
         assert ve <= VAR_RTOL, ve
         assert me == 0
+        # quality diagnostics against the oracle's solution and chi^2 statistics
+        used = g["chi2"][g["status"] == O.STATUS_USED]
+        oq = O.quality(chip["osol"], int(g["n_used"]), float(used.mean()), float(used.std()))
+        q = sol.quality()
+        for k in ("kernel_sum", "mom_x", "mom_y", "mom_xx", "mom_yy", "deconv_max"):
+            assert abs(q[k] - oq[k]) <= 1e-6 * max(1.0, abs(oq[k])), k
+        assert abs(q["chi2_mean"] - float(used.mean())) <= 1e-4 * float(used.mean())
+        assert q["flags"] == oq["flags"]
     # difference pseudo-matrix = (w1 P_conv + w2 delta) / (w1 + w2) (Sec. 4.4)
     Pc = O.pseudo_matrix(chip["osol"], chip["oc"])
     Pd = batch.cov[0].cpu().numpy()

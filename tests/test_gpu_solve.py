@@ -40,6 +40,12 @@ def _check_solution(sol, osol, ob, W, H):
     ke = kernel_rel_err(gsol, osol, pts)
     assert ke <= KERNEL_RTOL, ke
     assert sol.r_bad == O.r_bad(osol)
+    # quality diagnostics (Sec. 3.7) of the GPU solution, recomputed by the oracle
+    q = sol.quality()
+    oq = O.quality(gsol, sol.n_used, sol.chi2_mean, sol.chi2_rms)
+    for k in ("kernel_sum", "mom_x", "mom_y", "mom_xx", "mom_yy", "mom_xy", "deconv_max"):
+        assert abs(q[k] - oq[k]) <= 1e-10 * max(1.0, abs(oq[k])), k
+    assert q["flags"] == oq["flags"]
     return ke, coeff_rel_err(sol.coeff[:osol.a.size], osol.a.ravel())
 
 

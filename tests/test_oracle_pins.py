@@ -489,3 +489,40 @@ def test_per_pixel_forms_match_whole_image_forms():
             assert abs(O.variance_pixel(V, m, sol, 0xFF, x, y, 32, V2=V2) - Vimg[y, x]) <= \
                 1e-12 * Vimg[y, x]
             assert O.mask_pixel(m, sol, cfg, x, y, m2) == Mimg[y, x]
+
+
+# ---------------------------------------------------------------- quality (Sec. 3.7)
+
+def test_kernel_quality_closed_forms():
+    h = 10
+    u = np.arange(-h, h + 1, dtype=np.float64)
+    U, V = np.meshgrid(u, u)
+    # a normalised Gaussian: zero first moments, second moments sigma^2 (continuous limit),
+    # enclosed sum never above the total
+    sig = 1.5
+    G = np.exp(-(U * U + V * V) / (2 * sig * sig))
+    q = O.kernel_quality(3.0 * G / G.sum())
+    assert abs(q["kernel_sum"] - 3.0) < 1e-12
+    assert abs(q["mom_x"]) < 1e-14 and abs(q["mom_y"]) < 1e-14 and abs(q["mom_xy"]) < 1e-14
+    assert abs(q["mom_xx"] - sig * sig) < 1e-9 and abs(q["mom_yy"] - sig * sig) < 1e-9
+    assert 1.0 - 1e-9 < q["deconv_max"] <= 1.0
+    # a delta shifted by (2, -1): first moments (2, -1), no spread
+    D = np.zeros((2 * h + 1, 2 * h + 1))
+    D[h - 1, h + 2] = 1.0
+    q = O.kernel_quality(D)
+    assert (q["mom_x"], q["mom_y"], q["mom_xx"], q["mom_yy"]) == (2.0, -1.0, 0.0, 0.0)
+    # a sharpening kernel 2 delta - G (sum 1): negative second moments, central excess
+    S = -G / G.sum()
+    S[h, h] += 2.0
+    q = O.kernel_quality(S)
+    assert abs(q["mom_xx"] + sig * sig) < 1e-9
+    assert abs(q["deconv_max"] - (2.0 - G[h, h] / G.sum())) < 1e-12
+
+
+def test_quality_flags_follow_the_recommended_cuts():
+    sol = _fixed_solution(64, 64)
+    q = O.quality(sol, 10, 0.2, 0.1)
+    base = q["flags"]
+    assert O.quality(sol, 2, 0.2, 0.1)["flags"] == base | O.QUALITY_FEW_STAMPS
+    assert O.quality(sol, 10, 0.6, 0.1)["flags"] == base | O.QUALITY_MEAN_DEV
+    assert O.quality(sol, 10, 0.2, 0.31)["flags"] == base | O.QUALITY_RMS_DEV
