@@ -359,6 +359,23 @@ def run_stack(args, world, local):
     return 0
 
 
+def max_over_ranks(ms, world, device=None):
+    """Slowest rank's time of the timed region (every rank holds the same work: replicas)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(px_per_step, world, steps, ms):
+    """Whole-job Mpix/s: the pixels every rank processed over the slowest rank's time."""
+    return px_per_step * world * steps / 1e6 / (ms / 1e3)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -453,12 +470,8 @@ def main():
             launches = batch.kernel_count() * args.steps
         else:
             launches = P.psfm_launch_count() - l0
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    value = px_per_step * world * args.steps / 1e6 / (ms / 1e3)
+    ms = max_over_ranks(ms, world, dev)
+    value = job_throughput(px_per_step, world, args.steps, ms)
 
     # roofline of the dominant kernel, timed with the library's CUDA events on its stream in a
     # separate (non-graph, unshared) subtraction of chip 0 right after the timed region

@@ -261,6 +261,40 @@ psfm_status psfm_stack(int32_t n, const float* const* imgs, const float* const* 
                        double* cov_out, int32_t cov_out_w, psfm_solution* sols,
                        void* workspace, size_t ws_bytes, psfm_stream stream);
 
+/* PSF-homogenised stack with outlier rejection and the unconvolved companion stack (Sec. 5.1:
+ * outliers are identified once the inputs share a PSF, carried back to the unconvolved inputs
+ * by a matched filter, and the same rejection list serves a stack without convolution).
+ * Inputs as for psfm_stack, at most PSFM_STACK_FULL_MAX of them.
+ *   Pass 1: every input is matched to its target and convolved as in psfm_stack; the convolved
+ *   image, variance and mask of all inputs are kept in the workspace.
+ *   Outliers: at a pixel where at least 3 convolved inputs are usable (no badmask or CONV.BAD
+ *   bit), input i is an outlier when |I'_i - m| > clip_nsigma * sqrt(V'_i + soften_alpha |m|),
+ *   m the median of the usable convolved values there; n_rejected[i] (host, may be NULL)
+ *   counts them.
+ *   Rejection: input pixels within the CONV.BAD radius r_bad of input i's kernel (Chebyshev
+ *   distance) of one of its outliers get reject_bit (a bit outside badmask, conv_bad and
+ *   conv_poor) and count as masked from then on.
+ *   Pass 2: every input is convolved again with its pass-1 kernel and the rejected pixels
+ *   masked, then accumulated as in psfm_stack into out, out_var, out_mask, out_count (and
+ *   cov_out); the unconvolved inputs, without their badmask or rejected pixels, are
+ *   accumulated with the same pass-1 weights into uout, uout_var, uout_mask, uout_count.
+ * All output planes are device memory with `shape`.  Workspace:
+ * psfm_stack_full_workspace_size(n, shape, basis, cfg, max n_src) bytes, 256-byte aligned
+ * (it holds the n convolved inputs).  Synchronises `stream`. */
+#define PSFM_STACK_FULL_MAX 32
+size_t psfm_stack_full_workspace_size(int32_t n, psfm_shape shape, const psfm_basis_spec* basis,
+                                      const psfm_config* cfg, int32_t n_src_max);
+psfm_status psfm_stack_full(int32_t n, const float* const* imgs, const float* const* vars,
+                            const uint16_t* const* masks, psfm_shape shape,
+                            const double* const* src_xyf, const int32_t* n_src,
+                            double target_fwhm, const psfm_basis_spec* basis,
+                            const psfm_config* cfg, double clip_nsigma, uint16_t reject_bit,
+                            float* out, float* out_var, uint16_t* out_mask, int32_t* out_count,
+                            float* uout, float* uout_var, uint16_t* uout_mask,
+                            int32_t* uout_count, int32_t* n_rejected, double* cov_out,
+                            int32_t cov_out_w, psfm_solution* sols, void* workspace,
+                            size_t ws_bytes, psfm_stream stream);
+
 /* Batched subtraction (Sec. 3, Sec. 4 applied chip by chip; the batching itself has no
  * counterpart in the paper).  A batch is n chips, each with its own shape, basis (size, degrees,
  * spatial order) and buffers; the configuration is shared.  psfm_batch_create lays out one

@@ -27,6 +27,7 @@ tests in ``tests/test_oracle_*.py`` except where its docstring says "parity unpi
 from __future__ import annotations
 
 import math
+import warnings
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -886,3 +887,92 @@ def stack(warps, sources, target_fwhm, bases, cfg: Config):
     mout = np.where(cnt == 0, 1, 0).astype(np.uint16)
     P = combine_pseudo(Ps, pw)
     return img, vout, mout, cnt, P, sols
+
+
+STACK_REJECT = 1 << 13
+
+
+def stack_full(warps, sources, target_fwhm, bases, cfg: Config, clip_nsigma=5.0,
+               reject_bit=STACK_REJECT):
+    """PSF-homogenised stack with outlier rejection and the unconvolved companion stack
+    (Sec. 5.1).  Readings where the paper is silent:
+
+    * an outlier is a usable pixel of convolved input i, at a pixel where at least 3 inputs
+      are usable, whose deviation from the median m of the usable convolved inputs there
+      exceeds ``clip_nsigma`` times its error softened like the chi^2 of Sec. 3.6,
+      |I'_i - m| > n sqrt(V'_i + alpha |m|) with alpha = cfg.soften_alpha (the median, unlike
+      a mean, is not dragged by the outlier itself);
+    * the matched filter that carries the outlier mask back to the unconvolved input is the
+      CONV.BAD box of that input's kernel: an input pixel is rejected when an outlier lies
+      within Chebyshev distance r_bad of it (the pixels that dominate the outlier's value);
+    * rejected input pixels are masked (``reject_bit``) and the inputs convolved again with
+      their unchanged kernels; weights stay w_i = 1 / mean(V'_i) from the first pass;
+    * the unconvolved stack combines the original inputs with the same weights and the same
+      rejected pixels excluded.
+
+    Returns dict(conv=(I, V, mask, count), unconv=(I, V, mask, count), rejected=[outlier
+    pixels per input], sols=[...], pm=pseudo-matrix of the convolved stack)."""
+    H, W = warps[0]["image"].shape
+    T = render_target(W, H, sources, target_fwhm).astype(np.float32)
+    zero = np.zeros((H, W), np.float32)
+    zm = np.zeros((H, W), np.uint16)
+    sols, conv, wts = [], [], []
+    for wp, basis in zip(warps, bases):
+        sol = solve_kernel(wp["image"], T, wp["var"], zero, wp["mask"], zm, basis, cfg)
+        O = convolve_image(wp["image"], wp["mask"], sol, cfg.badmask)
+        Vp = variance_image(wp["var"], wp["mask"], sol, cfg.badmask, cfg.var_tile)
+        M = mask_image(wp["mask"], sol, cfg)
+        ok = (M.astype(np.int64) & (cfg.badmask | cfg.conv_bad)) == 0
+        sols.append(sol)
+        conv.append((O, Vp, ok))
+        wts.append(1.0 / mean_unmasked(Vp, M, cfg))
+    stackO = np.stack([np.where(ok, O, np.nan) for O, Vp, ok in conv])
+    nuse = np.sum(np.isfinite(stackO), axis=0)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore", RuntimeWarning)  # pixels with no usable input
+        med = np.nanmedian(np.where(nuse >= 3, stackO, np.nan), axis=0)
+    rejected, bad_in = [], []
+    for (O, Vp, ok), w, sol in zip(conv, wts, sols):
+        has = ok & (nuse >= 3)
+        m = np.where(has, med, 0.0)
+        out = has & (np.abs(O - m) > clip_nsigma * np.sqrt(Vp + cfg.soften_alpha * np.abs(m)))
+        rejected.append(int(out.sum()))
+        rb = r_bad(sol, cfg.bad_frac)
+        pad = np.zeros((H + 2 * rb, W + 2 * rb), bool)
+        pad[rb:rb + H, rb:rb + W] = out
+        grown = np.zeros((H, W), bool)
+        for dy in range(-rb, rb + 1):
+            for dx in range(-rb, rb + 1):
+                grown |= pad[rb + dy:rb + dy + H, rb + dx:rb + dx + W]
+        bad_in.append(grown)
+    cfg2 = Config(**{**cfg.__dict__, "badmask": cfg.badmask | reject_bit})
+    num = np.zeros((H, W)); den = np.zeros((H, W)); var = np.zeros((H, W))
+    cnt = np.zeros((H, W), np.int32)
+    unum = np.zeros((H, W)); uden = np.zeros((H, W)); uvar = np.zeros((H, W))
+    ucnt = np.zeros((H, W), np.int32)
+    for wp, sol, w, bad in zip(warps, sols, wts, bad_in):
+        m2 = np.where(bad, wp["mask"] | reject_bit, wp["mask"]).astype(np.uint16)
+        O = convolve_image(wp["image"], m2, sol, cfg2.badmask)
+        Vp = variance_image(wp["var"], m2, sol, cfg2.badmask, cfg.var_tile)
+        M = mask_image(m2, sol, cfg2)
+        ok = (M.astype(np.int64) & (cfg2.badmask | cfg.conv_bad)) == 0
+        num += np.where(ok, w * O, 0.0)
+        den += np.where(ok, w, 0.0)
+        var += np.where(ok, w * w * Vp, 0.0)
+        cnt += ok.astype(np.int32)
+        uok = (m2.astype(np.int64) & cfg2.badmask) == 0
+        I = np.asarray(wp["image"], np.float64)
+        Vin = np.asarray(wp["var"], np.float64)
+        unum += np.where(uok, w * I, 0.0)
+        uden += np.where(uok, w, 0.0)
+        uvar += np.where(uok, w * w * Vin, 0.0)
+        ucnt += uok.astype(np.int32)
+
+    def finish(nm, dn, vr, ct):
+        img = np.where(dn > 0, nm / np.where(dn > 0, dn, 1.0), 0.0)
+        v = np.where(dn > 0, vr / np.where(dn > 0, dn * dn, 1.0), 0.0)
+        return img, v, np.where(ct == 0, 1, 0).astype(np.uint16), ct
+
+    Ps = [pseudo_matrix(sol, cfg) for sol in sols]
+    return dict(conv=finish(num, den, var, cnt), unconv=finish(unum, uden, uvar, ucnt),
+                rejected=rejected, sols=sols, pm=combine_pseudo(Ps, wts), weights=wts)

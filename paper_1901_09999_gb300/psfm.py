@@ -450,6 +450,59 @@ def psfm_stack(imgs, vars_, masks, sources, target_fwhm, bases, cfg, want_cov=Tr
     return out, out_var, out_mask, out_count, cov, sols
 
 
+STACK_REJECT = 1 << 13
+
+
+def psfm_stack_full(imgs, vars_, masks, sources, target_fwhm, bases, cfg, clip_nsigma=5.0,
+                    reject_bit=STACK_REJECT, want_cov=True, workspace=None, stream=None):
+    """Stack with outlier rejection and the unconvolved companion stack (C: psfm_stack_full).
+
+    Returns dict(conv=(image, variance, mask, count), unconv=(image, variance, mask, count),
+    rejected=[outlier pixels per input], cov=pseudo-matrix or None, sols=[Solution])."""
+    torch = _torch()
+    lib = load()
+    vp, i32, P_ = C.c_void_p, C.c_int32, C.POINTER
+    lib.psfm_stack_full_workspace_size.argtypes = [i32, psfm_shape, P_(psfm_basis_spec),
+                                                   P_(psfm_config), i32]
+    lib.psfm_stack_full_workspace_size.restype = C.c_size_t
+    lib.psfm_stack_full.argtypes = [i32, P_(vp), P_(vp), P_(vp), psfm_shape, P_(P_(C.c_double)),
+                                    P_(i32), C.c_double, P_(psfm_basis_spec), P_(psfm_config),
+                                    C.c_double, C.c_uint16] + [vp] * 8 + [
+                                    P_(i32), vp, i32, P_(psfm_solution), vp, C.c_size_t, vp]
+    lib.psfm_stack_full.restype = i32
+    n = len(imgs)
+    shape = _shape_of(*imgs, *vars_, *masks)
+    dev = imgs[0].device
+    srcs = [np.ascontiguousarray(s_, np.float64) for s_ in sources]
+    nsrc = (C.c_int32 * n)(*[len(s_) for s_ in srcs])
+    sp = (P_(C.c_double) * n)(*[s_.ctypes.data_as(P_(C.c_double)) for s_ in srcs])
+    bs = (psfm_basis_spec * n)(*bases)
+    need = int(lib.psfm_stack_full_workspace_size(n, shape, bs, C.byref(cfg),
+                                                  max(len(s_) for s_ in srcs)))
+    if need == 0:
+        raise PsfmError(1, "psfm_stack_full_workspace_size")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    conv = (_like(imgs[0]), _like(imgs[0]), _like(masks[0]), _like(imgs[0], torch.int32))
+    unconv = (_like(imgs[0]), _like(imgs[0]), _like(masks[0]), _like(imgs[0], torch.int32))
+    ncov = max(cov_width(b, 1, 0) for b in bases)
+    cov = torch.empty((ncov, ncov), dtype=torch.float64, device=dev) if want_cov else None
+    sols = [Solution(basis_size(b) * spatial_size(b), _ncand(b, cfg, 0)) for b in bases]
+    csols = (psfm_solution * n)(*[s_.c for s_ in sols])
+    rej = (C.c_int32 * n)()
+    ptrs = lambda ts: (vp * n)(*[t.data_ptr() for t in ts])
+    st = lib.psfm_stack_full(n, ptrs(imgs), ptrs(vars_), ptrs(masks), shape, sp, nsrc,
+                             float(target_fwhm), bs, C.byref(cfg), float(clip_nsigma),
+                             int(reject_bit), *[_ptr(t) for t in conv], *[_ptr(t) for t in unconv],
+                             rej, _ptr(cov), ncov if want_cov else 0, csols, _ptr(workspace), need,
+                             _stream(stream))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_stack_full")
+    for s_, c in zip(sols, csols):
+        s_.c = c
+    return dict(conv=conv, unconv=unconv, rejected=list(rej), cov=cov, sols=sols)
+
+
 def psfm_gram(cols, weights, precision, stream=None):
     """Weighted Gram of column blocks (C: psfm_gram).  ``cols`` (n_blocks, n_cols, n_pix) and
     ``weights`` (n_blocks, n_pix) are contiguous float32 CUDA tensors; returns the

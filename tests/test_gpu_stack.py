@@ -86,3 +86,67 @@ def test_stack_single_input_equals_its_convolution(dev):
     g = host(img).astype(np.float64)
     assert np.all(np.abs(g[ok] - ref[ok]) <= IMG_TOL_SIGMA * np.sqrt(vref[ok]))
     assert np.allclose(host(var)[ok], vref[ok], rtol=VAR_RTOL)
+
+
+def _copies(n, spike=None):
+    warps, src = synth.skycell_warps(21, 1, 160, 80, gap_range=(60, 120), block_range=(8, 30),
+                                     masked_range=(0.02, 0.08))
+    out = []
+    for i in range(n):
+        w = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in warps[0].items()}
+        if spike is not None and i == spike[0]:
+            w["image"][spike[2], spike[1]] += spike[3]
+        out.append(w)
+    return out, src
+
+
+def _check_planes(got, exp, tol_sigma=IMG_TOL_SIGMA):
+    img, var, msk, cnt = [host(t) for t in got]
+    oimg, ovar, omsk, ocnt = exp
+    assert np.array_equal(cnt, ocnt)
+    assert np.array_equal(msk, omsk)
+    ok = ocnt > 0
+    assert np.all(np.abs(img[ok] - oimg[ok]) <= tol_sigma * np.sqrt(ovar[ok]))
+    assert np.allclose(var[ok], ovar[ok], rtol=VAR_RTOL, atol=0)
+
+
+@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_F32X2])
+def test_stack_full_spike_matches_oracle(dev, prec):
+    """Three copies of a warp, one with a planted spike: the spike's input is rejected around it
+    and only there, in both the convolved and the unconvolved stack, as in the oracle."""
+    x, y = 80, 80
+    warps, src = _copies(3, spike=(1, x, y, 20000.0))
+    b, c, ob, oc = specs((0.7, 1.5, 3.0), (2, 2, 2), 8, 0, badmask=synth.BADMASK, grid_nx=2,
+                         grid_ny=2, precision=prec)
+    tf = 1.15 * warps[0]["fwhm"]
+    r = P.psfm_stack_full([_put(w["image"], dev) for w in warps],
+                          [_put(w["var"], dev) for w in warps],
+                          [_put(w["mask"], dev) for w in warps], [src] * 3, tf, [b] * 3, c)
+    o = O.stack_full(warps, src, tf, [ob] * 3, oc)
+    assert r["rejected"] == o["rejected"]
+    assert r["rejected"][1] > 0 and r["rejected"][0] == 0 and r["rejected"][2] == 0
+    _check_planes(r["conv"], o["conv"])
+    _check_planes(r["unconv"], o["unconv"])
+    assert np.allclose(host(r["cov"]), o["pm"], rtol=0, atol=COV_DIFF_ATOL)
+
+
+def test_stack_full_uneven_warps_agree_with_oracle(dev):
+    """Uneven warps (different PSFs and masks): outlier decisions taken in FP32 on the GPU and
+    FP64 in the oracle may differ at pixels within rounding of the threshold, so the rejected
+    counts agree to 1 % and the stacks agree wherever the coverage counts agree (>= 99 %)."""
+    warps, src = _warps(7, 3, 320, 150)
+    b, c, ob, oc = specs((0.7, 1.5, 3.0), (4, 2, 2), 10, 1, badmask=synth.BADMASK, grid_nx=4,
+                         grid_ny=4, precision=P.PREC_F32X2)
+    tf = 1.15 * max(w["fwhm"] for w in warps)
+    r = P.psfm_stack_full([_put(w["image"], dev) for w in warps],
+                          [_put(w["var"], dev) for w in warps],
+                          [_put(w["mask"], dev) for w in warps], [src] * 3, tf, [b] * 3, c)
+    o = O.stack_full(warps, src, tf, [ob] * 3, oc)
+    for g_, e_ in zip(r["rejected"], o["rejected"]):
+        assert abs(g_ - e_) <= max(2, 0.01 * e_)
+    for key in ("conv", "unconv"):
+        img, var, msk, cnt = [host(t) for t in r[key]]
+        oimg, ovar, omsk, ocnt = o[key]
+        same = (cnt == ocnt) & (ocnt > 0)
+        assert same.sum() >= 0.99 * (ocnt > 0).sum()
+        assert np.all(np.abs(img[same] - oimg[same]) <= IMG_TOL_SIGMA * np.sqrt(ovar[same]))

@@ -526,3 +526,47 @@ def test_quality_flags_follow_the_recommended_cuts():
     assert O.quality(sol, 2, 0.2, 0.1)["flags"] == base | O.QUALITY_FEW_STAMPS
     assert O.quality(sol, 10, 0.6, 0.1)["flags"] == base | O.QUALITY_MEAN_DEV
     assert O.quality(sol, 10, 0.2, 0.31)["flags"] == base | O.QUALITY_RMS_DEV
+
+
+# ------------------------------------------- stacking with outlier rejection (Sec. 5.1)
+
+def _copies(n, spike=None):
+    warps, src = synth.skycell_warps(21, 1, 160, 80, gap_range=(60, 120), block_range=(8, 30),
+                                     masked_range=(0.02, 0.08))
+    out = []
+    for i in range(n):
+        w = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in warps[0].items()}
+        if spike is not None and i == spike[0]:
+            w["image"][spike[2], spike[1]] += spike[3]
+        out.append(w)
+    return out, src
+
+
+def test_stack_full_of_identical_inputs_rejects_nothing():
+    warps, src = _copies(3)
+    ob = O.Basis((0.7, 1.5, 3.0), (2, 2, 2), 8, 0)
+    oc = O.Config(grid_nx=2, grid_ny=2, badmask=synth.BADMASK)
+    tf = 1.15 * warps[0]["fwhm"]
+    r = O.stack_full(warps, src, tf, [ob] * 3, oc)
+    assert r["rejected"] == [0, 0, 0]
+    img, var, msk, cnt, _, _ = O.stack(warps, src, tf, [ob] * 3, oc)
+    assert np.array_equal(r["conv"][3], cnt) and np.array_equal(r["conv"][2], msk)
+    assert np.allclose(r["conv"][0], img, rtol=1e-13, atol=1e-9)
+    # unconvolved stack of equal inputs: the input itself where unmasked, variance / 3
+    ok = (warps[0]["mask"].astype(np.int64) & synth.BADMASK) == 0
+    uimg, uvar, _, ucnt = r["unconv"]
+    assert np.array_equal(ucnt, np.where(ok, 3, 0))
+    assert np.allclose(uimg[ok], warps[0]["image"][ok], rtol=1e-12)
+    assert np.allclose(uvar[ok], warps[0]["var"][ok].astype(np.float64) / 3.0, rtol=1e-12)
+
+
+def test_stack_full_rejects_a_planted_spike_in_its_input_only():
+    x, y, amp = 80, 80, 20000.0
+    warps, src = _copies(3, spike=(1, x, y, amp))
+    ob = O.Basis((0.7, 1.5, 3.0), (2, 2, 2), 8, 0)
+    oc = O.Config(grid_nx=2, grid_ny=2, badmask=synth.BADMASK)
+    r = O.stack_full(warps, src, 1.15 * warps[0]["fwhm"], [ob] * 3, oc)
+    assert r["rejected"][0] == 0 and r["rejected"][2] == 0 and r["rejected"][1] > 0
+    # the spiked input is out of both stacks around the spike; the others are equal there
+    assert r["conv"][3][y, x] == 2 and r["unconv"][3][y, x] == 2
+    assert abs(r["unconv"][0][y, x] - warps[0]["image"][y, x]) < 1e-9 * abs(warps[0]["image"][y, x])
