@@ -261,6 +261,25 @@ psfm_status psfm_stack(int32_t n, const float* const* imgs, const float* const* 
                        double* cov_out, int32_t cov_out_w, psfm_solution* sols,
                        void* workspace, size_t ws_bytes, psfm_stream stream);
 
+/* Integer binning by b (Sec. 4.3: a convolution with a constant kernel followed by a change
+ * of scale).  Output pixel (X, Y) covers the input block [bX, bX+b) x [bY, bY+b); partial
+ * blocks at the far edges are dropped, so out_shape must be (width / b, height / b) with any
+ * pitch >= its width.  out = sum of the block's pixels without `badmask` bits (flux kept),
+ * out_mask = OR of the block's masks, out_var = f * sum of those pixels' variances with
+ * f = (box * C * box)(0) / b^2 the covariance factor of the box (C = cov_in, the identity when
+ * NULL; cov_in_w odd).  cov_out (device, may be NULL) receives the box pseudo-matrix
+ * P(D) = sum_{|u| < b} (b - |u_x|)(b - |u_y|) C(D + u) sampled at lags that are multiples of b
+ * and normalised to centre 1, width psfm_bin_cov_width(cov_in_w, b).  Planes are device
+ * memory; workspace: PSFM_BIN_WORKSPACE bytes, 256-byte aligned.  Synchronises `stream` once
+ * (to read the factor). */
+#define PSFM_BIN_WORKSPACE 4096
+int32_t psfm_bin_cov_width(int32_t cov_in_w, int32_t b);
+psfm_status psfm_bin(const float* img, const float* var, const uint16_t* mask, psfm_shape shape,
+                     int32_t b, uint16_t badmask, const double* cov_in, int32_t cov_in_w,
+                     float* out, float* out_var, uint16_t* out_mask, psfm_shape out_shape,
+                     double* cov_out, int32_t cov_out_w, void* workspace, size_t ws_bytes,
+                     psfm_stream stream);
+
 /* PSF-homogenised stack with outlier rejection and the unconvolved companion stack (Sec. 5.1:
  * outliers are identified once the inputs share a PSF, carried back to the unconvolved inputs
  * by a matched filter, and the same rejection list serves a stack without convolution).

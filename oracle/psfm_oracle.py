@@ -28,7 +28,7 @@ from __future__ import annotations
 
 import math
 import warnings
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import numpy as np
 
@@ -79,6 +79,8 @@ class Config:
     conv_bad: int = CONV_BAD
     conv_poor: int = CONV_POOR
     max_cand: int = 8
+    dual: bool = False                 # convolve both images (c_i != 0, Eq. 2)
+    penalty: float = 1e-2              # lambda of the dual-kernel penalty scale (see below)
 
     def s(self, basis: Basis) -> int:
         return basis.h if self.stamp_half is None else self.stamp_half
@@ -296,6 +298,7 @@ class StampData:
     F2: float            # footprint sum of I2
     nfoot: int           # usable footprint pixels
     g: np.ndarray        # (N_s,) spatial factors at the stamp centre
+    C2: np.ndarray = None  # (P, N_b) basis-convolved masked science (dual kernel), else None
 
 
 def stamp_data(I1, I2, V1, V2, m1, m2, x, y, basis: Basis, cfg: Config, B=None) -> StampData:
@@ -334,7 +337,19 @@ def stamp_data(I1, I2, V1, V2, m1, m2, x, y, basis: Basis, cfg: Config, B=None) 
     F1 = float(np.sum(np.where(goodF, F, 0.0)))
     F2 = float(np.sum(np.where(goodF, I2F, 0.0)))
     g = spatial_values(x, y, W, H, basis.S)
-    return StampData(x, y, C, Rs, I2s, var, ok, F1, F2, int(goodF.sum()), g)
+    C2 = None
+    if cfg.dual:
+        # the same basis applied to the science image, its masked pixels zeroed (Eq. 2 with
+        # c_i != 0: the kernel terms g_i k_i (x) I2 join the design vector)
+        bad2 = (m2.astype(np.int64) & cfg.badmask) != 0
+        F2m = _get(np.where(bad2, 0.0, I2.astype(np.float64)), x - s - h, y - s - h, n)
+        Pm2 = np.empty((P, w * w))
+        for v in range(-h, h + 1):
+            for u in range(-h, h + 1):
+                t = (v + h) * w + (u + h)
+                Pm2[:, t] = F2m[h - v:h - v + 2 * s + 1, h - u:h - u + 2 * s + 1].ravel()
+        C2 = Pm2 @ B.reshape(B.shape[0], -1).T
+    return StampData(x, y, C, Rs, I2s, var, ok, F1, F2, int(goodF.sum()), g, C2)
 
 
 def solve_normalisation(stamps):
@@ -365,11 +380,43 @@ def solve_spd(M, v):
 
 def design_rows(st: StampData, n_s: int):
     """Rows of the concatenated design vector (Eq. 4) for the kernel terms of one stamp:
-    A[p, k * N_s + s] = g_s(stamp centre) C[p, k]."""
-    return (st.C[:, :, None] * st.g[None, None, :]).reshape(st.C.shape[0], -1)
+    A[p, k * N_s + s] = g_s(stamp centre) C[p, k]; with the dual kernel the terms applied to
+    I2 follow, A[p, (N_b + k) * N_s + s] = g_s C2[p, k] (the c_i of Eq. 2)."""
+    A = (st.C[:, :, None] * st.g[None, None, :]).reshape(st.C.shape[0], -1)
+    if st.C2 is not None:
+        A2 = (st.C2[:, :, None] * st.g[None, None, :]).reshape(st.C2.shape[0], -1)
+        A = np.concatenate([A, A2], 1)
+    return A
 
 
-def normal_equations(stamps, basis: Basis, mode: str, b0=None, d0=None):
+def penalty_terms(basis: Basis):
+    """p_k = sum_{u,v} (u^2 + v^2)^2 k_k(u, v)^2 for each basis kernel (the penalty function of
+    Yuan & Akerlof adopted in Sec. 2, before the scale Phi)."""
+    B, _, _ = basis_kernels(basis)
+    h = basis.h
+    u = np.arange(-h, h + 1, dtype=np.float64)
+    U, V = np.meshgrid(u, u)
+    r4 = (U * U + V * V) ** 2
+    return np.array([float(np.sum(r4 * Bk * Bk)) for Bk in B])
+
+
+def add_penalty(M, basis: Basis, lam, offset=0):
+    """Adds Phi p_i to the diagonal of the kernel unknowns (b_i and c_i; Eq. 5), each spatial
+    term of a basis kernel taking that kernel's p_k.  Reading of Phi ("neither negligible nor
+    dominant", Sec. 2): Phi = lam * sum_i M_ii / sum_i p_i over those unknowns, so that the
+    penalty adds lam times the diagonal's total."""
+    n_s = len(spatial_terms(basis.S))
+    pk = penalty_terms(basis)
+    n = 2 * len(pk) * n_s
+    p = np.tile(np.repeat(pk, n_s), 2)
+    idx = np.arange(offset, offset + n)
+    phi = lam * float(np.trace(M[np.ix_(idx, idx)])) / float(p.sum())
+    M = M.copy()
+    M[idx, idx] += phi * p
+    return M
+
+
+def normal_equations(stamps, basis: Basis, mode: str, b0=None, d0=None, lam=0.0):
     """M and v of Eq. 5-6 with sigma^2 = V1 + V2, summed over the stamp pixels.
 
     mode "separate": unknowns are the kernel terms only, target I2 - b0 R - d0.
@@ -389,6 +436,8 @@ def normal_equations(stamps, basis: Basis, mode: str, b0=None, d0=None):
         vi = A.T @ (wgt * y)
         M = Mi if M is None else M + Mi
         v = vi if v is None else v + vi
+    if stamps and stamps[0].C2 is not None:
+        M = add_penalty(M, basis, lam, 1 if mode == "joint" else 0)
     return M, v
 
 
@@ -408,11 +457,18 @@ class Solution:
     n_iter: int = 0
     n_used: int = 0
     history: list = field(default_factory=list)
+    dual: bool = False           # coeff holds (b terms, c terms, d0)
 
     @property
     def a(self):
         nb = len(basis_terms(self.basis))
         return self.coeff[:nb * len(spatial_terms(self.basis.S))].reshape(nb, -1)
+
+    @property
+    def c(self):
+        """Coefficients of the terms applied to I2 (dual kernel), (N_b, N_s)."""
+        nb, ns = len(basis_terms(self.basis)), len(spatial_terms(self.basis.S))
+        return self.coeff[nb * ns:2 * nb * ns].reshape(nb, -1)
 
 
 def stamp_model(st: StampData, sol_b0, a_flat, d0, n_s):
@@ -431,12 +487,13 @@ def stamp_chi2(st: StampData, b0, a_flat, d0, n_s, alpha):
 def solve_from_stamps(stamps, basis: Basis, cfg: Config):
     """One least-squares solve over a set of stamps; returns (b0, coeff, d0)."""
     n_s = len(spatial_terms(basis.S))
+    lam = cfg.penalty if cfg.dual else 0.0
     if cfg.norm_mode == "joint":
-        M, v = normal_equations(stamps, basis, "joint")
+        M, v = normal_equations(stamps, basis, "joint", lam=lam)
         a = solve_spd(M, v)
         return float(a[0]), a[1:-1], float(a[-1])
     b0, d0 = solve_normalisation(stamps)
-    M, v = normal_equations(stamps, basis, "separate", b0, d0)
+    M, v = normal_equations(stamps, basis, "separate", b0, d0, lam)
     a = solve_spd(M, v)
     return b0, a, d0
 
@@ -496,7 +553,7 @@ def solve_kernel(I1, I2, V1, V2, m1, m2, basis: Basis, cfg: Config, cand=None) -
         status[r, j] = STATUS_USED
     coeff = np.concatenate([a, [d0]])
     return Solution(b0, coeff, d0, basis, W, H, cand, status, chi2, mu, sd, n_iter, len(active),
-                    history)
+                    history, cfg.dual)
 
 
 # ----------------------------------------------------------------------------------------
@@ -514,15 +571,28 @@ def realise_kernel(sol: Solution, x, y):
     return K
 
 
+def realise_kernel2(sol: Solution, x, y):
+    """Dual kernel (Sec. 2): K2 = delta - sum_k (sum_s c_{k,s} g_s(x, y)) B_k, the kernel the
+    difference applies to I2, so that D = K2 (x) I2 - K1 (x) I1 - d0."""
+    B, _, _ = basis_kernels(sol.basis)
+    g = spatial_values(x, y, sol.W, sol.H, sol.basis.S)
+    K = -np.tensordot(sol.c @ g, B, axes=(0, 0))
+    h = sol.basis.h
+    K[h, h] += 1.0
+    return K
+
+
 def masked_ref(I1, m1, badmask):
     return np.where((m1.astype(np.int64) & badmask) != 0, 0.0, np.asarray(I1, np.float64))
 
 
-def convolve_image(I1, m1, sol: Solution, badmask, I2=None):
+def convolve_image(I1, m1, sol: Solution, badmask, I2=None, m2=None):
     """O(x, y) = sum_{u,v} K_{x,y}(u, v) R(x-u, y-v) + d0 over the whole image, R = I1 with
     masked pixels zeroed, K_{x,y} the kernel realised at the output pixel.  By linearity in
     the spatial factors this is sum_s g_s(x, y) (K_s (x) R)(x, y) with K_s = sum_k a_{k,s} B_k
-    (plus b0 delta for the constant term).  With ``I2`` returns the difference I2 - O."""
+    (plus b0 delta for the constant term).  With ``I2`` returns the difference I2 - O.  For a
+    dual-kernel solution the terms sum_k c_k(x, y) B_k (x) R2 are added to O, R2 = I2 with the
+    pixels masked in ``m2`` zeroed (Eq. 2), and the difference is returned."""
     B, _, _ = basis_kernels(sol.basis)
     H, W = I1.shape
     R = masked_ref(I1, m1, badmask)
@@ -536,6 +606,10 @@ def convolve_image(I1, m1, sol: Solution, badmask, I2=None):
             Ks = Ks.copy()
             Ks[h, h] += sol.b0
         out += g[si] * direct_conv2d(R, Ks)
+    if sol.dual:
+        R2 = masked_ref(I2, m2, badmask)
+        for si in range(g.shape[0]):
+            out += g[si] * direct_conv2d(R2, np.tensordot(sol.c[:, si], B, axes=(0, 0)))
     if I2 is not None:
         return np.asarray(I2, np.float64) - out
     return out
@@ -553,11 +627,18 @@ def _masked_window(img, m, badmask, x, y, h):
     return out
 
 
-def convolve_pixel(I1, m1, sol: Solution, badmask, x, y):
-    """Eq. 12 at one output pixel with the kernel realised there (plus d0)."""
+def convolve_pixel(I1, m1, sol: Solution, badmask, x, y, I2=None, m2=None):
+    """Eq. 12 at one output pixel with the kernel realised there (plus d0); for a dual-kernel
+    solution plus the terms applied to I2 (masked by m2)."""
     h = sol.basis.h
     R = _masked_window(I1, m1, badmask, x, y, h)
-    return conv_pixel(R, realise_kernel(sol, x, y), h, h) + sol.d0
+    o = conv_pixel(R, realise_kernel(sol, x, y), h, h) + sol.d0
+    if sol.dual:
+        R2 = _masked_window(I2, m2, badmask, x, y, h)
+        Kc = np.zeros_like(R2) - realise_kernel2(sol, x, y)
+        Kc[h, h] += 1.0
+        o += conv_pixel(R2, Kc, h, h)
+    return o
 
 
 def tile_centres(n, tile):
@@ -611,7 +692,7 @@ def covariance_factor(K, C_in):
     return tot / float(np.sum(K * K))
 
 
-def variance_image(V1, m1, sol: Solution, badmask, tile=64, C_in=None, V2=None):
+def variance_image(V1, m1, sol: Solution, badmask, tile=64, C_in=None, V2=None, m2=None):
     """V'(x, y) = f_t sum_{u,v} K_t(u, v)^2 V1(x-u, y-v) (Eq. 13), K_t realised at the centre
     of the fixed tile t (Sec. 4.4: a constant kernel per patch), f_t the covariance factor of
     K_t (1 for white input).  With ``V2`` returns V2 + V' (Sec. 4.4: variances of a difference
@@ -636,12 +717,27 @@ def variance_image(V1, m1, sol: Solution, badmask, tile=64, C_in=None, V2=None):
                 for u in range(-h, h + 1):
                     acc += K2[v + h, u + h] * sub[h - v:h - v + yb - ya, h - u:h - u + xb - xa]
             out[ya:yb, xa:xb] = f * acc
+    if sol.dual:
+        # Var(K2 (x) I2) with K2 = delta - sum c_k B_k per tile, the masked pixels of I2
+        # contributing zero (white inputs)
+        V2m = masked_ref(V2, m2, badmask)
+        for ty in range(len(ys0)):
+            for tx in range(len(xs0)):
+                K2 = realise_kernel2(sol, xc[tx], yc[ty]) ** 2
+                ya, yb, xa, xb = ys0[ty], ys1[ty], xs0[tx], xs1[tx]
+                sub = _get(V2m, int(xa) - h, int(ya) - h, max(yb - ya, xb - xa) + 2 * h)
+                acc = np.zeros((yb - ya, xb - xa))
+                for v in range(-h, h + 1):
+                    for u in range(-h, h + 1):
+                        acc += K2[v + h, u + h] * sub[h - v:h - v + yb - ya, h - u:h - u + xb - xa]
+                out[ya:yb, xa:xb] += acc
+        return out
     if V2 is not None:
         out = out + np.asarray(V2, np.float64)
     return out
 
 
-def variance_pixel(V1, m1, sol: Solution, badmask, x, y, tile=64, C_in=None, V2=None):
+def variance_pixel(V1, m1, sol: Solution, badmask, x, y, tile=64, C_in=None, V2=None, m2=None):
     """Eq. 13 at one output pixel: f_t sum_{u,v} K_t(u, v)^2 V1(x-u, y-v) with K_t realised at
     the centre of the fixed tile that contains (x, y) (same tiles as ``variance_image``)."""
     H, W = V1.shape
@@ -653,16 +749,20 @@ def variance_pixel(V1, m1, sol: Solution, badmask, x, y, tile=64, C_in=None, V2=
     f = 1.0 if C_in is None else covariance_factor(K, C_in)
     h = sol.basis.h
     v = f * conv_pixel(_masked_window(V1, m1, badmask, x, y, h), K * K, h, h)
+    if sol.dual:
+        K2 = realise_kernel2(sol, xc, yc)
+        return v + conv_pixel(_masked_window(V2, m2, badmask, x, y, h), K2 * K2, h, h)
     if V2 is not None:
         v += float(V2[y, x])
     return v
 
 
-def r_bad(sol: Solution, bad_frac=0.2):
+def r_bad(sol: Solution, bad_frac=0.2, second=False):
     """Box radius of CONV.BAD (Sec. 3.4): smallest r in [0, h] such that the sum of K^2 outside
     the box max(|u|, |v|) <= r is at most ``bad_frac`` of the total, K realised at the image
-    centre."""
-    K = realise_kernel(sol, (sol.W - 1) / 2.0, (sol.H - 1) / 2.0)
+    centre (``second``: the dual kernel K2 applied to I2)."""
+    realise = realise_kernel2 if second else realise_kernel
+    K = realise(sol, (sol.W - 1) / 2.0, (sol.H - 1) / 2.0)
     h = sol.basis.h
     K2 = K * K
     tot = float(K2.sum())
@@ -740,6 +840,13 @@ def mask_image(m1, sol: Solution, cfg: Config, m2=None, rb=None):
 
     nb = near(rb)
     npoor = near(h)
+    if sol.dual and m2 is not None:
+        # both images are convolved: masked pixels of I2 spread through K2 the same way
+        bad = (m2.astype(np.int64) & cfg.badmask) != 0
+        padded = np.ones((H + 2 * h, W + 2 * h), bool)
+        padded[h:h + H, h:h + W] = bad
+        nb = nb | near(r_bad(sol, cfg.bad_frac, second=True))
+        npoor = npoor | near(h)
     out = m1.astype(np.int64)
     if m2 is not None:
         out = out | m2.astype(np.int64)
@@ -757,13 +864,19 @@ def mask_pixel(m1, sol: Solution, cfg: Config, x, y, m2=None, rb=None):
     if rb is None:
         rb = r_bad(sol, cfg.bad_frac)
     near_bad = near_poor = False
+    rb2 = r_bad(sol, cfg.bad_frac, second=True) if (sol.dual and m2 is not None) else -1
     for dy in range(-h, h + 1):
         for dx in range(-h, h + 1):
             yy, xx = y + dy, x + dx
-            masked = not (0 <= yy < H and 0 <= xx < W) or (int(m1[yy, xx]) & cfg.badmask) != 0
+            off = not (0 <= yy < H and 0 <= xx < W)
+            masked = off or (int(m1[yy, xx]) & cfg.badmask) != 0
             if masked:
                 near_poor = True
                 if max(abs(dx), abs(dy)) <= rb:
+                    near_bad = True
+            if rb2 >= 0 and (off or (int(m2[yy, xx]) & cfg.badmask) != 0):
+                near_poor = True
+                if max(abs(dx), abs(dy)) <= rb2:
                     near_bad = True
     out = int(m1[y, x])
     if m2 is not None:
@@ -775,7 +888,7 @@ def mask_pixel(m1, sol: Solution, cfg: Config, x, y, m2=None, rb=None):
     return out
 
 
-def pseudo_matrix(sol: Solution, cfg: Config, C_in=None):
+def pseudo_matrix(sol: Solution, cfg: Config, C_in=None, second=False):
     """Average covariance pseudo-matrix of the convolved image (Sec. 4.4): the mean over a
     cov_grid x cov_grid sample of kernels, at ((i + 1/2) W / n, (j + 1/2) H / n), of
     pseudo_conv(K, C_in) / sum K^2, divided by its central value (the covariance factor has
@@ -784,9 +897,10 @@ def pseudo_matrix(sol: Solution, cfg: Config, C_in=None):
         C_in = np.ones((1, 1))
     n = cfg.cov_grid
     acc = None
+    realise = realise_kernel2 if second else realise_kernel
     for j in range(n):
         for i in range(n):
-            K = realise_kernel(sol, (i + 0.5) * sol.W / n, (j + 0.5) * sol.H / n)
+            K = realise(sol, (i + 0.5) * sol.W / n, (j + 0.5) * sol.H / n)
             P = pseudo_conv(K, C_in) / float(np.sum(K * K))
             acc = P if acc is None else acc + P
     acc /= n * n
@@ -818,6 +932,17 @@ def mean_unmasked(V, mask, cfg: Config):
 def subtract(I1, I2, V1, V2, m1, m2, sol: Solution, cfg: Config, C1=None, C2=None):
     """Difference image D = I2 - (K (x) I1 + d0), its variance V2 + V', mask and pseudo-matrix
     (Sec. 4.4: variances sum; pseudo-matrices averaged with the mean variances as weights)."""
+    if sol.dual:
+        # D = K2 (x) I2 - K1 (x) I1 - d0 (Eq. 2): two convolved parts with independent noise;
+        # their pseudo-matrices are averaged with the mean variances as weights (Sec. 4.4)
+        D = convolve_image(I1, m1, sol, cfg.badmask, I2, m2)
+        M = mask_image(m1, sol, cfg, m2)
+        V1p = variance_image(V1, m1, replace(sol, dual=False), cfg.badmask, cfg.var_tile)
+        Vd = variance_image(V1, m1, sol, cfg.badmask, cfg.var_tile, V2=V2, m2=m2)
+        w1, w2 = mean_unmasked(V1p, M, cfg), mean_unmasked(Vd - V1p, M, cfg)
+        P = combine_pseudo([pseudo_matrix(sol, cfg), pseudo_matrix(sol, cfg, second=True)],
+                           [w1, w2])
+        return D, Vd, M, P
     D = convolve_image(I1, m1, sol, cfg.badmask, I2)
     Vp = variance_image(V1, m1, sol, cfg.badmask, cfg.var_tile, C1)
     M = mask_image(m1, sol, cfg, m2)
@@ -976,3 +1101,44 @@ def stack_full(warps, sources, target_fwhm, bases, cfg: Config, clip_nsigma=5.0,
     Ps = [pseudo_matrix(sol, cfg) for sol in sols]
     return dict(conv=finish(num, den, var, cnt), unconv=finish(unum, uden, uvar, ucnt),
                 rejected=rejected, sols=sols, pm=combine_pseudo(Ps, wts), weights=wts)
+
+
+# ----------------------------------------------------------------------------------------
+# Binning (Sec. 4.3: binning as a box convolution followed by a change of scale)
+# ----------------------------------------------------------------------------------------
+
+def box_pseudo(C_in, b):
+    """Pseudo-matrix of a b x b box sum of noise with pseudo-matrix C_in (unnormalised):
+    pseudo_conv with the box kernel of ones (Eq. 10-11 written for the box)."""
+    return pseudo_conv(np.ones((b, b)), C_in)
+
+
+def bin_image(img, var, mask, b, badmask, C_in=None):
+    """Integer binning by b (Sec. 4.3).  Output pixel (X, Y) covers input pixels
+    [bX, bX + b) x [bY, bY + b) (partial blocks at the far edges are dropped).  Readings: the
+    binned image is the sum of the block's unmasked pixels (flux kept); its mask the OR of the
+    block's masks; its variance the covariance factor of the box times the sum of the block's
+    unmasked variances, f = (box * C_in * box)(0) / b^2, like the per-patch factor of a
+    convolution (Sec. 4.4); the binned pseudo-matrix is the box pseudo-matrix sampled at lags
+    that are multiples of b and normalised to centre 1.  Returns (image, variance, mask,
+    pseudo-matrix)."""
+    if C_in is None:
+        C_in = np.ones((1, 1))
+    H, W = img.shape
+    Hb, Wb = H // b, W // b
+    ok = (mask.astype(np.int64) & badmask) == 0
+    I = np.where(ok, np.asarray(img, np.float64), 0.0)[:Hb * b, :Wb * b]
+    V = np.where(ok, np.asarray(var, np.float64), 0.0)[:Hb * b, :Wb * b]
+    M = mask.astype(np.int64)[:Hb * b, :Wb * b]
+    Ib = I.reshape(Hb, b, Wb, b).sum(axis=(1, 3))
+    Vb = V.reshape(Hb, b, Wb, b).sum(axis=(1, 3))
+    Mb = np.zeros((Hb, Wb), np.int64)
+    for dy in range(b):
+        for dx in range(b):
+            Mb |= M[dy::b, dx::b]
+    Pbox = box_pseudo(C_in, b)
+    c = (Pbox.shape[0] - 1) // 2
+    f = Pbox[c, c] / (b * b)
+    r = c // b
+    Pb = Pbox[c - r * b:c + r * b + 1:b, c - r * b:c + r * b + 1:b]
+    return Ib, f * Vb, Mb.astype(np.uint16), Pb / Pb[r, r]

@@ -351,32 +351,38 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
   float* Al = Ah + ncr * kGramLd;
   float* Bh = Al + ncr * kGramLd;                                  // w * A
   float* Bl = Bh + ncr * kGramLd;
-  float* wh = Bl + ncr * kGramLd;                                  // [chunk] weights
-  float* wl = wh + kGramChunk;
+  // weights of every pixel this block takes, all computed up front: [chunk t][64]
+  const int nchunk = (P.P + kGramChunk - 1) / kGramChunk;
+  const int nch = (nchunk - split + kGramSplit - 1) / kGramSplit;
+  float* wh = Bl + ncr * kGramLd;
+  float* wl = wh + nch * kGramChunk;
   for (int i = tid; i < nsl * npair * 16; i += kGramThreads) acc[i] = make_float2(0.f, 0.f);
-  const float2* Cr = reinterpret_cast<const float2*>(P.C) + (int64_t)r * Nb * P.P;
-  for (int base = split * kGramChunk; base < P.P; base += kGramSplit * kGramChunk) {
-    __syncthreads();
-    if (tid < kGramChunk) {
-      const int pix = base + tid;
-      df wv = {0.f, 0.f};
-      if (pix < P.P) {
-        const int py = pix / P.sw, px = pix - py * P.sw;
-        const int gx = cx - P.s + px, gy = cy - P.s + py;
-        if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
-          const int64_t o = (int64_t)gy * P.g.pitch + gx;
-          if (!((P.m1[o] | P.m2[o]) & P.badmask)) {
-            const float a = P.i1[o], b = P.i2[o], vv = P.v1[o] + P.v2[o];
-            const double wd = 1.0 / ((double)P.v1[o] + (double)P.v2[o]);
-            if (!isfinite(a) || !isfinite(b) || !isfinite(vv) || !isfinite(wd))
-              raise_error(P.st, PSFM_ERR_NONFINITE);
-            wv = df_split(wd);
-          }
+  for (int i = tid; i < nch * kGramChunk; i += kGramThreads) {
+    const int t = i / kGramChunk;
+    const int pix = (split + t * kGramSplit) * kGramChunk + (i - t * kGramChunk);
+    df wv = {0.f, 0.f};
+    if (pix < P.P) {
+      const int py = pix / P.sw, px = pix - py * P.sw;
+      const int gx = cx - P.s + px, gy = cy - P.s + py;
+      if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
+        const int64_t o = (int64_t)gy * P.g.pitch + gx;
+        if (!((P.m1[o] | P.m2[o]) & P.badmask)) {
+          const float a = P.i1[o], b = P.i2[o], vv = P.v1[o] + P.v2[o];
+          const double wd = 1.0 / ((double)P.v1[o] + (double)P.v2[o]);
+          if (!isfinite(a) || !isfinite(b) || !isfinite(vv) || !isfinite(wd))
+            raise_error(P.st, PSFM_ERR_NONFINITE);
+          wv = df_split(wd);
         }
       }
-      wh[tid] = wv.hi;
-      wl[tid] = wv.lo;
     }
+    wh[i] = wv.hi;
+    wl[i] = wv.lo;
+  }
+  const float2* Cr = reinterpret_cast<const float2*>(P.C) + (int64_t)r * Nb * P.P;
+  for (int t = 0; t < nch; ++t) {
+    const int base = (split + t * kGramSplit) * kGramChunk;
+    const float* wht = wh + t * kGramChunk;
+    const float* wlt = wl + t * kGramChunk;
     __syncthreads();
     for (int i = tid; i < ncr * kGramChunk; i += kGramThreads) {
       const int c = i / kGramChunk, j = i - c * kGramChunk, pix = base + j;
@@ -396,7 +402,7 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
           }
         }
       }
-      const df b = df_mul(df{wh[j], wl[j]}, v);
+      const df b = df_mul(df{wht[j], wlt[j]}, v);
       Ah[c * kGramLd + j] = v.hi;
       Al[c * kGramLd + j] = v.lo;
       Bh[c * kGramLd + j] = b.hi;
@@ -426,13 +432,15 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
 #pragma unroll
           for (int f = 0; f < 4; ++f) df_fma(s[e * 4 + f], a[e], b[f]);
       }
-      float2* ac = acc + ((size_t)sl * npair + pr) * 16;
+      // accumulators laid out [slice][entry][pair]: the lanes of a warp (consecutive pairs)
+      // touch consecutive words
+      float2* ac = acc + (size_t)sl * 16 * npair + pr;
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
-        df t = {ac[e].x, ac[e].y};
-        df_acc(t, s[e].hi, s[e].lo);
-        t = df_norm(t);
-        ac[e] = make_float2(t.hi, t.lo);
+        df u = {ac[e * npair].x, ac[e * npair].y};
+        df_acc(u, s[e].hi, s[e].lo);
+        u = df_norm(u);
+        ac[e * npair] = make_float2(u.hi, u.lo);
       }
     }
   }
@@ -442,7 +450,7 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
     const int pq = q / 16, e = (q / 4) % 4, f = q % 4;
     double v = 0.0;
     for (int k = 0; k < nsl; ++k) {
-      const float2 a = acc[((size_t)k * npair + pq) * 16 + e * 4 + f];
+      const float2 a = acc[((size_t)k * 16 + e * 4 + f) * npair + pq];
       v += (double)a.x + (double)a.y;
     }
     int bi2 = 0, rem2 = pq;
@@ -1267,6 +1275,8 @@ __device__ __forceinline__ void basis_model4(const double* ak, const float2*, co
 __device__ __forceinline__ void basis_model4(const double*, const float2* akf, const float2* C,
                                              int Nb, int P, const int pix[4], double m[4]) {
   df acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  // unrolled so that the loads of several terms are in flight together
+#pragma unroll 8
   for (int k = 0; k < Nb; ++k) {
     const df a = {akf[k].x, akf[k].y};
     float2 c[4];
@@ -1580,7 +1590,9 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
     sm_design = sizeof(float) * ((size_t)p.foot * p.foot + 2 * (size_t)p.foot * p.sw +
                                  2 * (size_t)(p.dmax + 1) * p.w);
     const int nsl = kGramThreads / npair > 1 ? kGramThreads / npair : 1;
-    sm_gram = sizeof(float2) * nsl * npair * 16 + sizeof(float) * (4 * nblk * 4 * kGramLd + 2 * kGramChunk);
+    const int maxch = ((p.P + kGramChunk - 1) / kGramChunk + kGramSplit - 1) / kGramSplit;
+    sm_gram = sizeof(float2) * nsl * npair * 16 +
+              sizeof(float) * (4 * nblk * 4 * kGramLd + 2 * maxch * kGramChunk);
   }
   if (sm_design > 200 * 1024 || sm_gram > 200 * 1024) return PSFM_ERR_UNSUPPORTED;
   // TF32 / BF16X3: FP32 design blocks, the Gram on the tensor cores (k_gram_tc.cu)

@@ -450,6 +450,36 @@ def psfm_stack(imgs, vars_, masks, sources, target_fwhm, bases, cfg, want_cov=Tr
     return out, out_var, out_mask, out_count, cov, sols
 
 
+def psfm_bin(img, var, mask, b, badmask, cov_in=None, want_cov=True, stream=None):
+    """Integer binning by b with variance, mask and pseudo-matrix (C: psfm_bin).  Returns
+    (image, variance, mask, pseudo-matrix or None) at (H // b, W // b)."""
+    torch = _torch()
+    lib = load()
+    vp, i32 = C.c_void_p, C.c_int32
+    lib.psfm_bin_cov_width.argtypes = [i32, i32]
+    lib.psfm_bin_cov_width.restype = i32
+    lib.psfm_bin.argtypes = [vp, vp, vp, psfm_shape, i32, C.c_uint16, vp, i32, vp, vp, vp,
+                             psfm_shape, vp, i32, vp, C.c_size_t, vp]
+    lib.psfm_bin.restype = i32
+    shape = _shape_of(img, var, mask)
+    H, W = img.shape
+    Hb, Wb = H // b, W // b
+    out = torch.empty((Hb, Wb), dtype=torch.float32, device=img.device)
+    out_var = torch.empty_like(out)
+    out_mask = torch.empty((Hb, Wb), dtype=mask.dtype, device=img.device)
+    cw = cov_in.shape[0] if cov_in is not None else 1
+    nw = int(lib.psfm_bin_cov_width(cw, b))
+    cov = torch.empty((nw, nw), dtype=torch.float64, device=img.device) if want_cov else None
+    ws = torch.empty(4096, dtype=torch.uint8, device=img.device)
+    st = lib.psfm_bin(_ptr(img), _ptr(var), _ptr(mask), shape, int(b), int(badmask),
+                      _ptr(cov_in), cw, _ptr(out), _ptr(out_var), _ptr(out_mask),
+                      psfm_shape(Wb, Hb, Wb), _ptr(cov), nw if want_cov else 0, _ptr(ws), 4096,
+                      _stream(stream))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_bin")
+    return out, out_var, out_mask, cov
+
+
 STACK_REJECT = 1 << 13
 
 

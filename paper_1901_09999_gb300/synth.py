@@ -156,6 +156,30 @@ def small_gaussian_field(seed: int = 1, size: int = 512, n_stars: int = 200,
                       stars=np.stack([xs, ys, fl], 1)))
 
 
+def elongated_pair(seed: int = 3, size: int = 256, n_stars: int = 120, sigma: float = 1.8,
+                   e: float = 0.35, sky: float = 500.0, noise: bool = True) -> Field:
+    """Pair whose PSFs are elongated in orthogonal directions (reference along x, science
+    along y, axis ratio 1 - e, same area): neither can be matched to the other without
+    deconvolution, the case the dual-kernel formulation addresses.  Stars uniform, flux
+    log-uniform in [1e3, 1e5] e-, sky plus Poisson noise, variance = image, no mask."""
+    rng = np.random.default_rng(seed)
+    xs = rng.uniform(0, size - 1, n_stars)
+    ys = rng.uniform(0, size - 1, n_stars)
+    fl = _log_uniform(rng, 1e3, 1e5, n_stars)
+    ref = np.full((size, size), sky, np.float64)
+    sci = np.full((size, size), sky, np.float64)
+    for x, y, f in zip(xs, ys, fl):
+        add_gaussian(ref, x, y, f, sigma, e, 0.0)
+        add_gaussian(sci, x, y, f, sigma, e, 0.5 * math.pi)
+    if noise:
+        ref = rng.poisson(ref).astype(np.float64)
+        sci = rng.poisson(sci).astype(np.float64)
+    m = np.zeros((size, size), np.uint16)
+    return Field(ref.astype(np.float32), sci.astype(np.float32), ref.astype(np.float32),
+                 sci.astype(np.float32), m, m.copy(),
+                 dict(kind="elongated_pair", seed=seed, size=size, sigma=sigma, e=e))
+
+
 def full_chip_field(seed: int = 2, W: int = 4846, H: int = 4868, n_stars: int = 2500,
                     fwhm_ref=(3.5, 4.5), fwhm_sci=(4.5, 6.5), e_max: float = 0.15,
                     beta: float = 3.0, sky: float = 500.0, flux_lo: float = 1e3,

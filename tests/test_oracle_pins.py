@@ -570,3 +570,105 @@ def test_stack_full_rejects_a_planted_spike_in_its_input_only():
     # the spiked input is out of both stacks around the spike; the others are equal there
     assert r["conv"][3][y, x] == 2 and r["unconv"][3][y, x] == 2
     assert abs(r["unconv"][0][y, x] - warps[0]["image"][y, x]) < 1e-9 * abs(warps[0]["image"][y, x])
+
+
+# ---------------------------------------------------------------- binning (Sec. 4.3)
+
+def test_bin_image_white_noise_and_flux():
+    rng = np.random.default_rng(3)
+    img = rng.normal(10.0, 2.0, (60, 61)).astype(np.float32)
+    var = np.full((60, 61), 4.0, np.float32)
+    m = np.zeros((60, 61), np.uint16)
+    m[7, 9] = 1
+    Ib, Vb, Mb, Pb = O.bin_image(img, var, m, 4, 0xFF)
+    assert Ib.shape == (15, 15)
+    ok = m == 0
+    assert abs(Ib.sum() - np.where(ok, img, 0.0)[:60, :60].astype(np.float64).sum()) < 1e-9
+    # white noise: variance of a 4x4 sum is 16 sigma^2, no covariance between blocks
+    assert Vb[0, 0] == 64.0 and Vb[1, 2] == 60.0 and Mb[1, 2] == 1
+    assert Pb.shape == (1, 1) and Pb[0, 0] == 1.0
+
+
+def test_bin_image_correlated_noise_matches_empirical():
+    """Noise convolved with K has pseudo-matrix (K * K) / sum K^2 (Sec. 4.3); after 2x2
+    binning the empirical variance of the block sums and their lag-1 covariance match the
+    binned variance map and pseudo-matrix."""
+    K = np.array([[0.0, 0.1, 0.0], [0.1, 0.6, 0.3], [0.0, 0.2, 0.0]])
+    C = O.pseudo_conv(K, np.ones((1, 1)))
+    C = C / C[(C.shape[0] - 1) // 2, (C.shape[0] - 1) // 2]
+    noise = synth.white_noise(17, 1200, 1200, 1.0)
+    conv = O.direct_conv2d(noise, K)[8:-8, 8:-8]
+    s2 = float(np.sum(K * K))
+    n = conv.shape[0] // 2 * 2
+    conv = conv[:n, :n]
+    Ib, Vb, Mb, Pb = O.bin_image(conv, np.full(conv.shape, s2), np.zeros(conv.shape, np.uint16),
+                                 2, 0xFF, C)
+    emp_var = float(Ib.var())
+    assert abs(emp_var - float(Vb.mean())) < 0.03 * emp_var
+    c = (Pb.shape[0] - 1) // 2
+    emp_cov = float(np.mean((Ib[:, 1:] - Ib.mean()) * (Ib[:, :-1] - Ib.mean())))
+    assert abs(emp_cov / emp_var - Pb[c, c + 1]) < 0.03
+
+
+# ---------------------------------------------------------------- dual kernel (Eq. 2)
+
+def test_dual_normal_equations_equal_ridge_least_squares():
+    """Dual-kernel normal equations with the penalty (Eq. 5-6 with P_i on the diagonal) equal
+    the least-squares solution of the stacked weighted design augmented by sqrt(Phi p_i) rows."""
+    f = synth.elongated_pair(5, 64, 12, noise=True)
+    ob = O.Basis((1.0, 2.0), (1, 0), 3, 0)
+    oc = O.Config(badmask=synth.BADMASK, dual=True, penalty=0.05)
+    sts = [O.stamp_data(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, x, y, ob, oc)
+           for x, y in ((16, 16), (40, 20), (30, 45))]
+    b0, d0 = O.solve_normalisation(sts)
+    M, v = O.normal_equations(sts, ob, "separate", b0, d0, oc.penalty)
+    rows, rhs = [], []
+    for st in sts:
+        w = np.sqrt(np.where(st.ok, 1.0 / st.var, 0.0))
+        rows.append(O.design_rows(st, 1) * w[:, None])
+        rhs.append((st.I2 - b0 * st.R - d0) * w)
+    A = np.concatenate(rows)
+    p = np.tile(O.penalty_terms(ob), 2)
+    phi = oc.penalty * float(np.trace(A.T @ A)) / float(p.sum())
+    A = np.concatenate([A, np.diag(np.sqrt(phi * p))])
+    y = np.concatenate(rhs + [np.zeros(p.size)])
+    ref, *_ = np.linalg.lstsq(A, y, rcond=None)
+    assert np.allclose(np.linalg.solve(M, v), ref, rtol=1e-8, atol=1e-12)
+
+
+def test_dual_identical_images_give_zero_kernels():
+    f = synth.elongated_pair(6, 96, 30)
+    ob = O.Basis((1.0, 2.0), (2, 0), 5, 0)
+    oc = O.Config(grid_nx=2, grid_ny=2, badmask=synth.BADMASK, dual=True)
+    sol = O.solve_kernel(f.ref, f.ref, f.var_ref, f.var_ref, f.mask_ref, f.mask_ref, ob, oc)
+    assert abs(sol.b0 - 1.0) < 1e-12 and abs(sol.d0) < 1e-9
+    assert np.max(np.abs(sol.coeff)) < 1e-9
+
+
+def test_dual_variance_of_white_noise_is_sum_of_both_kernels():
+    """V_D = sigma1^2 sum K1^2 + sigma2^2 sum K2^2 for white inputs and constant kernels."""
+    f = synth.elongated_pair(7, 64, 10)
+    ob = O.Basis((1.0, 2.0), (2, 0), 5, 0)
+    nb = len(O.basis_terms(ob))
+    rng = np.random.default_rng(1)
+    coeff = np.concatenate([rng.normal(0, 0.1, nb), rng.normal(0, 0.1, nb), [3.0]])
+    sol = O.Solution(0.9, coeff, 3.0, ob, 64, 64, dual=True)
+    V1 = np.full((64, 64), 4.0, np.float32)
+    V2 = np.full((64, 64), 9.0, np.float32)
+    m = np.zeros((64, 64), np.uint16)
+    Vd = O.variance_image(V1, m, sol, 0xFF, 64, V2=V2, m2=m)
+    K1, K2 = O.realise_kernel(sol, 0, 0), O.realise_kernel2(sol, 0, 0)
+    expect = 4.0 * np.sum(K1 * K1) + 9.0 * np.sum(K2 * K2)
+    assert np.allclose(Vd[5:-5, 5:-5], expect, rtol=1e-12)
+
+
+def test_dual_kernel_matches_orthogonal_elongations_better():
+    """PSFs elongated in orthogonal directions: convolving both images (Eq. 2) leaves smaller
+    stamp residuals than convolving the reference alone, which would need deconvolution."""
+    f = synth.elongated_pair(8, 192, 90)
+    ob = O.Basis((0.8, 1.6, 3.0), (4, 2, 2), 8, 0)
+    single = O.solve_kernel(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, ob,
+                            O.Config(grid_nx=3, grid_ny=3, badmask=synth.BADMASK))
+    dual = O.solve_kernel(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, ob,
+                          O.Config(grid_nx=3, grid_ny=3, badmask=synth.BADMASK, dual=True))
+    assert dual.chi2_mean < single.chi2_mean
