@@ -118,6 +118,15 @@ typedef struct {
   uint16_t conv_bad;        /* CONV.BAD output bit [1 << 14] */
   uint16_t conv_poor;       /* CONV.POOR output bit [1 << 15] */
   uint16_t nodata;          /* stack pixel with no contributing input [1 << 0] */
+  int32_t dual;             /* 1: convolve both images, D = K2 (x) I2 - K1 (x) I1 - d0 with
+                               K2 = delta - sum_i c_i g_i k_i (Eq. 2, c_i != 0); needs
+                               precision F32X2, the science image and white inputs (no
+                               cov_ref / cov_img); the solution holds 2 N_b N_s coefficients
+                               (b terms, then c terms); the stacks and psfm_convolve_noalloc
+                               return PSFM_ERR_UNSUPPORTED for it [0] */
+  double penalty;           /* dual only: lambda of the penalty Phi p_i, p_i = sum (u^2+v^2)^2
+                               k_i^2, Phi = lambda * sum M_ii / sum p_i over the kernel unknowns
+                               (Sec. 2) [0.01] */
 } psfm_config;
 
 #define PSFM_CAND_UNUSED 0

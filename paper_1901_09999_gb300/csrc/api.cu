@@ -20,7 +20,7 @@ size_t head_layout(const Plan& p, Head& h) {
   pack_tables(p, h.blob, h.offs);
   size_t o = al(sizeof(DevState));
   const size_t o_dsol = o;
-  o = al(o + sizeof(double) * (2 + p.ncoef + 2));
+  o = al(o + sizeof(double) * (2 + p.ncoef + 2 + 2 * (2 + p.Nb * p.Ns)));
   const size_t o_tab = o;
   o = al(o + h.blob.size());
   h.bytes = o;
@@ -34,11 +34,13 @@ void head_bind(Head& h, char* base, const Plan& p) {
   h.st = reinterpret_cast<DevState*>(base);
   size_t o = al(sizeof(DevState));
   h.dsol = reinterpret_cast<double*>(base + o);
-  o = al(o + sizeof(double) * (2 + p.ncoef + 2));
+  h.dsol2 = h.dsol + (2 + p.ncoef + 2);
+  h.dsol3 = h.dsol2 + (2 + p.Nb * p.Ns);
+  o = al(o + sizeof(double) * (2 + p.ncoef + 2 + 2 * (2 + p.Nb * p.Ns)));
   h.tables = base + o;
 }
 
-DevTables bind_tables(char* t, const size_t offs[6]) {
+DevTables bind_tables(char* t, const size_t offs[7]) {
   DevTables d;
   d.f1d = reinterpret_cast<float*>(t + offs[0]);
   d.f1d64 = reinterpret_cast<double*>(t + offs[1]);
@@ -46,6 +48,7 @@ DevTables bind_tables(char* t, const size_t offs[6]) {
   d.sk = reinterpret_cast<double*>(t + offs[3]);
   d.term = reinterpret_cast<int32_t*>(t + offs[4]);
   d.spat = reinterpret_cast<int32_t*>(t + offs[5]);
+  d.pen = reinterpret_cast<double*>(t + offs[6]);
   return d;
 }
 
@@ -63,6 +66,7 @@ void carve_apply(const Plan& p, Workspace& ws, ApplyBuffers& b) {
   b.kern_t = ws.take<double>((size_t)ns * wt * wt);
   b.kern_s2 = ws.take<double>(ns);
   b.cov_acc = ws.take<double>((size_t)nconv * nconv);
+  b.cov_tmp = ws.take<double>((size_t)(2 * p.w - 1) * (2 * p.w - 1));
 }
 
 bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
@@ -100,6 +104,70 @@ psfm_status check_cov(const Plan& p, const double* cov_ref, int cov_ref_w, bool 
 
 // The apply path (Eq. 12-13, Sec. 3.4, Sec. 4.3-4.4) given the head already uploaded or
 // computed on the device.  r_bad is read from the device state.
+namespace {
+
+// Dual kernel (Eq. 2): from the solution (b0, d0, b terms, c terms) the views (0, 0, c), the
+// terms applied to I2, and (1, 0, -c), the kernel K2 = delta - sum c_k B_k of the difference.
+__global__ void k_dual_split(const double* dsol, int nbs, double* dsol2, double* dsol3) {
+  for (int i = threadIdx.x; i < 2 + nbs; i += blockDim.x) {
+    const double c = i >= 2 ? dsol[2 + nbs + (i - 2)] : 0.0;
+    dsol2[i] = c;
+    dsol3[i] = i == 0 ? 1.0 : (i == 1 ? 0.0 : -c);
+  }
+}
+
+// D = K2 (x) I2 - K1 (x) I1 - d0, its variance sum K1^2 (x) V1 + sum K2^2 (x) V2 (per patch),
+// the mask of both convolutions and the pseudo-matrices of K1 and K2 averaged with the mean
+// variances of the two parts as weights (Sec. 4.4).  White inputs only.
+psfm_status run_apply_dual(const Plan& p, const Head& h, const ApplyBuffers& b,
+                           const DevTables& t, const float* ref, const float* var_ref,
+                           const uint16_t* mask_ref, const float* img, const float* var_img,
+                           const uint16_t* mask_img, float* out, float* out_var,
+                           uint16_t* out_mask, double* cov_out, int cov_out_w, bool stats,
+                           cudaStream_t st) {
+  uint16_t* mask_dst = out_mask ? out_mask : (stats ? b.mask_tmp : nullptr);
+  k_dual_split<<<1, 256, 0, st>>>(h.dsol, p.Nb * p.Ns, h.dsol2, h.dsol3);
+  cudaError_t e = launch_rbad(p, t, h.dsol3, h.st, st, true);
+  if (e != cudaSuccess) return PSFM_ERR_CUDA;
+  if (mask_dst) {
+    prof_begin("mask", st);
+    e = launch_mask(p, b, mask_ref, mask_img, mask_dst, st, 1);
+    if (e == cudaSuccess) e = launch_mask(p, b, mask_ref, mask_img, mask_dst, st, 2);
+    prof_end("mask", st, 6);
+    if (e != cudaSuccess) return PSFM_ERR_CUDA;
+  }
+  prof_begin("conv_image", st);
+  e = launch_conv_image(p, t, h.dsol, ref, mask_ref, img, out, st);
+  if (e == cudaSuccess) e = launch_conv_image(p, t, h.dsol2, img, mask_img, out, out, st);
+  prof_end("conv_image", st, 2);
+  if (e != cudaSuccess) return PSFM_ERR_CUDA;
+  if (out_var || stats) {
+    prof_begin("variance", st);
+    e = launch_variance(p, t, h.dsol, var_ref, mask_ref, nullptr, nullptr, 1, nullptr, out_var,
+                        h.st, st);
+    if (e == cudaSuccess)
+      e = launch_variance(p, t, h.dsol3, var_img, mask_img, out_var, nullptr, 1,
+                          stats ? mask_dst : nullptr, out_var, h.st, st);
+    prof_end("variance", st, 2);
+    if (e != cudaSuccess) return PSFM_ERR_CUDA;
+  }
+  if (cov_out) {
+    prof_begin("covariance", st);
+    const int w1 = 2 * p.w - 1;
+    e = launch_cov(p, b, nullptr, 1, nullptr, 0, b.cov_tmp, w1, st);
+    if (e == cudaSuccess) {
+      ApplyBuffers b3 = b;
+      b3.dsol = h.dsol3;
+      e = launch_cov(p, b3, nullptr, 1, b.cov_tmp, w1, cov_out, cov_out_w, st);
+    }
+    prof_end("covariance", st, 6);
+    if (e != cudaSuccess) return PSFM_ERR_CUDA;
+  }
+  return PSFM_OK;
+}
+
+}  // namespace
+
 psfm_status run_apply(const Plan& p, const Head& h, const ApplyBuffers& b, const float* ref,
                       const float* var_ref, const uint16_t* mask_ref, const float* img,
                       const float* var_img, const uint16_t* mask_img, const double* cov_ref,
@@ -107,6 +175,13 @@ psfm_status run_apply(const Plan& p, const Head& h, const ApplyBuffers& b, const
                       uint16_t* out_mask, double* cov_out, int cov_out_w, bool stats,
                       cudaStream_t st) {
   const DevTables t = bind_tables(h.tables, h.offs);
+  if (p.cfg.dual) {
+    // the dual kernel convolves I2 as well, so it needs the science image; white inputs
+    if (!img || !var_img || !mask_img) return PSFM_ERR_BAD_ARG;
+    if (cov_ref || cov_img || (out_var && !var_ref)) return PSFM_ERR_UNSUPPORTED;
+    return run_apply_dual(p, h, b, t, ref, var_ref, mask_ref, img, var_img, mask_img, out,
+                          out_var, out_mask, cov_out, cov_out_w, stats, st);
+  }
   const bool diff = img != nullptr;
   uint16_t* mask_dst = out_mask ? out_mask : (stats ? b.mask_tmp : nullptr);
   cudaError_t e = cudaSuccess;
@@ -160,6 +235,8 @@ psfm_status run_stack_impl(int n, const float* const* imgs, const float* const* 
   Plan p0;
   psfm_status s = make_plan(p0, shape, &basis[0], cfg, 0);
   if (s != PSFM_OK) return s;
+  // each input is matched to the rendered target, which has no noise to convolve
+  if (cfg->dual) return PSFM_ERR_UNSUPPORTED;
   Workspace ws;
   ws.base = base;
   ws.size = ws_bytes;
@@ -271,6 +348,8 @@ void psfm_config_default(psfm_config* c) {
   c->conv_bad = (uint16_t)(1u << 14);
   c->conv_poor = (uint16_t)(1u << 15);
   c->nodata = 1;
+  c->dual = 0;
+  c->penalty = 1e-2;
 }
 
 const char* psfm_status_string(psfm_status s) {

@@ -13,15 +13,17 @@ constexpr int kMaxCovIn = 129;
 struct Head {
   DevState* st = nullptr;
   double* dsol = nullptr;
+  double* dsol2 = nullptr;  // dual kernel: (0, 0, c) the terms applied to I2
+  double* dsol3 = nullptr;  // dual kernel: (1, 0, -c) = K2, for its variance and pseudo-matrix
   char* tables = nullptr;
   size_t bytes = 0;
-  size_t offs[6];
+  size_t offs[7];
   std::vector<char> blob;
 };
 
 size_t head_layout(const Plan& p, Head& h);
 void head_bind(Head& h, char* base, const Plan& p);
-DevTables bind_tables(char* t, const size_t offs[6]);
+DevTables bind_tables(char* t, const size_t offs[7]);
 void carve_apply(const Plan& p, Workspace& ws, ApplyBuffers& b);
 bool aligned256(const void* p);
 cudaError_t upload_head(const Plan& p, Head& h, const double* sol_vals, int r_bad,

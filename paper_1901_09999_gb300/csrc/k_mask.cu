@@ -58,22 +58,25 @@ __global__ void k_mask_hdilate(const uint32_t* bits, int W, int H, int nwords, i
   const uint32_t p = word_at(row, wx - 1, nwords, W);
   const uint32_t c = word_at(row, wx, nwords, W);
   const uint32_t n = word_at(row, wx + 1, nwords, W);
-  const int rb = r_fixed >= 0 ? r_fixed : st->r_bad;
+  const int rb = r_fixed >= 0 ? r_fixed : (r_fixed == -2 ? st->r_bad2 : st->r_bad);
   hb_bad[(int64_t)y * nwords + wx] = hdilate(p, c, n, rb);
   hb_poor[(int64_t)y * nwords + wx] = hdilate(p, c, n, h);
 }
 
 // One warp per (row, 32-pixel word): lanes load the rows within h above and below, the warp
 // ORs them (vertical dilation), then each lane writes one output pixel.
+// mode 0: out = m1 | m2 with CONV.BAD near a bad pixel, else CONV.POOR;
+// mode 1 (first pass of the dual kernel): out holds only the two proximity flags;
+// mode 2 (second pass): the flags already in out are ORed with this pass's, then mode 0's rule.
 __global__ void k_mask_out(const uint32_t* hb_bad, const uint32_t* hb_poor, const uint16_t* m1,
                            const uint16_t* m2, int W, int H, int64_t pitch, int nwords,
                            int r_fixed, const DevState* st, int h, uint16_t conv_bad,
-                           uint16_t conv_poor, uint16_t* out) {
+                           uint16_t conv_poor, int mode, uint16_t* out) {
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (gw >= (int64_t)H * nwords) return;  // uniform per warp
   const int y = (int)(gw / nwords), wx = (int)(gw - (int64_t)y * nwords);
-  const int rb = r_fixed >= 0 ? r_fixed : st->r_bad;
+  const int rb = r_fixed >= 0 ? r_fixed : (r_fixed == -2 ? st->r_bad2 : st->r_bad);
   uint32_t vb = 0, vp = 0;
   for (int d = lane - h; d <= h; d += 32) {
     const int yy = y + d;
@@ -89,11 +92,21 @@ __global__ void k_mask_out(const uint32_t* hb_bad, const uint32_t* hb_poor, cons
   if (x >= W) return;
   const uint32_t bit = 1u << lane;
   const int64_t o = (int64_t)y * pitch + x;
+  bool nb = (vb & bit) != 0, np = (vp & bit) != 0;
+  if (mode == 1) {
+    out[o] = (uint16_t)((nb ? conv_bad : 0) | (np ? conv_poor : 0));
+    return;
+  }
+  if (mode == 2) {
+    const uint16_t prev = out[o];
+    nb = nb || (prev & conv_bad);
+    np = np || (prev & conv_poor);
+  }
   uint16_t m = m1[o];
   if (m2) m |= m2[o];
-  if (vb & bit)
+  if (nb)
     m |= conv_bad;
-  else if (vp & bit)
+  else if (np)
     m |= conv_poor;
   out[o] = m;
 }
@@ -102,7 +115,7 @@ __global__ void k_mask_out(const uint32_t* hb_bad, const uint32_t* hb_poor, cons
 // survives), in FP64: K_c(u, v) = sum_k a_{k,0} psi_k f_{g,p}(u) f_{g,q}(v) + delta (b0 -
 // sum_k a_{k,0} s_k).  One CTA.
 __global__ void k_rbad(BasisDev b, const double* f1d64, const double* psi, const double* sk,
-                       const double* dsol, double bad_frac, DevState* st) {
+                       const double* dsol, double bad_frac, int second, DevState* st) {
   extern __shared__ double sh[];
   const int W = b.w, h = b.h;
   double* colgp = sh;            // [NH][W]
@@ -163,8 +176,10 @@ __global__ void k_rbad(BasisDev b, const double* f1d64, const double* psi, const
         rb = r;
         break;
       }
-    st->r_bad = rb;
+    if (second) st->r_bad2 = rb;
+    else st->r_bad = rb;
   }
+  if (second) return;
   // quality diagnostics (Sec. 3.7): moments and enclosed kernel sums; every sum is taken in a
   // fixed order (per-thread strided partials, xor-shuffle trees, warps in order)
   __shared__ double wpart[8][6];
@@ -225,28 +240,33 @@ __global__ void k_rbad(BasisDev b, const double* f1d64, const double* psi, const
 }  // namespace
 
 cudaError_t launch_mask(const Plan& p, const ApplyBuffers& b, const uint16_t* mref,
-                        const uint16_t* mimg, uint16_t* out, cudaStream_t st) {
+                        const uint16_t* mimg, uint16_t* out, cudaStream_t st, int dual_pass) {
   const int nwords = (p.W + 31) / 32;
+  const int rsel = dual_pass == 2 ? -2 : -1;
+  // the dilated bad pixels: of the reference, or of the science image in the dual kernel's
+  // second pass (both input masks still form the output bits)
+  const uint16_t* src = dual_pass == 2 ? mimg : mref;
   dim3 blk(256);
-  k_mask_bits<<<dim3((p.W + 255) / 256, p.H), blk, 0, st>>>(mref, nullptr, p.W, p.H, p.pitch,
+  k_mask_bits<<<dim3((p.W + 255) / 256, p.H), blk, 0, st>>>(src, nullptr, p.W, p.H, p.pitch,
                                                             nwords, p.cfg.badmask, b.bits);
   k_mask_hdilate<<<dim3((nwords + 127) / 128, p.H), 128, 0, st>>>(
-      b.bits, p.W, p.H, nwords, -1, b.st, p.h, b.hb_bad, b.hb_poor);
+      b.bits, p.W, p.H, nwords, rsel, b.st, p.h, b.hb_bad, b.hb_poor);
   const int64_t warps = (int64_t)p.H * nwords;
   k_mask_out<<<(unsigned)((warps * 32 + 255) / 256), blk, 0, st>>>(
-      b.hb_bad, b.hb_poor, mref, mimg, p.W, p.H, p.pitch, nwords, -1, b.st, p.h, p.cfg.conv_bad,
-      p.cfg.conv_poor, out);
+      b.hb_bad, b.hb_poor, mref, mimg, p.W, p.H, p.pitch, nwords, rsel, b.st, p.h,
+      p.cfg.conv_bad, p.cfg.conv_poor, dual_pass, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rbad(const Plan& p, const DevTables& t, const double* dsol, DevState* ds,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool second) {
   const size_t smem =
       sizeof(double) * ((size_t)p.NH * p.w + 2 * (size_t)p.w * p.w + 3 * (size_t)p.h + 4);
   cudaError_t e = cudaFuncSetAttribute(k_rbad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_rbad<<<1, 256, smem, st>>>(basis_dev(p), t.f1d64, t.psi, t.sk, dsol, p.cfg.bad_frac, ds);
+  k_rbad<<<1, 256, smem, st>>>(basis_dev(p), t.f1d64, t.psi, t.sk, dsol, p.cfg.bad_frac,
+                               second ? 1 : 0, ds);
   return cudaGetLastError();
 }
 

@@ -187,7 +187,10 @@ __device__ __forceinline__ double df_to_d(df a) { return (double)a.hi + (double)
 // N_H blocks, so a handful of replaced stamps still fill many SMs.
 __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
   extern __shared__ __align__(16) unsigned char sh_raw[];
-  const int r = blockIdx.x, pl = blockIdx.y, tid = threadIdx.x;
+  // blockIdx.y = set * N_H + plane: set 0 convolves the masked reference, set 1 (dual kernel,
+  // Eq. 2) the science image with its own mask, into design columns N_b..2 N_b - 1
+  const int r = blockIdx.x, set = blockIdx.y / P.b.NH, pl = blockIdx.y - set * P.b.NH;
+  const int tid = threadIdx.x;
   if (block_skip(P.st)) return;
   int cx, cy;
   if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return;
@@ -216,8 +219,12 @@ __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
     if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
       const int64_t o = (int64_t)gy * P.g.pitch + gx;
       const uint16_t a = P.m1[o] & P.badmask, b = P.m2[o] & P.badmask;
-      if (!a) v = P.i1[o];
-      if (pl == 0 && !a && !b) {
+      if (set == 0) {
+        if (!a) v = P.i1[o];
+      } else if (!b) {
+        v = P.i2[o];
+      }
+      if (set == 0 && pl == 0 && !a && !b) {
         f1 += v;
         f2 += P.i2[o];
         nf += 1.0;
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
     }
     F[i] = v;
   }
-  if (pl == 0) {
+  if (set == 0 && pl == 0) {
     __shared__ double red[3][8];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -293,7 +300,8 @@ __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
   for (int q = 0; q <= dg - p; ++q) {
     const float* qh = wh + q * W;
     const float* ql = wl + q * W;
-    float2* out = reinterpret_cast<float2*>(P.C) + ((int64_t)r * P.b.Nb + kgp + q) * P.P;
+    float2* out = reinterpret_cast<float2*>(P.C) +
+                  ((int64_t)r * P.Nd + set * P.b.Nb + kgp + q) * P.P;
     for (int it = tid; it < sw * nrg; it += 256) {
       const int rg = it / sw, px = it - rg * sw, py0 = rg * 4;
       auto ld = [&](int row) {
@@ -342,7 +350,8 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
   int cx, cy;
   if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return;
   if (P.have[r] == P.ptr[r]) return;
-  const int Nc = P.Nc, Nb = P.b.Nb;
+  // design columns: N_d (the basis applied to R, then to I2 with the dual kernel), then R, 1, I2
+  const int Nc = P.Nc, Nb = P.Nd;
   const int nblk = (Nc + 3) / 4, npair = nblk * (nblk + 1) / 2;
   const int nsl = max(1, kGramThreads / npair);
   const int ncr = nblk * 4;                                        // padded column count
@@ -480,16 +489,20 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
     Gr[q] = v;
   }
   __syncthreads();
+  // transformed Gram: design column i of basis term k becomes psi_k C_i - s_k X, X the image
+  // the term convolves (R for the first N_b columns, I2 for the dual kernel's)
   double* Gtr = P.Gt + (int64_t)r * Nc * Nc;
-  const int cR = Nb;
+  const int nbk = P.b.Nb;
   for (int q = tid; q < Nc * Nc; q += kGramThreads) {
     const int i = q / Nc, j = q - i * Nc;
-    const double ai = i < Nb ? P.psi[i] : 1.0, bi3 = i < Nb ? P.sk[i] : 0.0;
-    const double aj = j < Nb ? P.psi[j] : 1.0, bj3 = j < Nb ? P.sk[j] : 0.0;
+    const int ki = i < nbk ? i : i - nbk, kj = j < nbk ? j : j - nbk;
+    const double ai = i < Nb ? P.psi[ki] : 1.0, bi3 = i < Nb ? P.sk[ki] : 0.0;
+    const double aj = j < Nb ? P.psi[kj] : 1.0, bj3 = j < Nb ? P.sk[kj] : 0.0;
+    const int ci = i < nbk ? Nb : Nb + 2, cj = j < nbk ? Nb : Nb + 2;
     double e = ai * aj * Gr[i * Nc + j];
-    if (bj3 != 0.0) e -= ai * bj3 * Gr[i * Nc + cR];
-    if (bi3 != 0.0) e -= bi3 * aj * Gr[cR * Nc + j];
-    if (bi3 != 0.0 && bj3 != 0.0) e += bi3 * bj3 * Gr[cR * Nc + cR];
+    if (bj3 != 0.0) e -= ai * bj3 * Gr[i * Nc + cj];
+    if (bi3 != 0.0) e -= bi3 * aj * Gr[ci * Nc + j];
+    if (bi3 != 0.0 && bj3 != 0.0) e += bi3 * bj3 * Gr[ci * Nc + cj];
     Gtr[q] = e;
   }
   __syncthreads();
@@ -629,6 +642,10 @@ struct SysParams {
   BasisDev b;
   ImgGeom g;
   int nreg, max_cand, Nc, Nsys, joint;
+  int Nd;              // design columns (N_b, or 2 N_b with the dual kernel)
+  double lambda;       // dual kernel: penalty scale; 0 without penalty
+  const double* pen;   // [N_b] p_k
+  double* pdiag;       // [Nsys] Phi p_i added to the diagonal (dual kernel), else zeros
   const int32_t* cand;
   const int32_t* ptr;
   const double* Gt;
@@ -746,12 +763,12 @@ __global__ void __launch_bounds__(1024) k_norm(SysParams P) {
 __device__ __forceinline__ void unknown_col(const SysParams& P, int u, int* a, int* s) {
   if (P.joint) {
     if (u == 0) {
-      *a = P.b.Nb;  // R
+      *a = P.Nd;  // R
       *s = -1;
       return;
     }
     if (u == P.Nsys - 1) {
-      *a = P.b.Nb + 1;  // 1
+      *a = P.Nd + 1;  // 1
       *s = -1;
       return;
     }
@@ -838,7 +855,7 @@ __global__ void __launch_bounds__(256) k_rhs(SysParams P) {
   const int Ns = P.b.Ns, N1 = Ns + 1, Nc = P.Nc;
   int av = 0, sv = -1;
   unknown_col(P, t, &av, &sv);
-  const int colR = P.b.Nb, col1 = P.b.Nb + 1, colI = P.b.Nb + 2;
+  const int colR = P.Nd, col1 = P.Nd + 1, colI = P.Nd + 2;
   const double b0 = P.dsol[0], d0 = P.dsol[1];
   double accv = 0.0;
   for (int r = lane; r < P.nreg; r += 32) {
@@ -852,6 +869,37 @@ __global__ void __launch_bounds__(256) k_rhs(SysParams P) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) accv += __shfl_xor_sync(0xffffffffu, accv, o);
   if (lane == 0) P.v[t] = accv;
+}
+
+// Dual kernel (Sec. 2): Phi = lambda * sum M_ii / sum p_i over the kernel unknowns, and
+// Phi p_i added to the diagonal of the double-float working copy of M (M itself stays the
+// plain normal matrix, updated incrementally); the FP64 residuals of the refinement add
+// pdiag * x.  One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_penalty(SysParams P) {
+  __shared__ double sh[33];
+  if (P.st->error || P.st->done) return;
+  const int N = P.Nsys, nbk = P.b.Nb;
+  double tm = 0.0, tp = 0.0;
+  for (int u = threadIdx.x; u < N; u += blockDim.x) {
+    int a, sidx;
+    unknown_col(P, u, &a, &sidx);
+    if (sidx < 0) continue;  // b0, d0 of the joint fit
+    tm += P.M[(int64_t)u * N + u];
+    tp += P.pen[a < nbk ? a : a - nbk];
+  }
+  tm = block_sum(tm, sh);
+  tp = block_sum(tp, sh);
+  const double phi = tp > 0.0 ? P.lambda * tm / tp : 0.0;
+  for (int u = threadIdx.x; u < N; u += blockDim.x) {
+    int a, sidx;
+    unknown_col(P, u, &a, &sidx);
+    const double pd = sidx < 0 ? 0.0 : phi * P.pen[a < nbk ? a : a - nbk];
+    P.pdiag[u] = pd;
+    const int64_t o = (int64_t)u * N + u;
+    const df d = df_split(P.M[o] + pd);
+    P.Lh[o] = d.hi;
+    P.Ll[o] = d.lo;
+  }
 }
 
 constexpr int kNB = 32;
@@ -1137,8 +1185,8 @@ __global__ void __launch_bounds__(1024) k_chol_solve(int n, const float* Lh, con
 }
 
 // r = b - M x in FP64 (one warp per row).
-__global__ void __launch_bounds__(256) k_residual(int n, const double* M, const double* b,
-                                                  const double* x, double* r,
+__global__ void __launch_bounds__(256) k_residual(int n, const double* M, const double* pdiag,
+                                                  const double* b, const double* x, double* r,
                                                   const DevState* st) {
   if (st->error || st->done || st->chol_fail) return;
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -1147,7 +1195,7 @@ __global__ void __launch_bounds__(256) k_residual(int n, const double* M, const 
   for (int c = lane; c < n; c += 32) s = fma(M[(int64_t)row * n + c], x[c], s);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) r[row] = b[row] - s;
+  if (lane == 0) r[row] = b[row] - s - pdiag[row] * x[row];
 }
 
 // Scatter the solution vector into the device solution (b0, d0, a_{k,s}).
@@ -1170,12 +1218,14 @@ __global__ void k_store_solution(int n, int joint, const double* x, double* dsol
 // Fallback when the Cholesky factorisation meets a non-positive pivot: LU with partial
 // pivoting in FP64, one CTA (rare path).
 __global__ void __launch_bounds__(1024) k_lu_solve(int N, int joint, const double* M,
-                                                   const double* v, double* L, double* y,
-                                                   int32_t* piv, double* dsol, DevState* st) {
+                                                   const double* pdiag, const double* v,
+                                                   double* L, double* y, int32_t* piv,
+                                                   double* dsol, DevState* st) {
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ int s_fail;
   if (st->error || st->done || !st->chol_fail) return;
-  for (int64_t i = tid; i < (int64_t)N * N; i += nt) L[i] = M[i];
+  for (int64_t i = tid; i < (int64_t)N * N; i += nt)
+    L[i] = M[i] + (i / N == i % N ? pdiag[i / N] : 0.0);
   for (int i = tid; i < N; i += nt) y[i] = v[i];
   if (tid == 0) s_fail = 0;
   __syncthreads();
@@ -1303,38 +1353,40 @@ struct Chi2Params {
 template <typename T>
 __global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
   const StampParams& P = Q.sp;
-  extern __shared__ double ak[];  // [Nb]: a_k(stamp) psi_k
+  extern __shared__ double ak[];  // [Nd]: a_k(stamp) psi_k (then c_k psi_k, dual kernel)
   __shared__ double red[2][8];
-  __shared__ double s_delta;
+  __shared__ double s_delta, s_delta2;
   const int r = blockIdx.x, tid = threadIdx.x;
   if (block_skip(P.st)) return;
   int cx, cy;
   if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return;
-  const int Nb = P.b.Nb, Ns = P.b.Ns;
+  const int Nb = P.b.Nb, Nd = P.Nd, Ns = P.b.Ns;
   const double* gr = Q.gv + (int64_t)r * Ns;
-  for (int k = tid; k < Nb; k += 256) {
+  for (int k = tid; k < Nd; k += 256) {
     double a = 0.0;
     for (int s = 0; s < Ns; ++s) a += Q.dsol[2 + k * Ns + s] * gr[s];
     ak[k] = a;
   }
   __syncthreads();
   if (tid == 0) {
-    double d = Q.dsol[0];
-    for (int k = 0; k < Nb; ++k) {
-      d -= ak[k] * P.sk[k];
-    }
+    // the delta parts of the zero-sum terms: on R for the first N_b columns, on I2 for the
+    // dual kernel's
+    double d = Q.dsol[0], d2 = 0.0;
+    for (int k = 0; k < Nb; ++k) d -= ak[k] * P.sk[k];
+    for (int k = Nb; k < Nd; ++k) d2 -= ak[k] * P.sk[k - Nb];
     s_delta = d;
+    s_delta2 = d2;
   }
   __syncthreads();
-  float2* akf = reinterpret_cast<float2*>(ak + Nb);  // the same split into FP32 pairs
-  for (int k = tid; k < Nb; k += 256) {
-    ak[k] *= P.psi[k];
+  float2* akf = reinterpret_cast<float2*>(ak + Nd);  // the same split into FP32 pairs
+  for (int k = tid; k < Nd; k += 256) {
+    ak[k] *= P.psi[k < Nb ? k : k - Nb];
     const df d = df_split(ak[k]);
     akf[k] = make_float2(d.hi, d.lo);
   }
   __syncthreads();
-  const double delta = s_delta, d0 = Q.dsol[1];
-  const T* Cr = reinterpret_cast<const T*>(P.C) + (int64_t)r * Nb * P.P;
+  const double delta = s_delta, delta2 = s_delta2, d0 = Q.dsol[1];
+  const T* Cr = reinterpret_cast<const T*>(P.C) + (int64_t)r * Nd * P.P;
   double q = 0.0, n = 0.0;
   // 4 pixels per thread at a time, so that their design-column loads overlap
   for (int base = tid; base < P.P; base += 4 * 256) {
@@ -1354,13 +1406,13 @@ __global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
       off[j] = o;
     }
     double mod[4];
-    basis_model4(ak, akf, Cr, Nb, P.P, pix, mod);
+    basis_model4(ak, akf, Cr, Nd, P.P, pix, mod);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (pix[j] < 0) continue;
       const int64_t o = off[j];
       const double R = P.i1[o], I2 = P.i2[o];
-      const double model = delta * R + d0 + mod[j];
+      const double model = delta * R + delta2 * (Nd > Nb ? (double)P.i2[o] : 0.0) + d0 + mod[j];
       const double res = I2 - model;
       const double den = ((double)P.v1[o] + (double)P.v2[o]) + Q.alpha * fabs(I2);
       q += res * res / den;
@@ -1482,7 +1534,7 @@ void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b) {
   b.cand_chi2 = ws.take<double>((size_t)p.nreg * p.max_cand);
   b.ptr = ws.take<int32_t>(p.nreg);
   b.have = ws.take<int32_t>(p.nreg);
-  b.C = ws.take<double>((size_t)p.nreg * p.Nb * p.P);
+  b.C = ws.take<double>((size_t)p.nreg * p.Nd * p.P);
   b.G = ws.take<double>((size_t)p.nreg * p.Nc * p.Nc);
   b.Gt = ws.take<double>((size_t)p.nreg * p.Nc * p.Nc);
   b.Gpart = ws.take<double>((size_t)p.nreg * kGramSplit * p.Nc * p.Nc);
@@ -1496,6 +1548,7 @@ void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b) {
   b.Lh = ws.take<float>((size_t)p.Nsys * p.Nsys);
   b.Ll = ws.take<float>((size_t)p.Nsys * p.Nsys);
   b.x = ws.take<double>(p.Nsys);
+  b.pdiag = ws.take<double>(p.Nsys);
   b.y = ws.take<double>(p.Nsys);
   b.piv = ws.take<int32_t>(p.Nsys);
   b.gv = ws.take<double>((size_t)p.nreg * p.Ns);
@@ -1533,6 +1586,7 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   sp.foot = p.foot;
   sp.max_cand = p.max_cand;
   sp.Nc = p.Nc;
+  sp.Nd = p.Nd;
   sp.f1d = t.f1d;
   sp.f1d64 = t.f1d64;
   sp.psi = t.psi;
@@ -1555,6 +1609,10 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   sy.nreg = p.nreg;
   sy.max_cand = p.max_cand;
   sy.Nc = p.Nc;
+  sy.Nd = p.Nd;
+  sy.lambda = p.cfg.dual ? p.cfg.penalty : 0.0;
+  sy.pen = t.pen;
+  sy.pdiag = b.pdiag;
   sy.Nsys = p.Nsys;
   sy.joint = p.cfg.norm_mode == PSFM_NORM_JOINT;
   sy.cand = b.cand;
@@ -1625,12 +1683,13 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
       cudaMemsetAsync(b.M, 0, sizeof(double) * (size_t)p.Nsys * p.Nsys, s) != cudaSuccess ||
       cudaMemsetAsync(b.fresh, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess ||
       cudaMemsetAsync(b.removed, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess ||
-      cudaMemsetAsync(b.gram_count, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess)
+      cudaMemsetAsync(b.gram_count, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess ||
+      cudaMemsetAsync(b.pdiag, 0, sizeof(double) * p.Nsys, s) != cudaSuccess)
     return PSFM_ERR_CUDA;
   const bool dfm = prec == PSFM_PREC_F32X2;
   for (int it = 0; it < p.cfg.max_iter; ++it) {
     prof_begin("stamps", s);
-    design<<<dim3(p.nreg, dfm ? p.NH : p.ng), 256, sm_design, s>>>(sp);
+    design<<<dim3(p.nreg, dfm ? p.NH * (p.cfg.dual ? 2 : 1) : p.ng), 256, sm_design, s>>>(sp);
     if (tcm) {
       if (launch_gram_tc(prec == PSFM_PREC_TF32 ? 0 : 1, sp, p.nreg, s) != cudaSuccess)
         return PSFM_ERR_CUDA;
@@ -1641,8 +1700,9 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
     prof_begin("system", s);
     k_norm<<<1, 1024, 0, s>>>(sy);
     k_system_delta<<<(unsigned)((nthr + 255) / 256), 256, sm_asm, s>>>(sy, 0, asm_chunk);
+    if (p.cfg.dual) k_penalty<<<1, 1024, 0, s>>>(sy);
     k_rhs<<<(N * 32 + 255) / 256, 256, 0, s>>>(sy);
-    prof_end("system", s, 3);
+    prof_end("system", s, p.cfg.dual ? 4 : 3);
     prof_begin("cholesky", s);
     for (int kb = 0; kb < npanel; ++kb) {
       k_chol_diag<<<1, kDiagThreads, 0, s>>>(N, kb, b.Lh, b.Ll, b.rinv, st);
@@ -1656,14 +1716,14 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
     }
     k_chol_solve<<<1, 1024, sm_solve, s>>>(N, b.Lh, b.Ll, b.rinv, b.v, nullptr, b.x, st);
     for (int ref = 0; ref < 2; ++ref) {
-      k_residual<<<(N * 32 + 255) / 256, 256, 0, s>>>(N, b.M, b.v, b.x, b.y, st);
+      k_residual<<<(N * 32 + 255) / 256, 256, 0, s>>>(N, b.M, b.pdiag, b.v, b.x, b.y, st);
       k_chol_solve<<<1, 1024, sm_solve, s>>>(N, b.Lh, b.Ll, b.rinv, b.y, b.x, b.x, st);
     }
     k_store_solution<<<(N + 255) / 256, 256, 0, s>>>(N, sy.joint, b.x, dsol, st);
-    k_lu_solve<<<1, 1024, 0, s>>>(N, sy.joint, b.M, b.v, b.L, b.y, b.piv, dsol, st);
+    k_lu_solve<<<1, 1024, 0, s>>>(N, sy.joint, b.M, b.pdiag, b.v, b.L, b.y, b.piv, dsol, st);
     prof_end("cholesky", s, 3 * npanel + 7);
     prof_begin("chi2_reject", s);
-    chi2<<<p.nreg, 256, (sizeof(double) + sizeof(float2)) * p.Nb + 16, s>>>(cq);
+    chi2<<<p.nreg, 256, (sizeof(double) + sizeof(float2)) * p.Nd + 16, s>>>(cq);
     k_reject<<<1, 1024, 0, s>>>(p.nreg, p.max_cand, p.cfg.max_iter, p.cfg.reject_nsigma, b.cand,
                                 b.ptr, b.cand_stat, b.chi2, b.fresh, b.removed, st);
     k_system_delta<<<(unsigned)((nthr + 255) / 256), 256, sm_asm, s>>>(sy, 1, asm_chunk);

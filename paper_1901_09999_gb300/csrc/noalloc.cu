@@ -68,6 +68,7 @@ extern "C" psfm_status psfm_convolve_noalloc(
   Plan p;
   psfm_status s = make_plan(p, shape, basis, cfg, 0);
   if (s != PSFM_OK) return s;
+  if (cfg->dual) return PSFM_ERR_UNSUPPORTED;  // the dual kernel's passes need a workspace
   const bool diff = img != nullptr;
   if (!ref || !mask_ref || !out || !sol) return PSFM_ERR_BAD_ARG;
   if (out_var && !var_ref) return PSFM_ERR_BAD_ARG;
@@ -79,7 +80,7 @@ extern "C" psfm_status psfm_convolve_noalloc(
 
   // head: [DevState][b0, d0, coeff][tables], as in the workspace of psfm_convolve
   std::vector<char> blob;
-  size_t offs[6];
+  size_t offs[7];
   pack_tables(p, blob, offs);
   const size_t o_dsol = al256(sizeof(DevState));
   const size_t o_tab = al256(o_dsol + sizeof(double) * (2 + p.ncoef));
@@ -111,6 +112,7 @@ extern "C" psfm_status psfm_convolve_noalloc(
   tab.sk = reinterpret_cast<double*>(t + offs[3]);
   tab.term = reinterpret_cast<int32_t*>(t + offs[4]);
   tab.spat = reinterpret_cast<int32_t*>(t + offs[5]);
+  tab.pen = reinterpret_cast<double*>(t + offs[6]);
   DevState* dst = reinterpret_cast<DevState*>(base);
   const double* dsol = reinterpret_cast<const double*>(base + o_dsol);
 

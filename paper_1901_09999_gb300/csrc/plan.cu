@@ -80,7 +80,8 @@ psfm_status make_plan(Plan& p, psfm_shape shape, const psfm_basis_spec* b, const
       p.sm[si] = m;
       ++si;
     }
-  p.ncoef = p.Nb * p.Ns;
+  p.Nd = c->dual ? 2 * p.Nb : p.Nb;
+  p.ncoef = p.Nd * p.Ns;
   // 1-D factors f_{g,n}(t) = t^n exp(-t^2 / (2 sigma_g^2)), the Gaussian of Eq. 7 with the
   // decaying sign
   p.f1d.assign((size_t)p.NH * p.w, 0.0);
@@ -104,6 +105,16 @@ psfm_status make_plan(Plan& p, psfm_shape shape, const psfm_basis_spec* b, const
     }
     p.psi[k] = 1.0 / std::sqrt(np * nq);
     p.sk[k] = (p.tp[k] % 2 == 0 && p.tq[k] % 2 == 0) ? p.psi[k] * sp * sq : 0.0;
+    // penalty p_k = sum_{u,v} (u^2 + v^2)^2 k_k(u, v)^2 (Sec. 2); the delta of the zero-sum
+    // correction sits at u = v = 0 where the weight vanishes
+    double pen = 0.0;
+    for (int a = 0; a < p.w; ++a)
+      for (int b2 = 0; b2 < p.w; ++b2) {
+        const double u = a - p.h, v = b2 - p.h, r2 = u * u + v * v;
+        const double kv = p.psi[k] * fp[a] * fq[b2];
+        pen += r2 * r2 * kv * kv;
+      }
+    p.pen[k] = pen;
   }
   // configuration
   p.cfg = *c;
@@ -114,6 +125,10 @@ psfm_status make_plan(Plan& p, psfm_shape shape, const psfm_basis_spec* b, const
   if (c->var_tile != kVarTile) return PSFM_ERR_UNSUPPORTED;
   if (c->norm_mode != PSFM_NORM_SEPARATE && c->norm_mode != PSFM_NORM_JOINT)
     return PSFM_ERR_BAD_ARG;
+  if (c->dual != 0 && c->dual != 1) return PSFM_ERR_BAD_ARG;
+  if (c->dual && (!(c->penalty >= 0.0) || !std::isfinite(c->penalty))) return PSFM_ERR_BAD_ARG;
+  // the dual kernel is built on the double-float design and Gram
+  if (c->dual && c->precision != PSFM_PREC_F32X2) return PSFM_ERR_UNSUPPORTED;
   if (c->precision != PSFM_PREC_FP64 && c->precision != PSFM_PREC_FP32 &&
       c->precision != PSFM_PREC_F32X2 && c->precision != PSFM_PREC_TF32 &&
       c->precision != PSFM_PREC_BF16X3)
@@ -136,14 +151,14 @@ psfm_status make_plan(Plan& p, psfm_shape shape, const psfm_basis_spec* b, const
     p.max_cand = c->max_cand;
   }
   p.Nsys = p.ncoef + (c->norm_mode == PSFM_NORM_JOINT ? 2 : 0);
-  p.Nc = p.Nb + 3;
+  p.Nc = p.Nd + 3;
   // the tensor-core Gram holds the augmented block in one 128-lane accumulator tile
   if ((c->precision == PSFM_PREC_TF32 || c->precision == PSFM_PREC_BF16X3) && p.Nc > 128)
     return PSFM_ERR_UNSUPPORTED;
   return PSFM_OK;
 }
 
-void pack_tables(const Plan& p, std::vector<char>& blob, size_t offs[6]) {
+void pack_tables(const Plan& p, std::vector<char>& blob, size_t offs[7]) {
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t o = 0;
   offs[0] = o;  // f1d fp32 [NH][wpad]
@@ -158,6 +173,8 @@ void pack_tables(const Plan& p, std::vector<char>& blob, size_t offs[6]) {
   o = al(o + sizeof(int32_t) * p.Nb);
   offs[5] = o;  // spatial
   o = al(o + sizeof(int32_t) * p.Ns);
+  offs[6] = o;  // penalty p_k
+  o = al(o + sizeof(double) * p.Nb);
   blob.assign(o, 0);
   float* f32 = reinterpret_cast<float*>(blob.data() + offs[0]);
   double* f64 = reinterpret_cast<double*>(blob.data() + offs[1]);
@@ -172,6 +189,7 @@ void pack_tables(const Plan& p, std::vector<char>& blob, size_t offs[6]) {
   for (int k = 0; k < p.Nb; ++k) term[k] = p.tg[k] | (p.tp[k] << 8) | (p.tq[k] << 16);
   int32_t* sp = reinterpret_cast<int32_t*>(blob.data() + offs[5]);
   for (int s = 0; s < p.Ns; ++s) sp[s] = p.sl[s] | (p.sm[s] << 8);
+  std::memcpy(blob.data() + offs[6], p.pen, sizeof(double) * p.Nb);
 }
 
 }  // namespace psfm

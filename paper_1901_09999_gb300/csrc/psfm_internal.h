@@ -46,7 +46,7 @@ struct DevState {
   int32_t sel_pad;
   // quality diagnostics of the solution (Sec. 3.7), kernel realised at the image centre
   int32_t q_flags;
-  int32_t q_pad;
+  int32_t r_bad2;       // CONV.BAD radius of the dual kernel K2 applied to I2
   double q_ksum, q_mx, q_my, q_mxx, q_myy, q_mxy, q_deconv;
 };
 
@@ -61,18 +61,19 @@ struct Plan {
   int plane_base[PSFM_MAX_GAUSS] = {0, 0, 0, 0};
   int kbase[PSFM_MAX_GAUSS] = {0, 0, 0, 0};
   int S = 0, Ns = 0, Nb = 0, NH = 0, dmax = 0;
-  int ncoef = 0;  // Nb * Ns
+  int Nd = 0;     // design columns per stamp: Nb, or 2 Nb with the dual kernel (I1 then I2)
+  int ncoef = 0;  // Nd * Ns
   // terms
   int tg[kMaxBasis], tp[kMaxBasis], tq[kMaxBasis];
   int sl[kMaxSpatial], sm[kMaxSpatial];
-  double psi[kMaxBasis], sk[kMaxBasis];
+  double psi[kMaxBasis], sk[kMaxBasis], pen[kMaxBasis];
   std::vector<double> f1d;  // [NH][w]
   // configuration
   psfm_config cfg;
   int s = 0, P = 0, sw = 0, foot = 0;   // stamp half, pixels, side, footprint side
   int nreg = 0, max_cand = 0, n_stamps = 0;
   int Nsys = 0;  // unknowns of the kernel-term system (Nb*Ns [+2 for joint])
-  int Nc = 0;    // columns of a stamp's augmented design block (Nb + 3: basis, R, 1, I2)
+  int Nc = 0;    // columns of a stamp's augmented design block (Nd + 3: basis, R, 1, I2)
 };
 
 // Tables uploaded to the device at the start of a call (one blob in the workspace).
@@ -83,6 +84,7 @@ struct DevTables {
   double* sk;       // [Nb]
   int32_t* term;    // [Nb] g | p << 8 | q << 16
   int32_t* spat;    // [Ns] l | m << 8
+  double* pen;      // [Nb] penalty p_k of the dual kernel (Sec. 2)
 };
 
 // Basis geometry passed by value to kernels.
@@ -125,6 +127,7 @@ struct ApplyBuffers {
   double* kern_t;      // [n_cov][(w+c-1)^2] K (x) C_in
   double* kern_s2;     // [n_cov] sum K^2
   double* cov_acc;     // [n_out^2]
+  double* cov_tmp;     // [(2w-1)^2] pseudo-matrix of the dual kernel's first part
 };
 
 BasisDev basis_dev(const Plan& p);
@@ -173,7 +176,7 @@ void prof_begin(const char* name, cudaStream_t s);
 void prof_end(const char* name, cudaStream_t s, int n_launches);
 psfm_status make_plan(Plan& p, psfm_shape shape, const psfm_basis_spec* b, const psfm_config* c,
                       int n_stamps);
-void pack_tables(const Plan& p, std::vector<char>& blob, size_t offs[6]);
+void pack_tables(const Plan& p, std::vector<char>& blob, size_t offs[7]);
 
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t launch_conv_image(const Plan& p, const DevTables& t, const double* dsol,
@@ -183,12 +186,16 @@ cudaError_t launch_variance(const Plan& p, const DevTables& t, const double* dso
                             const float* var_ref, const uint16_t* mref, const float* var_img,
                             const double* cov_in, int cov_in_w, const uint16_t* omask,
                             float* out_var, DevState* ds, cudaStream_t st);
+// dual_pass 0: the single kernel; 1: the dual kernel's first pass (proximity flags of the
+// reference's bad pixels only); 2: its second pass (the science image's bad pixels dilated by
+// r_bad2, combined with the first pass's flags into the output mask)
 cudaError_t launch_mask(const Plan& p, const ApplyBuffers& b, const uint16_t* mref,
-                        const uint16_t* mimg, uint16_t* out, cudaStream_t st);
+                        const uint16_t* mimg, uint16_t* out, cudaStream_t st,
+                        int dual_pass = 0);
 cudaError_t launch_cov(const Plan& p, const ApplyBuffers& b, const double* cov_in,
                        int cov_in_w, const double* cov_img, int cov_img_w, double* cov_out,
                        int cov_out_w, cudaStream_t st);
 cudaError_t launch_rbad(const Plan& p, const DevTables& t, const double* dsol, DevState* ds,
-                        cudaStream_t st);
+                        cudaStream_t st, bool second = false);
 
 }  // namespace psfm

@@ -38,6 +38,7 @@ struct SolveBuffers {
   float* Lh;     // [Nsys][Nsys] double-float Cholesky factor, high parts
   float* Ll;     // low parts
   double* x;     // [Nsys] solution being refined
+  double* pdiag; // [Nsys] penalty on the diagonal (dual kernel; zeros otherwise)
   double* y;  // [Nsys]
   int32_t* piv;  // [Nsys] LU pivots
   double* gv;    // [nreg][Ns] spatial factors at the stamp centres, 0 when inactive

@@ -125,6 +125,10 @@ size_t full_layout(int n, psfm_shape shape, const psfm_basis_spec* basis, const 
   *st = PSFM_OK;
   Plan p0;
   if ((*st = make_plan(p0, shape, &basis[0], cfg, 0)) != PSFM_OK) return 0;
+  if (cfg->dual) {  // the inputs are matched to a noiseless rendered target
+    *st = PSFM_ERR_UNSUPPORTED;
+    return 0;
+  }
   const size_t npx = (size_t)shape.height * shape.pitch;
   StackBuffers kb;
   carve_stack(p0, ws, kb, n_src_max);

@@ -39,6 +39,7 @@ struct StampParams {
   const uint16_t* m2;
   uint16_t badmask;
   int s, sw, P, foot, max_cand, Nc;
+  int Nd;  // design columns (N_b, or 2 N_b with the dual kernel)
   const float* f1d;     // [NH][wpad]
   const double* f1d64;  // [NH][w]
   const double* psi;

@@ -58,7 +58,7 @@ class psfm_config(C.Structure):
                 ("bad_frac", C.c_double), ("max_iter", C.c_int32), ("var_tile", C.c_int32),
                 ("cov_grid", C.c_int32), ("norm_mode", C.c_int32), ("precision", C.c_int32),
                 ("badmask", C.c_uint16), ("conv_bad", C.c_uint16), ("conv_poor", C.c_uint16),
-                ("nodata", C.c_uint16)]
+                ("nodata", C.c_uint16), ("dual", C.c_int32), ("penalty", C.c_double)]
 
 
 class psfm_solution(C.Structure):
@@ -216,7 +216,8 @@ def _workspace(op, shape, basis, cfg, n_stamps, workspace, device):
     torch = _torch()
     need = psfm_workspace_size(op, shape, basis, cfg, n_stamps)
     if need == 0:
-        raise PsfmError(1, "psfm_workspace_size")
+        # an argument the library rejects: the call itself returns the precise status
+        return None, 0
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=device)
     return workspace, need
@@ -302,6 +303,11 @@ def _stamps_arg(stamps):
     return C.cast(arr, C.POINTER(psfm_stamp)), len(stamps), arr
 
 
+def _ncoef(basis, cfg):
+    """Kernel coefficients of a solution: N_b N_s, twice that with the dual kernel."""
+    return basis_size(basis) * spatial_size(basis) * (2 if getattr(cfg, "dual", 0) else 1)
+
+
 def _ncand(basis, cfg, n_stamps):
     return n_stamps if n_stamps > 0 else cfg.grid_nx * cfg.grid_ny * cfg.max_cand
 
@@ -313,7 +319,7 @@ def psfm_solve_kernel(img, ref, var_img, var_ref, mask_img, mask_ref, basis, cfg
     shape = _shape_of(img, ref, var_img, var_ref, mask_img, mask_ref)
     sp, ns, _keep = _stamps_arg(stamps)
     ws, need = _workspace(OP_SOLVE, shape, basis, cfg, ns, workspace, img.device)
-    sol = Solution(basis_size(basis) * spatial_size(basis), _ncand(basis, cfg, ns))
+    sol = Solution(_ncoef(basis, cfg), _ncand(basis, cfg, ns))
     st = lib.psfm_solve_kernel(_ptr(img), _ptr(ref), _ptr(var_img), _ptr(var_ref), _ptr(mask_img),
                                _ptr(mask_ref), shape, sp, ns, C.byref(basis), C.byref(cfg),
                                C.byref(sol.c), _ptr(ws), need, _stream(stream))
@@ -400,7 +406,7 @@ def psfm_subtract(img, ref, var_img, var_ref, mask_img, mask_ref, basis, cfg, st
         ncov = cov_width(basis, c_ref, c_img)
         cov = torch.empty((ncov, ncov), dtype=torch.float64, device=dev)
     ws, need = _workspace(OP_SUBTRACT, shape, basis, cfg, ns, workspace, dev)
-    sol = Solution(basis_size(basis) * spatial_size(basis), _ncand(basis, cfg, ns)) if solution else None
+    sol = Solution(_ncoef(basis, cfg), _ncand(basis, cfg, ns)) if solution else None
     st = lib.psfm_subtract(_ptr(img), _ptr(ref), _ptr(var_img), _ptr(var_ref), _ptr(mask_img),
                            _ptr(mask_ref), shape, sp, ns, C.byref(basis), C.byref(cfg),
                            _ptr(cov_ref), c_ref, _ptr(cov_img), c_img if cov_img is not None else 0,
@@ -436,7 +442,7 @@ def psfm_stack(imgs, vars_, masks, sources, target_fwhm, bases, cfg, want_cov=Tr
         workspace = torch.empty(need, dtype=torch.uint8, device=dev)
     ncov = max(cov_width(b, 1, 0) for b in bases)
     cov = torch.empty((ncov, ncov), dtype=torch.float64, device=dev) if want_cov else None
-    sols = [Solution(basis_size(b) * spatial_size(b), _ncand(b, cfg, 0)) for b in bases]
+    sols = [Solution(_ncoef(b, cfg), _ncand(b, cfg, 0)) for b in bases]
     csols = (psfm_solution * n)(*[s.c for s in sols])
     ptrs = lambda ts: (C.c_void_p * n)(*[t.data_ptr() for t in ts])
     st = lib.psfm_stack(n, ptrs(imgs), ptrs(vars_), ptrs(masks), shape, sp, nsrc, float(target_fwhm),
@@ -517,7 +523,7 @@ def psfm_stack_full(imgs, vars_, masks, sources, target_fwhm, bases, cfg, clip_n
     unconv = (_like(imgs[0]), _like(imgs[0]), _like(masks[0]), _like(imgs[0], torch.int32))
     ncov = max(cov_width(b, 1, 0) for b in bases)
     cov = torch.empty((ncov, ncov), dtype=torch.float64, device=dev) if want_cov else None
-    sols = [Solution(basis_size(b) * spatial_size(b), _ncand(b, cfg, 0)) for b in bases]
+    sols = [Solution(_ncoef(b, cfg), _ncand(b, cfg, 0)) for b in bases]
     csols = (psfm_solution * n)(*[s_.c for s_ in sols])
     rej = (C.c_int32 * n)()
     ptrs = lambda ts: (vp * n)(*[t.data_ptr() for t in ts])
@@ -667,7 +673,7 @@ class Batch:
         return int(self.lib.psfm_batch_kernel_count(self.h))
 
     def solutions(self, stream=None):
-        sols = [Solution(basis_size(b) * spatial_size(b), _ncand(b, self.cfg, 0)) for b in self.bases]
+        sols = [Solution(_ncoef(b, self.cfg), _ncand(b, self.cfg, 0)) for b in self.bases]
         arr = (psfm_solution * self.n)(*[s.c for s in sols])
         st = self.lib.psfm_batch_solutions(self.h, arr, _stream(stream))
         for s, c in zip(sols, arr):

@@ -61,14 +61,17 @@ def specs(sigma, degree, h, S, **cfg):
                   var_tile=c.var_tile, cov_grid=c.cov_grid,
                   norm_mode="joint" if c.norm_mode == P.NORM_JOINT else "separate",
                   badmask=c.badmask, conv_bad=c.conv_bad, conv_poor=c.conv_poor,
-                  max_cand=c.max_cand)
+                  max_cand=c.max_cand, dual=bool(c.dual), penalty=c.penalty)
     return b, c, ob, oc
 
 
 def oracle_solution_from_gpu(sol: P.Solution, ob, W, H):
+    """The oracle's Solution holding a GPU solution's coefficients (both kernels' terms when
+    the solution has 2 N_b N_s of them: the dual kernel)."""
     n = len(O.basis_terms(ob)) * len(O.spatial_terms(ob.S))
-    coeff = np.concatenate([sol.coeff[:n], [sol.d0]])
-    return O.Solution(sol.b0, coeff, sol.d0, ob, W, H)
+    dual = sol.ncoef == 2 * n
+    coeff = np.concatenate([sol.coeff[:sol.ncoef], [sol.d0]])
+    return O.Solution(sol.b0, coeff, sol.d0, ob, W, H, dual=dual)
 
 
 def gpu_solution_from_oracle(osol: O.Solution, r_bad):

@@ -636,6 +636,20 @@ def test_dual_normal_equations_equal_ridge_least_squares():
     assert np.allclose(np.linalg.solve(M, v), ref, rtol=1e-8, atol=1e-12)
 
 
+def test_penalty_of_gaussian_terms_closed_form():
+    """p_k = sum (u^2 + v^2)^2 k_k^2 with k_k of unit L2 norm: k_k^2 is a Gaussian weight of
+    per-axis variance s^2 = sigma^2 / 2 times the polynomial squared, so for the (p, q) = (0, 0)
+    term p = E[r^4] = 8 s^4 = 2 sigma^4, and for (1, 0) p = E[r^4 u^2] / E[u^2] = 24 s^4 =
+    6 sigma^4 (Gaussian moments E u^2 = s^2, E u^4 = 3 s^4, E u^6 = 15 s^6).  The lattice sums
+    equal the integrals to ~1e-6 relative for sigma = 1.5 and h = 8 sigma."""
+    sig = 1.5
+    ob = O.Basis((sig,), (1,), 12, 0)
+    terms = O.basis_terms(ob)
+    pk = O.penalty_terms(ob)
+    for term, k in (((0, 0, 0), 2.0), ((0, 1, 0), 6.0), ((0, 0, 1), 6.0)):
+        assert abs(pk[terms.index(term)] - k * sig ** 4) <= 1e-5 * k * sig ** 4, term
+
+
 def test_dual_identical_images_give_zero_kernels():
     f = synth.elongated_pair(6, 96, 30)
     ob = O.Basis((1.0, 2.0), (2, 0), 5, 0)
