@@ -730,6 +730,7 @@ __global__ void __launch_bounds__(1024) k_norm(SysParams P) {
   if (threadIdx.x != 0) return;
   P.st->n_active = (int)n;
   P.st->chol_fail = 0;
+  P.st->refined = 0;
   if (n < 3) {
     raise_error(P.st, PSFM_ERR_TOO_FEW_STAMPS);
     return;
@@ -917,188 +918,277 @@ __device__ __forceinline__ df df_add(df a, df b) {
   return df_norm(t);
 }
 
-// 1 / sqrt(d): FP32 estimate refined by one Newton step in double-float.
-__device__ __forceinline__ df df_rsqrt(df d) {
-  const float r0 = rsqrtf(d.hi);
-  df t = df_mul(d, df{r0, 0.f});
-  t = df_mul(t, df{r0, 0.f});                    // d r0^2 ~ 1
-  const df e = df_add(df{1.f, 0.f}, df_neg(t));  // 1 - d r0^2
-  df corr = df_mul(e, df{0.5f * r0, 0.f});
-  return df_add(df{r0, 0.f}, corr);
-}
+// Panel pipeline: one launch per 32-column panel.  Launch kb applies panel kb to the whole
+// trailing matrix and, in its block 0, finishes the next diagonal block (its update by panel
+// kb, factor and inverse), so the sequential chain per panel is one block's work inside one
+// launch.  The working matrix A (Lh/Ll, lower triangle) is only ever read in the panel's own
+// column block and written beyond it; the factor goes to F (Fh/Fl), so no block reads a value
+// another block of the same launch writes.
+// Panel rows L_ik = A_ik inv(L_kk)^T are recomputed by every block that needs them from the
+// panel's block inverse (a few hundred double-float FMAs per thread) instead of a launch.
 
-__device__ __forceinline__ df df_shfl(df a, int src) {
-  return df{__shfl_sync(0xffffffffu, a.hi, src), __shfl_sync(0xffffffffu, a.lo, src)};
-}
+constexpr int kCholThreads = 512;
+constexpr int kTileLd = kNB + 1;
 
-// Diagonal block, 128 threads with the block in shared memory: column-by-column Cholesky
-// (pivot, scale, rank-1 update of the trailing block, each phase across the CTA), then the
-// inverse of the block by the same column sweep.  The inverse turns the panel solve and the
-// triangular solves into dot products with no sequential chain.
-constexpr int kDiagThreads = 128;
-__global__ void __launch_bounds__(kDiagThreads) k_chol_diag(int n, int kb, float* Lh, float* Ll,
-                                                            float2* Linv_all, DevState* st) {
-  __shared__ float2 A[kNB][kNB + 1];
-  __shared__ float2 X[kNB][kNB + 1];
-  __shared__ float2 rp[kNB];
-  __shared__ int s_fail;
-  if (st->error || st->done || st->chol_fail) return;
-  const int k0 = kb * kNB, m = min(kNB, n - k0), tid = threadIdx.x;
-  for (int q = tid; q < kNB * kNB; q += kDiagThreads) {
-    const int r = q / kNB, c = q % kNB;
-    float2 v = make_float2(r == c ? 1.f : 0.f, 0.f);
-    if (r < m && c < m && c <= r) {
-      const int64_t o = (int64_t)(k0 + r) * n + k0 + c;
-      v = make_float2(Lh[o], Ll[o]);
-    } else if (r < m && c < m) {
-      v = make_float2(0.f, 0.f);
+__device__ __forceinline__ float2 f2(df a) { return make_float2(a.hi, a.lo); }
+__device__ __forceinline__ df dfv(float2 a) { return df{a.x, a.y}; }
+
+// out[y][c] = sum_t a[y][t] inv[c][t] for y < rows (inv lower triangular with exact zeros
+// above the diagonal, so every dot product runs over all 32 terms without predicates).
+__device__ __forceinline__ void panel_rows(const float2 (*a)[kTileLd], const float2 (*inv)[kTileLd],
+                                           float2 (*out)[kTileLd], int rows) {
+  const int c = threadIdx.x & 31;
+  for (int y = threadIdx.x >> 5; y < rows; y += kCholThreads / 32) {
+    df s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+#pragma unroll 8
+    for (int t = 0; t < kNB; t += 2) {
+      df_fma(s0, dfv(a[y][t]), dfv(inv[c][t]));
+      df_fma(s1, dfv(a[y][t + 1]), dfv(inv[c][t + 1]));
     }
-    A[r][c] = v;
-    X[r][c] = make_float2(r == c ? 1.f : 0.f, 0.f);
+    out[y][c] = f2(df_add(df_norm(s0), df_norm(s1)));
   }
-  if (tid == 0) s_fail = 0;
+}
+
+// 1 / sqrt(d) for the pivots: the FP32 estimate r0 and one Newton step r0 + r0 (1 - d r0^2) / 2,
+// with the residual 1 - d r0^2 formed from exact FMA products (1 - p is exact for p near 1).
+__device__ __forceinline__ df df_rsqrt_pivot(df d) {
+  const float r0 = rsqrtf(d.hi);
+  const float a = __fmul_rn(d.hi, r0);
+  const float a_err = __fmaf_rn(d.hi, r0, -a);
+  const float p = __fmul_rn(a, r0);
+  const float p_err = __fmaf_rn(a, r0, -p);
+  const float tail = __fmaf_rn(__fmaf_rn(d.lo, r0, a_err), r0, p_err);
+  const float e = __fsub_rn(__fsub_rn(1.0f, p), tail);
+  const float corr = __fmul_rn(__fmul_rn(0.5f, r0), e);
+  const float s = __fadd_rn(r0, corr);
+  return df{s, __fsub_rn(corr, __fsub_rn(s, r0))};
+}
+
+// Cholesky factor and inverse of the 32 x 32 block T (lower triangle; rows and columns past
+// the block's size padded with the identity).  Factor: one barrier per column; thread = (row
+// i, column group g) updating columns g and g + 16; column j is scaled on the fly by the pivot
+// 1 / sqrt(T_jj), which the thread that completes T_jj (in step j - 1) computes at once, so the
+// sequential chain per column is one update plus one reciprocal square root.  Inverse: from
+// the diagonal 1 / L_ii up by doubling, [A 0; B C]^-1 = [A^-1 0; -C^-1 B A^-1 C^-1], two
+// products per level, five levels.  Lo receives L, Xf inv(L) (zeros above the diagonal), W is
+// scratch.  Returns false (uniformly) when a pivot is not positive and finite.
+__device__ bool tile_factor_inverse(float2 (*T)[kTileLd], float2 (*Lo)[kTileLd],
+                                    float2 (*W)[kTileLd], float2 (*Xf)[kTileLd], float2* rp) {
+  const int tid = threadIdx.x, i = tid >> 4, g = tid & 15;
+  for (int q = tid; q < kNB * kNB; q += kCholThreads) {
+    const int r = q >> 5, c = q & 31;
+    Lo[r][c] = make_float2(0.f, 0.f);
+    Xf[r][c] = make_float2(0.f, 0.f);
+  }
+  if (tid == 0) rp[0] = f2(df_rsqrt_pivot(dfv(T[0][0])));
   __syncthreads();
   for (int j = 0; j < kNB; ++j) {
-    // pivot and column scaling inside warp 0 (lane j computes the pivot, a shuffle spreads it)
-    if (tid < 32) {
-      df d = {A[j][j].x, A[j][j].y};
-      df r = {0.f, 0.f};
-      if (tid == j) {
-        if (!(d.hi > 0.f) || !isfinite(d.hi)) s_fail = 1;
-        r = df_rsqrt(d);
-        const df l = df_mul(d, r);
-        A[j][j] = make_float2(l.hi, l.lo);
-        rp[j] = make_float2(r.hi, r.lo);
+    const df d = dfv(T[j][j]);
+    if (!(d.hi > 0.f) || !isfinite(d.hi)) return false;  // the same d for every thread
+    const df r = dfv(rp[j]);
+    if (i >= j) {
+      const df lij = i == j ? df_mul(d, r) : df_mul(dfv(T[i][j]), r);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int c = g + 16 * q;
+        if (c > j && c <= i) {
+          df a = dfv(T[i][c]);
+          df_fma(a, df_neg(lij), df_mul(dfv(T[c][j]), r));
+          a = df_norm(a);
+          T[i][c] = f2(a);
+          if (c == i && i == j + 1) rp[i] = f2(df_rsqrt_pivot(a));
+        }
       }
-      r = df_shfl(r, j);
-      if (tid > j) {
-        const df a = df_mul(df{A[tid][j].x, A[tid][j].y}, r);
-        A[tid][j] = make_float2(a.hi, a.lo);
-      }
-    }
-    __syncthreads();
-    if (s_fail) break;
-    const int rem = kNB - j - 1;
-    for (int q = tid; q < rem * rem; q += kDiagThreads) {
-      const int i = j + 1 + q / rem, c = j + 1 + q % rem;
-      if (c <= i) {
-        df a = {A[i][c].x, A[i][c].y};
-        df_fma(a, df_neg(df{A[i][j].x, A[i][j].y}), df{A[c][j].x, A[c][j].y});
-        a = df_norm(a);
-        A[i][c] = make_float2(a.hi, a.lo);
-      }
+      if (g == 0) Lo[i][j] = f2(lij);
     }
     __syncthreads();
   }
-  if (s_fail) {
-    if (tid == 0) st->chol_fail = 1;
+  if (tid < kNB) Xf[tid][tid] = rp[tid];
+  __syncthreads();
+  for (int b = 1; b < kNB; b *= 2) {
+    // W = B A^-1 for each pair of diagonal blocks of size b (A at p0, C at p0 + b)
+    const int nout = (kNB / (2 * b)) * b * b;
+    int p0 = 0, rr = 0, cc = 0;
+    if (tid < nout) {
+      const int pair = tid / (b * b), rem = tid - pair * b * b;
+      p0 = pair * 2 * b;
+      rr = rem / b;
+      cc = rem - rr * b;
+      df s = {0.f, 0.f};
+      for (int t = cc; t < b; ++t)
+        df_fma(s, dfv(Lo[p0 + b + rr][p0 + t]), dfv(Xf[p0 + t][p0 + cc]));
+      W[p0 + b + rr][p0 + cc] = f2(df_norm(s));
+    }
+    __syncthreads();
+    if (tid < nout) {
+      df s = {0.f, 0.f};
+      for (int t = 0; t <= rr; ++t)
+        df_fma(s, dfv(Xf[p0 + b + rr][p0 + b + t]), dfv(W[p0 + b + t][p0 + cc]));
+      Xf[p0 + b + rr][p0 + cc] = f2(df_neg(df_norm(s)));
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// The first diagonal block.
+__global__ void __launch_bounds__(kCholThreads) k_chol_first(int n, const float* Lh,
+                                                             const float* Ll, float* Fh, float* Fl,
+                                                             float2* Linv_all, DevState* st) {
+  __shared__ float2 S[4][kNB][kTileLd];
+  __shared__ float2 rp[kNB];
+  if (st->error || st->done || st->chol_fail) return;
+  const int m = min(kNB, n);
+  for (int q = threadIdx.x; q < kNB * kNB; q += kCholThreads) {
+    const int r = q >> 5, c = q & 31;
+    float2 v = make_float2(r == c ? 1.f : 0.f, 0.f);
+    if (r < m && c < m) v = c <= r ? make_float2(Lh[(int64_t)r * n + c], Ll[(int64_t)r * n + c])
+                                   : make_float2(0.f, 0.f);
+    S[0][r][c] = v;
+  }
+  __syncthreads();
+  if (!tile_factor_inverse(S[0], S[1], S[2], S[3], rp)) {
+    if (threadIdx.x == 0) st->chol_fail = 1;
     return;
   }
-  // inverse: for t = 0..: row t of X scaled by 1/L_tt, then X[i][:] -= L[i][t] X[t][:]
-  for (int t = 0; t < kNB; ++t) {
-    if (tid < kNB) {
-      // 1 / L_tt is the pivot's reciprocal square root kept from the factorisation
-      const df x = df_mul(df{X[t][tid].x, X[t][tid].y}, df{rp[t].x, rp[t].y});
-      X[t][tid] = make_float2(x.hi, x.lo);
-    }
-    __syncthreads();
-    const int rem = kNB - t - 1;
-    for (int q = tid; q < rem * kNB; q += kDiagThreads) {
-      const int i = t + 1 + q / kNB, c = q % kNB;
-      df x = {X[i][c].x, X[i][c].y};
-      df_fma(x, df_neg(df{A[i][t].x, A[i][t].y}), df{X[t][c].x, X[t][c].y});
-      x = df_norm(x);
-      X[i][c] = make_float2(x.hi, x.lo);
-    }
-    __syncthreads();
-  }
-  float2* Linv = Linv_all + (int64_t)kb * kNB * kNB;
-  for (int q = tid; q < kNB * kNB; q += kDiagThreads) {
-    const int r = q / kNB, c = q % kNB;
-    Linv[q] = X[r][c];
+  for (int q = threadIdx.x; q < kNB * kNB; q += kCholThreads) {
+    const int r = q >> 5, c = q & 31;
+    Linv_all[q] = S[3][r][c];
     if (r < m && c <= r) {
-      const int64_t o = (int64_t)(k0 + r) * n + k0 + c;
-      Lh[o] = A[r][c].x;
-      Ll[o] = A[r][c].y;
+      Fh[(int64_t)r * n + c] = S[1][r][c].x;
+      Fl[(int64_t)r * n + c] = S[1][r][c].y;
     }
   }
 }
 
-// Rows below the diagonal block: L_ik = A_ik inv(L_kk)^T, one output element per thread
-// (8 rows x 32 columns per CTA), no sequential chain.
-__global__ void __launch_bounds__(256) k_chol_trsm(int n, int kb, float* Lh, float* Ll,
-                                                   const float2* Linv_all, const DevState* st) {
-  __shared__ float2 Li[kNB][kNB + 1];
-  __shared__ float2 Ar[8][kNB + 1];
+// Launch kb (panel kb full, kb + 1 < number of panels).  Block 0: rows of block kb + 1 of the
+// panel, their update of diagonal block kb + 1, its factor and inverse.  Blocks 1..: one 16 x 16
+// tile (ti, tj) of the trailing lower triangle past block kb + 1's own 32 x 32 block; diagonal
+// tiles also store their 16 panel rows into F.
+__global__ void __launch_bounds__(kCholThreads) k_chol_panel(int n, int kb, float* Lh, float* Ll,
+                                                             float* Fh, float* Fl,
+                                                             float2* Linv_all, DevState* st) {
+  __shared__ float2 S[5][kNB][kTileLd];
+  __shared__ float2 rp[kNB];
   if (st->error || st->done || st->chol_fail) return;
-  const int k0 = kb * kNB, m = min(kNB, n - k0);
+  const int tid = threadIdx.x;
+  const int k0 = kb * kNB, base = k0 + kNB;
   const float2* Linv = Linv_all + (int64_t)kb * kNB * kNB;
-  for (int q = threadIdx.x; q < kNB * kNB; q += blockDim.x) Li[q / kNB][q % kNB] = Linv[q];
-  const int rr = threadIdx.x / kNB, c = threadIdx.x % kNB;
-  const int row = k0 + m + blockIdx.x * 8 + rr;
-  float2 a = make_float2(0.f, 0.f);
-  if (row < n && c < m) {
-    const int64_t o = (int64_t)row * n + k0 + c;
-    a = make_float2(Lh[o], Ll[o]);
+  float2(*Li)[kTileLd] = S[0];
+  for (int q = tid; q < kNB * kNB; q += kCholThreads) Li[q >> 5][q & 31] = Linv[q];
+  if (blockIdx.x == 0) {
+    const int mb = min(kNB, n - base);
+    float2(*Ar)[kTileLd] = S[4];
+    float2(*Pn)[kTileLd] = S[1];
+    float2(*T)[kTileLd] = S[2];
+    for (int q = tid; q < kNB * kNB; q += kCholThreads) {
+      const int r = q >> 5, c = q & 31;
+      float2 a = make_float2(0.f, 0.f), tv = make_float2(r == c ? 1.f : 0.f, 0.f);
+      if (r < mb) {
+        const int64_t o = (int64_t)(base + r) * n;
+        a = make_float2(Lh[o + k0 + c], Ll[o + k0 + c]);
+        if (c < mb) tv = c <= r ? make_float2(Lh[o + base + c], Ll[o + base + c])
+                                : make_float2(0.f, 0.f);
+      }
+      Ar[r][c] = a;
+      T[r][c] = tv;
+    }
+    __syncthreads();
+    panel_rows(Ar, Li, Pn, kNB);
+    __syncthreads();
+    // panel rows of block kb + 1 into F; T -= Pn Pn^T on the lower triangle
+    for (int q = tid; q < kNB * kNB; q += kCholThreads) {
+      const int r = q >> 5, c = q & 31;
+      if (r < mb) {
+        const int64_t o = (int64_t)(base + r) * n + k0 + c;
+        Fh[o] = Pn[r][c].x;
+        Fl[o] = Pn[r][c].y;
+      }
+    }
+    {
+      const int r = tid >> 4, cg = tid & 15;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int c = cg + 16 * q;
+        if (c <= r && r < mb) {
+          df s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+#pragma unroll 8
+          for (int t = 0; t < kNB; t += 2) {
+            df_fma(s0, dfv(Pn[r][t]), dfv(Pn[c][t]));
+            df_fma(s1, dfv(Pn[r][t + 1]), dfv(Pn[c][t + 1]));
+          }
+          T[r][c] = f2(df_add(dfv(T[r][c]), df_neg(df_add(df_norm(s0), df_norm(s1)))));
+        }
+      }
+    }
+    __syncthreads();
+    // Li and Ar are free from here: Xf and W reuse them
+    if (!tile_factor_inverse(T, S[3], S[4], S[0], rp)) {
+      if (tid == 0) st->chol_fail = 1;
+      return;
+    }
+    float2* Lnext = Linv_all + (int64_t)(kb + 1) * kNB * kNB;
+    for (int q = tid; q < kNB * kNB; q += kCholThreads) {
+      const int r = q >> 5, c = q & 31;
+      Lnext[q] = S[0][r][c];
+      if (r < mb && c <= r) {
+        const int64_t o = (int64_t)(base + r) * n + base + c;
+        Fh[o] = S[3][r][c].x;
+        Fl[o] = S[3][r][c].y;
+      }
+    }
+    return;
   }
-  Ar[rr][c] = a;
-  __syncthreads();
-  if (row < n && c < m) {
-    df sacc = {0.f, 0.f};
-    for (int t = 0; t <= c; ++t) df_fma(sacc, df{Ar[rr][t].x, Ar[rr][t].y}, df{Li[c][t].x, Li[c][t].y});
-    sacc = df_norm(sacc);
-    const int64_t o = (int64_t)row * n + k0 + c;
-    Lh[o] = sacc.hi;
-    Ll[o] = sacc.lo;
-  }
-}
-
-// Trailing update of the lower triangle: A_ij -= L_i,panel . L_j,panel, 16 x 16 tiles.
-__global__ void __launch_bounds__(256) k_chol_update(int n, int kb, float* Lh, float* Ll,
-                                                     const DevState* st) {
-  __shared__ float2 Pi[16][kNB + 1];
-  __shared__ float2 Pj[16][kNB + 1];
-  if (st->error || st->done || st->chol_fail) return;
-  const int k0 = kb * kNB, m = min(kNB, n - k0);
-  const int base = k0 + m;
+  // trailing tile
   const int nt = (n - base + 15) / 16;
-  int t = blockIdx.x, ti = 0;
+  int t = blockIdx.x - 1, ti = 0;
   while (t >= ti + 1) {
     t -= ti + 1;
     ++ti;
   }
   const int tj = t;
-  if (ti >= nt) return;
+  if (ti >= nt || (ti < 2 && tj < 2)) return;  // the 32 x 32 diagonal block is block 0's
   const int r0 = base + ti * 16, c0 = base + tj * 16;
-  for (int i = threadIdx.x; i < 16 * kNB; i += blockDim.x) {
-    const int r = i / kNB, c = i % kNB;
-    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-    if (r0 + r < n && c < m) {
-      const int64_t o = (int64_t)(r0 + r) * n + k0 + c;
+  const bool diag = ti == tj;
+  float2(*Ar)[kTileLd] = S[1];  // rows 0..15: tile rows, 16..31: tile columns
+  float2(*Pn)[kTileLd] = S[2];
+  for (int q = tid; q < kNB * kNB; q += kCholThreads) {
+    const int r = q >> 5, c = q & 31;
+    const int row = r < 16 ? r0 + r : c0 + r - 16;
+    float2 a = make_float2(0.f, 0.f);
+    if (row < n && (r < 16 || !diag)) {
+      const int64_t o = (int64_t)row * n + k0 + c;
       a = make_float2(Lh[o], Ll[o]);
     }
-    if (c0 + r < n && c < m) {
-      const int64_t o = (int64_t)(c0 + r) * n + k0 + c;
-      b = make_float2(Lh[o], Ll[o]);
-    }
-    Pi[r][c] = a;
-    Pj[r][c] = b;
+    Ar[r][c] = a;
   }
   __syncthreads();
-  const int y = threadIdx.x / 16, x = threadIdx.x % 16;
+  panel_rows(Ar, Li, Pn, diag ? 16 : kNB);
+  __syncthreads();
+  const int y = (tid >> 4) & 15, x = tid & 15;
   const int row = r0 + y, col = c0 + x;
-  if (row < n && col < n && col <= row) {
+  const int xc = diag ? x : 16 + x;  // the column's panel row in Pn
+  if (tid < 256 && row < n && col < n && col <= row) {
     df s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
-    for (int c = 0; c < m; c += 2) {
-      df_fma(s0, df{Pi[y][c].x, Pi[y][c].y}, df{Pj[x][c].x, Pj[x][c].y});
-      if (c + 1 < m) df_fma(s1, df{Pi[y][c + 1].x, Pi[y][c + 1].y}, df{Pj[x][c + 1].x, Pj[x][c + 1].y});
+#pragma unroll 8
+    for (int c = 0; c < kNB; c += 2) {
+      df_fma(s0, dfv(Pn[y][c]), dfv(Pn[xc][c]));
+      df_fma(s1, dfv(Pn[y][c + 1]), dfv(Pn[xc][c + 1]));
     }
     const int64_t o = (int64_t)row * n + col;
-    df sum = df_add(df_norm(s0), df_norm(s1));
-    df a = df{Lh[o], Ll[o]};
-    a = df_add(a, df_neg(sum));
+    const df a = df_add(df{Lh[o], Ll[o]}, df_neg(df_add(df_norm(s0), df_norm(s1))));
     Lh[o] = a.hi;
     Ll[o] = a.lo;
+  }
+  if (diag) {
+    for (int q = tid; q < 16 * kNB; q += kCholThreads) {
+      const int r = q >> 5, c = q & 31;
+      if (r0 + r < n) {
+        const int64_t o = (int64_t)(r0 + r) * n + k0 + c;
+        Fh[o] = Pn[r][c].x;
+        Fl[o] = Pn[r][c].y;
+      }
+    }
   }
 }
 
@@ -1111,84 +1201,116 @@ __device__ __forceinline__ df warp_sum_df(df v) {
   return v;
 }
 
-// L z = b then L^T y = z in double-float, with the block inverses: per panel a dot-product
-// phase (warp per row) and a 32 x 32 inverse application (warp per row); x_out = x_in + y.
-__global__ void __launch_bounds__(1024) k_chol_solve(int n, const float* Lh, const float* Ll,
-                                                     const float2* Linv_all, const double* b,
-                                                     const double* x_in, double* x_out,
-                                                     const DevState* st) {
-  extern __shared__ float2 ys[];  // [n] + [33][33] + [32]
+// L z = b then L^T y = z in double-float with the block inverses: per 32-row block a
+// dot-product phase (warp per row over the solved part) and a 32 x 32 inverse application
+// (warp per row), one CTA; x_out = x_in + y.  Each block's inverse entries are loaded before
+// its dot products so that their latency overlaps; the backward phase combines the 32 warps'
+// column partials with a shuffle tree.
+//
+// Refinement: the factor's relative error e0 (about cond(M) times the double-float rounding)
+// is also the contraction of each refinement step, so after a step whose correction is y the
+// error left is about (|y| / |x|) |y|.  mode 1 (the first step) records whether |y| <= 1e-5 |x|
+// (error left below about 1e-10 |x|, under the FP64 residual's own floor for these systems);
+// mode 2 (the second step) is skipped when it did.
+constexpr int kSolveThreads = 1024;
+
+__global__ void __launch_bounds__(kSolveThreads) k_chol_solve(int n, const float* Lh,
+                                                              const float* Ll,
+                                                              const float2* Linv_all,
+                                                              const double* b, const double* x_in,
+                                                              double* x_out, DevState* st,
+                                                              int mode) {
+  extern __shared__ float2 ys[];  // [n] + [32][33] + [32]
   float2* pw = ys + n;
-  float2* zb = pw + 33 * 33;
-  if (st->error || st->done || st->chol_fail) return;
+  float2* zb = pw + 32 * 33;
+  if (st->error || st->done || st->chol_fail || (mode == 2 && st->refined)) return;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int i = tid; i < n; i += blockDim.x) {
-    const df d = df_split(b[i]);
-    ys[i] = make_float2(d.hi, d.lo);
-  }
+  for (int i = tid; i < n; i += blockDim.x) ys[i] = f2(df_split(b[i]));
   __syncthreads();
   const int nb = (n + kNB - 1) / kNB;
   for (int bk = 0; bk < nb; ++bk) {
     const int k0 = bk * kNB, m = min(kNB, n - k0);
+    const float2* Li = Linv_all + (int64_t)bk * kNB * kNB;
+    const float2 li = (w < m && lane <= w) ? Li[w * kNB + lane] : make_float2(0.f, 0.f);
     df sacc = {0.f, 0.f};
     if (w < m)
       for (int c = lane; c < k0; c += 32) {
         const int64_t o = (int64_t)(k0 + w) * n + c;
-        df_fma(sacc, df{Lh[o], Ll[o]}, df{ys[c].x, ys[c].y});
+        df_fma(sacc, df{Lh[o], Ll[o]}, dfv(ys[c]));
       }
     sacc = warp_sum_df(df_norm(sacc));
-    if (w < m && lane == 0) {
-      const df y = df_add(df{ys[k0 + w].x, ys[k0 + w].y}, df_neg(sacc));
-      zb[w] = make_float2(y.hi, y.lo);
-    }
+    if (w < m && lane == 0) zb[w] = f2(df_add(dfv(ys[k0 + w]), df_neg(sacc)));
     __syncthreads();
-    const float2* Li = Linv_all + (int64_t)bk * kNB * kNB;
     if (w < m) {
       df t2 = {0.f, 0.f};
-      if (lane <= w && lane < m) df_fma(t2, df{Li[w * kNB + lane].x, Li[w * kNB + lane].y}, df{zb[lane].x, zb[lane].y});
+      if (lane < m) df_fma(t2, dfv(li), dfv(zb[lane]));
       t2 = warp_sum_df(df_norm(t2));
-      if (lane == 0) ys[k0 + w] = make_float2(t2.hi, t2.lo);
+      if (lane == 0) ys[k0 + w] = f2(t2);
     }
     __syncthreads();
   }
   for (int bk = nb - 1; bk >= 0; --bk) {
     const int k0 = bk * kNB, m = min(kNB, n - k0);
+    const float2* Li = Linv_all + (int64_t)bk * kNB * kNB;
+    const float2 li = (w < m && lane >= w && lane < m) ? Li[lane * kNB + w]
+                                                       : make_float2(0.f, 0.f);
     df sacc = {0.f, 0.f};
     if (lane < m)
       for (int i = k0 + m + w; i < n; i += 32) {
         const int64_t o = (int64_t)i * n + k0 + lane;
-        df_fma(sacc, df{Lh[o], Ll[o]}, df{ys[i].x, ys[i].y});
+        df_fma(sacc, df{Lh[o], Ll[o]}, dfv(ys[i]));
       }
-    sacc = df_norm(sacc);
-    pw[w * 33 + lane] = make_float2(sacc.hi, sacc.lo);
+    pw[w * 33 + lane] = f2(df_norm(sacc));
     __syncthreads();
-    if (tid < m) {
-      df z = {ys[k0 + tid].x, ys[k0 + tid].y};
-      for (int q = 0; q < 32; ++q) z = df_add(z, df_neg(df{pw[q * 33 + tid].x, pw[q * 33 + tid].y}));
-      zb[tid] = make_float2(z.hi, z.lo);
+    if (w < m) {
+      // column w: the partials of the 32 warps, one per lane, summed by a shuffle tree
+      const df z = warp_sum_df(dfv(pw[lane * 33 + w]));
+      if (lane == 0) zb[w] = f2(df_add(dfv(ys[k0 + w]), df_neg(z)));
     }
     __syncthreads();
-    const float2* Li = Linv_all + (int64_t)bk * kNB * kNB;
     if (w < m) {
       // x_w = sum_j inv(L)[j][w] z_j, j >= w
       df t2 = {0.f, 0.f};
-      if (lane >= w && lane < m) df_fma(t2, df{Li[lane * kNB + w].x, Li[lane * kNB + w].y}, df{zb[lane].x, zb[lane].y});
+      if (lane < m) df_fma(t2, dfv(li), dfv(zb[lane]));
       t2 = warp_sum_df(df_norm(t2));
-      if (lane == 0) ys[k0 + w] = make_float2(t2.hi, t2.lo);
+      if (lane == 0) ys[k0 + w] = f2(t2);
     }
     __syncthreads();
   }
+  float ymax = 0.f, xmax = 0.f;
   for (int i = tid; i < n; i += blockDim.x) {
     const double y = (double)ys[i].x + (double)ys[i].y;
-    x_out[i] = x_in ? x_in[i] + y : y;
+    const double x = x_in ? x_in[i] + y : y;
+    x_out[i] = x;
+    ymax = fmaxf(ymax, (float)fabs(y));
+    xmax = fmaxf(xmax, (float)fabs(x));
+  }
+  if (mode != 1) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+    xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+  }
+  __syncthreads();  // pw is reused
+  if (lane == 0) pw[w] = make_float2(ymax, xmax);
+  __syncthreads();
+  if (w == 0) {
+    float2 v = lane < (int)(blockDim.x >> 5) ? pw[lane] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x = fmaxf(v.x, __shfl_xor_sync(0xffffffffu, v.x, o));
+      v.y = fmaxf(v.y, __shfl_xor_sync(0xffffffffu, v.y, o));
+    }
+    // NaN compares false: not converged
+    if (lane == 0) st->refined = v.x <= 1e-5f * v.y ? 1 : 0;
   }
 }
 
 // r = b - M x in FP64 (one warp per row).
 __global__ void __launch_bounds__(256) k_residual(int n, const double* M, const double* pdiag,
                                                   const double* b, const double* x, double* r,
-                                                  const DevState* st) {
-  if (st->error || st->done || st->chol_fail) return;
+                                                  const DevState* st, int mode) {
+  if (st->error || st->done || st->chol_fail || (mode == 2 && st->refined)) return;
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (row >= n) return;
   double s = 0.0;
@@ -1547,6 +1669,8 @@ void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b) {
   b.rinv = ws.take<float2>((size_t)((p.Nsys + kNB - 1) / kNB) * kNB * kNB);
   b.Lh = ws.take<float>((size_t)p.Nsys * p.Nsys);
   b.Ll = ws.take<float>((size_t)p.Nsys * p.Nsys);
+  b.Fh = ws.take<float>((size_t)p.Nsys * p.Nsys);
+  b.Fl = ws.take<float>((size_t)p.Nsys * p.Nsys);
   b.x = ws.take<double>(p.Nsys);
   b.pdiag = ws.take<double>(p.Nsys);
   b.y = ws.take<double>(p.Nsys);
@@ -1672,7 +1796,7 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   const int asm_chunk = (40 * 1024) / (N1 * N1 * (int)sizeof(double));
   const size_t sm_asm = (sizeof(double) * N1 * N1 + sizeof(int)) * (size_t)asm_chunk;
   const int npanel = (N + kNB - 1) / kNB;
-  const size_t sm_solve = sizeof(float2) * ((size_t)N + 33 * 33 + 32);
+  const size_t sm_solve = sizeof(float2) * ((size_t)N + 32 * 33 + 32);
   if (sm_solve > 200 * 1024) return PSFM_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sm_solve) != cudaSuccess)
@@ -1704,24 +1828,22 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
     k_rhs<<<(N * 32 + 255) / 256, 256, 0, s>>>(sy);
     prof_end("system", s, p.cfg.dual ? 4 : 3);
     prof_begin("cholesky", s);
-    for (int kb = 0; kb < npanel; ++kb) {
-      k_chol_diag<<<1, kDiagThreads, 0, s>>>(N, kb, b.Lh, b.Ll, b.rinv, st);
-      const int k0 = kb * kNB, m = (N - k0) < kNB ? N - k0 : kNB;
-      const int rest = N - k0 - m;
-      if (rest > 0) {
-        k_chol_trsm<<<(rest + 7) / 8, 256, 0, s>>>(N, kb, b.Lh, b.Ll, b.rinv, st);
-        const int nt = (rest + 15) / 16;
-        k_chol_update<<<nt * (nt + 1) / 2, 256, 0, s>>>(N, kb, b.Lh, b.Ll, st);
-      }
+    k_chol_first<<<1, kCholThreads, 0, s>>>(N, b.Lh, b.Ll, b.Fh, b.Fl, b.rinv, st);
+    for (int kb = 0; kb + 1 < npanel; ++kb) {
+      const int nt = (N - (kb + 1) * kNB + 15) / 16;
+      k_chol_panel<<<1 + nt * (nt + 1) / 2, kCholThreads, 0, s>>>(N, kb, b.Lh, b.Ll, b.Fh, b.Fl,
+                                                                   b.rinv, st);
     }
-    k_chol_solve<<<1, 1024, sm_solve, s>>>(N, b.Lh, b.Ll, b.rinv, b.v, nullptr, b.x, st);
-    for (int ref = 0; ref < 2; ++ref) {
-      k_residual<<<(N * 32 + 255) / 256, 256, 0, s>>>(N, b.M, b.pdiag, b.v, b.x, b.y, st);
-      k_chol_solve<<<1, 1024, sm_solve, s>>>(N, b.Lh, b.Ll, b.rinv, b.y, b.x, b.x, st);
+    k_chol_solve<<<1, kSolveThreads, sm_solve, s>>>(N, b.Fh, b.Fl, b.rinv, b.v, nullptr, b.x,
+                                                    st, 0);
+    for (int mode = 1; mode <= 2; ++mode) {
+      k_residual<<<(N * 32 + 255) / 256, 256, 0, s>>>(N, b.M, b.pdiag, b.v, b.x, b.y, st, mode);
+      k_chol_solve<<<1, kSolveThreads, sm_solve, s>>>(N, b.Fh, b.Fl, b.rinv, b.y, b.x, b.x,
+                                                      st, mode);
     }
     k_store_solution<<<(N + 255) / 256, 256, 0, s>>>(N, sy.joint, b.x, dsol, st);
     k_lu_solve<<<1, 1024, 0, s>>>(N, sy.joint, b.M, b.pdiag, b.v, b.L, b.y, b.piv, dsol, st);
-    prof_end("cholesky", s, 3 * npanel + 7);
+    prof_end("cholesky", s, npanel + 7);
     prof_begin("chi2_reject", s);
     chi2<<<p.nreg, 256, (sizeof(double) + sizeof(float2)) * p.Nd + 16, s>>>(cq);
     k_reject<<<1, 1024, 0, s>>>(p.nreg, p.max_cand, p.cfg.max_iter, p.cfg.reject_nsigma, b.cand,

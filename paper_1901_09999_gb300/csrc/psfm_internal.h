@@ -35,7 +35,7 @@ struct DevState {
   int32_t r_bad;        // CONV.BAD radius
   int32_t n_cand_total; // detections seen
   int32_t chol_fail;    // Cholesky met a non-positive pivot: LU fallback
-  int32_t pad1;
+  int32_t refined;      // the first refinement step's correction was small: skip the second
   double sum_var_conv;  // sum of V' over unmasked output pixels
   double sum_var_img;   // sum of V2 over unmasked output pixels
   double n_unmasked;    // count of unmasked output pixels

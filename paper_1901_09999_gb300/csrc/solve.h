@@ -35,8 +35,10 @@ struct SolveBuffers {
   double* v;  // [Nsys]
   double* L;  // [Nsys][Nsys] factor
   float2* rinv;  // [Nsys/32][32][32] inverses of the diagonal blocks (double-float)
-  float* Lh;     // [Nsys][Nsys] double-float Cholesky factor, high parts
+  float* Lh;     // [Nsys][Nsys] double-float working copy of M (lower triangle), high parts
   float* Ll;     // low parts
+  float* Fh;     // [Nsys][Nsys] double-float Cholesky factor L by rows (lower), high parts
+  float* Fl;     // low parts
   double* x;     // [Nsys] solution being refined
   double* pdiag; // [Nsys] penalty on the diagonal (dual kernel; zeros otherwise)
   double* y;  // [Nsys]
