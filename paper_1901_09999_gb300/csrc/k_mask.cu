@@ -13,20 +13,29 @@
 namespace psfm {
 namespace {
 
-__global__ void k_mask_bits(const uint16_t* m1, const uint16_t* m2, int W, int H, int64_t pitch,
-                            int nwords, uint16_t badmask, uint32_t* bits) {
-  const int y = blockIdx.y;
+// Tiles of 256 pixels x kTileRows rows: a CTA walks its rows, one pixel per thread.
+constexpr int kTileRows = 32;
+constexpr int kTileWords = 8;  // 256 pixels
+
+__global__ void __launch_bounds__(256) k_mask_bits(const uint16_t* m1, const uint16_t* m2, int W,
+                                                   int H, int64_t pitch, int nwords,
+                                                   uint16_t badmask, uint32_t* bits) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  bool bad = false;
-  if (x < W) {
-    const int64_t o = (int64_t)y * pitch + x;
-    uint16_t m = m1[o];
-    if (m2) m |= m2[o];
-    bad = (m & badmask) != 0;
-  }
-  const uint32_t word = __ballot_sync(0xffffffffu, bad);
+  const int y0 = blockIdx.y * kTileRows;
   const int wx = x >> 5;
-  if ((threadIdx.x & 31) == 0 && wx < nwords) bits[(int64_t)y * nwords + wx] = word;
+  const int rows = min(kTileRows, H - y0);
+#pragma unroll 4
+  for (int r = 0; r < rows; ++r) {
+    bool bad = false;
+    if (x < W) {
+      const int64_t o = (int64_t)(y0 + r) * pitch + x;
+      uint16_t m = m1[o];
+      if (m2) m |= m2[o];
+      bad = (m & badmask) != 0;
+    }
+    const uint32_t word = __ballot_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && wx < nwords) bits[(int64_t)(y0 + r) * nwords + wx] = word;
+  }
 }
 
 // Bits beyond the row end count as masked (off-image).
@@ -63,52 +72,73 @@ __global__ void k_mask_hdilate(const uint32_t* bits, int W, int H, int nwords, i
   hb_poor[(int64_t)y * nwords + wx] = hdilate(p, c, n, h);
 }
 
-// One warp per (row, 32-pixel word): lanes load the rows within h above and below, the warp
-// ORs them (vertical dilation), then each lane writes one output pixel.
+// Vertical dilation and output, one CTA per tile of 256 pixels x kTileRows rows: the tile's
+// horizontally dilated words and the h rows above and below go to shared memory, each thread
+// ORs one word's column window (r_bad rows for CONV.BAD, h for CONV.POOR), then the CTA writes
+// the tile's pixels a row at a time (one pixel per thread, consecutive addresses).
 // mode 0: out = m1 | m2 with CONV.BAD near a bad pixel, else CONV.POOR;
 // mode 1 (first pass of the dual kernel): out holds only the two proximity flags;
 // mode 2 (second pass): the flags already in out are ORed with this pass's, then mode 0's rule.
-__global__ void k_mask_out(const uint32_t* hb_bad, const uint32_t* hb_poor, const uint16_t* m1,
-                           const uint16_t* m2, int W, int H, int64_t pitch, int nwords,
-                           int r_fixed, const DevState* st, int h, uint16_t conv_bad,
-                           uint16_t conv_poor, int mode, uint16_t* out) {
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (gw >= (int64_t)H * nwords) return;  // uniform per warp
-  const int y = (int)(gw / nwords), wx = (int)(gw - (int64_t)y * nwords);
+__global__ void __launch_bounds__(256) k_mask_out(const uint32_t* hb_bad, const uint32_t* hb_poor,
+                                                  const uint16_t* m1, const uint16_t* m2, int W,
+                                                  int H, int64_t pitch, int nwords, int r_fixed,
+                                                  const DevState* st, int h, uint16_t conv_bad,
+                                                  uint16_t conv_poor, int mode, uint16_t* out) {
+  __shared__ uint32_t sb[kTileRows + 2 * PSFM_MAX_HALF_WIDTH][kTileWords];
+  __shared__ uint32_t sp[kTileRows + 2 * PSFM_MAX_HALF_WIDTH][kTileWords];
+  __shared__ uint32_t vbs[kTileRows][kTileWords], vps[kTileRows][kTileWords];
+  const int tid = threadIdx.x;
+  const int wx0 = blockIdx.x * kTileWords, y0 = blockIdx.y * kTileRows;
   const int rb = r_fixed >= 0 ? r_fixed : (r_fixed == -2 ? st->r_bad2 : st->r_bad);
-  uint32_t vb = 0, vp = 0;
-  for (int d = lane - h; d <= h; d += 32) {
-    const int yy = y + d;
-    const bool off = yy < 0 || yy >= H;
-    const uint32_t wb = off ? 0xffffffffu : hb_bad[(int64_t)yy * nwords + wx];
-    const uint32_t wp = off ? 0xffffffffu : hb_poor[(int64_t)yy * nwords + wx];
-    if ((d < 0 ? -d : d) <= rb) vb |= wb;
-    vp |= wp;
+  const int nr = kTileRows + 2 * h;
+  for (int q = tid; q < nr * kTileWords; q += blockDim.x) {
+    const int r = q / kTileWords, c = q - r * kTileWords;
+    const int yy = y0 - h + r, wx = wx0 + c;
+    uint32_t wb = 0xffffffffu, wp = 0xffffffffu;  // rows off the image count as masked
+    if (yy >= 0 && yy < H) {
+      wb = wx < nwords ? hb_bad[(int64_t)yy * nwords + wx] : 0u;
+      wp = wx < nwords ? hb_poor[(int64_t)yy * nwords + wx] : 0u;
+    }
+    sb[r][c] = wb;
+    sp[r][c] = wp;
   }
-  vb = __reduce_or_sync(0xffffffffu, vb);
-  vp = __reduce_or_sync(0xffffffffu, vp);
-  const int x = wx * 32 + lane;
+  __syncthreads();
+  {
+    const int r = tid / kTileWords, c = tid - r * kTileWords;
+    uint32_t vb = 0, vp = 0;
+    for (int d = -h; d <= h; ++d) {
+      if ((d < 0 ? -d : d) <= rb) vb |= sb[r + h + d][c];
+      vp |= sp[r + h + d][c];
+    }
+    vbs[r][c] = vb;
+    vps[r][c] = vp;
+  }
+  __syncthreads();
+  const int x = wx0 * 32 + tid;
   if (x >= W) return;
-  const uint32_t bit = 1u << lane;
-  const int64_t o = (int64_t)y * pitch + x;
-  bool nb = (vb & bit) != 0, np = (vp & bit) != 0;
-  if (mode == 1) {
-    out[o] = (uint16_t)((nb ? conv_bad : 0) | (np ? conv_poor : 0));
-    return;
+  const uint32_t bit = 1u << (tid & 31);
+  const int wc = tid >> 5;
+  const int rows = min(kTileRows, H - y0);
+  for (int r = 0; r < rows; ++r) {
+    const int64_t o = (int64_t)(y0 + r) * pitch + x;
+    bool nb = (vbs[r][wc] & bit) != 0, np = (vps[r][wc] & bit) != 0;
+    if (mode == 1) {
+      out[o] = (uint16_t)((nb ? conv_bad : 0) | (np ? conv_poor : 0));
+      continue;
+    }
+    if (mode == 2) {
+      const uint16_t prev = out[o];
+      nb = nb || (prev & conv_bad);
+      np = np || (prev & conv_poor);
+    }
+    uint16_t m = m1[o];
+    if (m2) m |= m2[o];
+    if (nb)
+      m |= conv_bad;
+    else if (np)
+      m |= conv_poor;
+    out[o] = m;
   }
-  if (mode == 2) {
-    const uint16_t prev = out[o];
-    nb = nb || (prev & conv_bad);
-    np = np || (prev & conv_poor);
-  }
-  uint16_t m = m1[o];
-  if (m2) m |= m2[o];
-  if (nb)
-    m |= conv_bad;
-  else if (np)
-    m |= conv_poor;
-  out[o] = m;
 }
 
 // r_bad from the kernel at the image centre (xt = yt = 0, so only the constant spatial term
@@ -247,14 +277,14 @@ cudaError_t launch_mask(const Plan& p, const ApplyBuffers& b, const uint16_t* mr
   // second pass (both input masks still form the output bits)
   const uint16_t* src = dual_pass == 2 ? mimg : mref;
   dim3 blk(256);
-  k_mask_bits<<<dim3((p.W + 255) / 256, p.H), blk, 0, st>>>(src, nullptr, p.W, p.H, p.pitch,
-                                                            nwords, p.cfg.badmask, b.bits);
+  const dim3 tiles((p.W + 255) / 256, (p.H + kTileRows - 1) / kTileRows);
+  k_mask_bits<<<tiles, blk, 0, st>>>(src, nullptr, p.W, p.H, p.pitch, nwords, p.cfg.badmask,
+                                     b.bits);
   k_mask_hdilate<<<dim3((nwords + 127) / 128, p.H), 128, 0, st>>>(
       b.bits, p.W, p.H, nwords, rsel, b.st, p.h, b.hb_bad, b.hb_poor);
-  const int64_t warps = (int64_t)p.H * nwords;
-  k_mask_out<<<(unsigned)((warps * 32 + 255) / 256), blk, 0, st>>>(
-      b.hb_bad, b.hb_poor, mref, mimg, p.W, p.H, p.pitch, nwords, rsel, b.st, p.h,
-      p.cfg.conv_bad, p.cfg.conv_poor, dual_pass, out);
+  k_mask_out<<<tiles, blk, 0, st>>>(b.hb_bad, b.hb_poor, mref, mimg, p.W, p.H, p.pitch, nwords,
+                                    rsel, b.st, p.h, p.cfg.conv_bad, p.cfg.conv_poor, dual_pass,
+                                    out);
   return cudaGetLastError();
 }
 

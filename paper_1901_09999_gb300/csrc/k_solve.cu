@@ -1648,6 +1648,7 @@ void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b) {
   const int nwords = (p.W + 31) / 32;
   b.hist = ws.take<uint32_t>(3 * 2048);
   b.badbits = ws.take<uint32_t>((size_t)p.H * nwords);
+  b.keys = ws.take<uint32_t>((size_t)p.H * p.W);
   b.bin_val = ws.take<float>((size_t)p.nreg * kBinCap);
   b.bin_idx = ws.take<int32_t>((size_t)p.nreg * kBinCap);
   b.bin_cnt = ws.take<int32_t>(p.nreg);

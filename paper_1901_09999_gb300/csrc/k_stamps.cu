@@ -3,7 +3,10 @@
 // no masked pixel in the footprint that the kernel fit reads.
 //
 //   background: lower median of S over pixels unmasked in both images, found exactly by a
-//               three-pass radix select on order-preserving 32-bit keys (11 + 11 + 10 bits);
+//               three-pass radix select on order-preserving 32-bit keys (11 + 11 + 10 bits):
+//               the first pass reads the images and masks once and writes every pixel's key
+//               (0 for a masked pixel, a value no finite S takes) and the bad-bit plane, the
+//               other two passes and the detection read the 4-byte keys;
 //   peak:       S beats its 8 neighbours under the order (value, -linear index);
 //   footprint:  no bad bit within Chebyshev radius s + h, read from a 1-bit-per-pixel plane;
 //   ranking:    detections go to per-subregion bins, then each subregion keeps its
@@ -34,57 +37,101 @@ struct HistParams {
   const float* i2;
   const uint16_t* m1;
   const uint16_t* m2;
-  int W, H;
+  int W, H, nwords;
   int64_t pitch;
   uint16_t badmask;
-  int pass;
+  uint32_t* keys;  // [H][W]
+  uint32_t* bits;  // [H][nwords] bad bits of m1 | m2
   uint32_t* hist;
   DevState* st;
 };
 
-__global__ void k_median_hist(HistParams P) {
+// Adds a warp's bins to the block histogram: sky pixels crowd into a few bins, so one
+// shared-memory atomic per distinct bin per warp.
+__device__ __forceinline__ void warp_hist(uint32_t* h, bool valid, uint32_t bin) {
+  const unsigned act = __ballot_sync(0xffffffffu, valid);
+  if (valid) {
+    const unsigned same = __match_any_sync(act, bin);
+    if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&h[bin], (uint32_t)__popc(same));
+  }
+}
+
+// First pass: keys, bad bits and the histogram of the top 11 key bits.  Rows strided over the
+// grid, one pixel per thread (warp-uniform trip count for the warp-wide votes).
+__global__ void __launch_bounds__(256) k_median_keys(HistParams P) {
   __shared__ uint32_t h[2048];
   for (int i = threadIdx.x; i < 2048; i += blockDim.x) h[i] = 0;
   __syncthreads();
-  const uint32_t prefix = P.st->sel_prefix;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  // rows strided over the grid; warp-uniform trip count so that the warp-wide match below
-  // sees every lane
+  const int wx = x >> 5;
   for (int y = blockIdx.y; y < P.H; y += gridDim.y) {
-    bool valid = false;
-    uint32_t bin = 0;
+    bool valid = false, bad = false;
+    uint32_t k = 0;
     if (x < P.W) {
       const int64_t o = (int64_t)y * P.pitch + x;
-      if (!((P.m1[o] | P.m2[o]) & P.badmask)) {
+      bad = ((P.m1[o] | P.m2[o]) & P.badmask) != 0;
+      if (!bad) {
         const float s = P.i1[o] + P.i2[o];
         if (!isfinite(s)) {
           raise_error(P.st, PSFM_ERR_NONFINITE);
         } else {
-          const uint32_t k = fkey(s);
-          if (P.pass == 0) {
-            bin = k >> 21;
-            valid = true;
-          } else if (P.pass == 1) {
-            bin = (k >> 10) & 2047u;
-            valid = (k >> 21) == prefix;
-          } else {
-            bin = k & 1023u;
-            valid = (k >> 10) == prefix;
-          }
+          k = fkey(s);
+          valid = true;
         }
       }
+      P.keys[(int64_t)y * P.W + x] = k;
     }
-    // sky pixels crowd into a few bins: one shared-memory atomic per distinct bin per warp
-    const unsigned act = __ballot_sync(0xffffffffu, valid);
-    if (valid) {
-      const unsigned same = __match_any_sync(act, bin);
-      if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&h[bin], (uint32_t)__popc(same));
+    const uint32_t word = __ballot_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && wx < P.nwords) P.bits[(int64_t)y * P.nwords + wx] = word;
+    warp_hist(h, valid, k >> 21);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x)
+    if (h[i]) atomicAdd(&P.hist[i], h[i]);
+}
+
+// Passes 1 and 2 over the key image (4 keys per thread per step, grid-stride).
+__global__ void __launch_bounds__(256) k_median_key_hist(const uint32_t* keys, int64_t n,
+                                                         int pass, uint32_t* hist,
+                                                         const DevState* st) {
+  __shared__ uint32_t h[2048];
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const uint32_t prefix = st->sel_prefix;
+  const int64_t n4 = n >> 2;
+  const uint4* k4 = reinterpret_cast<const uint4*>(keys);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // warp-uniform trip count
+  const int64_t steps = (n4 + stride - 1) / stride;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint4 nxt = make_uint4(0u, 0u, 0u, 0u);
+  if (steps > 0 && i < n4) nxt = k4[i];
+  for (int64_t it = 0; it <= steps; ++it, i += stride) {
+    uint32_t kv[4] = {0u, 0u, 0u, 0u};
+    if (it < steps) {
+      kv[0] = nxt.x;
+      kv[1] = nxt.y;
+      kv[2] = nxt.z;
+      kv[3] = nxt.w;
+      // the next step's keys are requested before this step's votes
+      nxt = make_uint4(0u, 0u, 0u, 0u);
+      if (it + 1 < steps && i + stride < n4) nxt = k4[i + stride];
+    } else {
+      // the last n % 4 keys, one per thread of the first block
+      const int64_t j = 4 * n4 + threadIdx.x;
+      if (blockIdx.x == 0 && j < n) kv[0] = keys[j];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t k = kv[q];
+      const bool valid = k != 0u && (pass == 1 ? (k >> 21) == prefix : (k >> 10) == prefix);
+      warp_hist(h, valid, pass == 1 ? (k >> 10) & 2047u : k & 1023u);
     }
   }
   __syncthreads();
-  uint32_t* g = P.hist + P.pass * 2048;
-  for (int i = threadIdx.x; i < 2048; i += blockDim.x)
-    if (h[i]) atomicAdd(&g[i], h[i]);
+  uint32_t* g = hist + pass * 2048;
+  for (int i2 = threadIdx.x; i2 < 2048; i2 += blockDim.x)
+    if (h[i2]) atomicAdd(&g[i2], h[i2]);
 }
 
 // Pick the bin holding the rank-th key and narrow the prefix: a 1024-thread scan over the
@@ -166,6 +213,7 @@ __device__ __forceinline__ bool row_clean(const uint32_t* row, int xa, int xb) {
 struct DetectParams {
   const float* i1;
   const float* i2;
+  const uint32_t* keys;  // [H][W] order-preserving keys of S, 0 where masked
   const float* v1;
   const float* v2;
   const uint32_t* bits;
@@ -174,6 +222,8 @@ struct DetectParams {
   int R;  // s + h
   int nx, ny;
   double thresh;
+  float thresh32;     // thresh rounded to FP32 (the pre-test only; FP64 is slow here)
+  int thresh_nonneg;  // thresh >= 0
   float* bin_val;
   int32_t* bin_idx;
   int32_t* bin_cnt;
@@ -186,13 +236,18 @@ __global__ void k_detect(DetectParams P) {
   if (P.st->error) return;
   if (x < P.R || x >= P.W - P.R || y < P.R || y >= P.H - P.R) return;
   const int64_t o = (int64_t)y * P.pitch + x;
-  const float s = P.i1[o] + P.i2[o];
+  const uint32_t key = P.keys[(int64_t)y * P.W + x];
+  if (key == 0u) return;  // a masked centre fails its own footprint test
+  const float s = fkey_inv(key);  // the same FP32 value as I1 + I2
   const float medf = fkey_inv(P.st->median_key);
+  // with thresh >= 0 the threshold is >= 0 (or NaN, which fails too): at or below the median
+  // never passes, and the variances need not be read
+  if (P.thresh_nonneg && !(s > medf)) return;
   const float v1 = P.v1[o], v2 = P.v2[o];
   // FP32 pre-test with a margin far above FP32 rounding: pixels well below the threshold
   // skip the FP64 test (FP64 runs at 1/64 of the FP32 rate here); the decision itself is
   // always the FP64 one
-  const float t32 = (float)P.thresh * sqrtf(v1 + v2);
+  const float t32 = P.thresh32 * sqrtf(v1 + v2);
   if (isfinite(t32) && isfinite(s) && s - medf < 0.999f * t32) return;
   const double med = (double)medf;
   const double thr = P.thresh * sqrt((double)v1 + (double)v2);
@@ -307,20 +362,6 @@ __global__ void k_init_caller_stamps(int nreg, int W, int H, int32_t* cand, int3
   have[r] = -1;
 }
 
-__global__ void k_bad_bits2(const uint16_t* m1, const uint16_t* m2, int W, int64_t pitch,
-                            int nwords, uint16_t badmask, uint32_t* bits) {
-  const int y = blockIdx.y;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  bool bad = false;
-  if (x < W) {
-    const int64_t o = (int64_t)y * pitch + x;
-    bad = ((m1[o] | m2[o]) & badmask) != 0;
-  }
-  const uint32_t word = __ballot_sync(0xffffffffu, bad);
-  const int wx = x >> 5;
-  if ((threadIdx.x & 31) == 0 && wx < nwords) bits[(int64_t)y * nwords + wx] = word;
-}
-
 }  // namespace
 
 cudaError_t launch_extract(const Plan& p, DevState* st, const SolveBuffers& b, const float* img,
@@ -330,18 +371,34 @@ cudaError_t launch_extract(const Plan& p, DevState* st, const SolveBuffers& b, c
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(b.bin_cnt, 0, sizeof(int32_t) * p.nreg, s);
   if (e != cudaSuccess) return e;
-  HistParams hp{ref, img, mask_ref, mask_img, p.W, p.H, p.pitch, p.cfg.badmask, 0, b.hist, st};
-  for (int pass = 0; pass < 3; ++pass) {
-    hp.pass = pass;
-    k_median_hist<<<dim3((p.W + 255) / 256, p.H < 256 ? p.H : 256), 256, 0, s>>>(hp);
+  const int nwords = (p.W + 31) / 32;
+  HistParams hp;
+  hp.i1 = ref;
+  hp.i2 = img;
+  hp.m1 = mask_ref;
+  hp.m2 = mask_img;
+  hp.W = p.W;
+  hp.H = p.H;
+  hp.nwords = nwords;
+  hp.pitch = p.pitch;
+  hp.badmask = p.cfg.badmask;
+  hp.keys = b.keys;
+  hp.bits = b.badbits;
+  hp.hist = b.hist;
+  hp.st = st;
+  k_median_keys<<<dim3((p.W + 255) / 256, p.H < 256 ? p.H : 256), 256, 0, s>>>(hp);
+  k_median_select<<<1, 1024, 0, s>>>(b.hist, 0, st);
+  const int64_t npx = (int64_t)p.W * p.H;
+  const int64_t blocks = ((npx >> 2) + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < 1 ? 1 : (blocks > 1216 ? 1216 : blocks));
+  for (int pass = 1; pass < 3; ++pass) {
+    k_median_key_hist<<<grid, 256, 0, s>>>(b.keys, npx, pass, b.hist, st);
     k_median_select<<<1, 1024, 0, s>>>(b.hist, pass, st);
   }
-  const int nwords = (p.W + 31) / 32;
-  k_bad_bits2<<<dim3((p.W + 255) / 256, p.H), 256, 0, s>>>(mask_ref, mask_img, p.W, p.pitch,
-                                                          nwords, p.cfg.badmask, b.badbits);
   DetectParams dp;
   dp.i1 = ref;
   dp.i2 = img;
+  dp.keys = b.keys;
   dp.v1 = var_ref;
   dp.v2 = var_img;
   dp.bits = b.badbits;
@@ -353,6 +410,8 @@ cudaError_t launch_extract(const Plan& p, DevState* st, const SolveBuffers& b, c
   dp.nx = p.cfg.grid_nx;
   dp.ny = p.cfg.grid_ny;
   dp.thresh = p.cfg.thresh_nsigma;
+  dp.thresh32 = (float)p.cfg.thresh_nsigma;
+  dp.thresh_nonneg = p.cfg.thresh_nsigma >= 0.0;
   dp.bin_val = b.bin_val;
   dp.bin_idx = b.bin_idx;
   dp.bin_cnt = b.bin_cnt;

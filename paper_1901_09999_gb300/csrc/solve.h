@@ -13,6 +13,7 @@ struct SolveBuffers {
   // extractor (Sec. 3.3)
   uint32_t* hist;     // [3][2048] radix-select histograms of the detection image
   uint32_t* badbits;  // [H][nwords] bad bits of mask_ref | mask_img
+  uint32_t* keys;     // [H][W] order-preserving keys of the detection image, 0 where masked
   float* bin_val;     // [nreg][kBinCap] detections per subregion
   int32_t* bin_idx;   // [nreg][kBinCap] their linear index y * W + x
   int32_t* bin_cnt;   // [nreg]
