@@ -181,6 +181,14 @@ __device__ __forceinline__ df df_norm(df a) {
 
 __device__ __forceinline__ double df_to_d(df a) { return (double)a.hi + (double)a.lo; }
 
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  df t = a;
+  df_acc(t, b.hi, b.lo);
+  return df_norm(t);
+}
+
 // grid (nreg, N_H): the basis-convolved footprint of the terms of one horizontal plane (g, p),
 // that is B_{g,p,q} (x) R for q = 0..d_g - p, in double-float.  The reference pixels are exact
 // FP32; the 1-D factors are split into FP32 pairs.  One block per plane spreads a stamp over
@@ -330,19 +338,28 @@ __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
   }
 }
 
-// grid (nreg, kGramSplit), 512 threads: weighted Gram of the augmented block in double-float.
-// Block (r, j) takes the 64-pixel chunks j, j + kGramSplit, ... of stamp r.  Each thread owns
-// a 4 x 4 block of the Gram and one of `nsl` interleaved pixel slices of every chunk; the
-// weighted columns w * A are formed once per chunk in shared memory.  Chunk partial sums go
-// to per-slice double-float accumulators, then each block writes its FP64 partial Gram; the
-// last block of a stamp to finish (counted with an atomic) adds the partials in split order,
-// so the result does not depend on which block finishes last, and forms the transformed Gram.
+// grid (nreg, kGramSplit), 384 threads, two blocks per SM: weighted Gram of the augmented
+// block in double-float.  Block (r, j) takes the 64-pixel chunks j, j + kGramSplit, ... of
+// stamp r.  Each thread owns a 4 x 4 block of the Gram and one of `nsl` interleaved pixel
+// slices of every chunk (nsl a power of two, the slices of a block in adjacent lanes); its 16
+// double-float sums stay in registers over all chunks, the slices are combined by shuffles,
+// and each block writes its FP64 partial Gram.  The weighted columns w * A are formed once per
+// chunk in shared memory.  The last block of a stamp to finish (counted with an atomic) adds
+// the partials in split order, so the result does not depend on which block finishes last,
+// and forms the transformed Gram.
 constexpr int kGramChunk = 64;
 // row stride of the staged columns: one float of padding puts the rows that the threads of a
 // warp read (different columns, same pixel) in different shared-memory banks
 constexpr int kGramLd = kGramChunk + 1;
-constexpr int kGramThreads = 512;
-__global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
+constexpr int kGramThreads = 384;
+
+__host__ __device__ constexpr int gram_slices(int npair) {
+  int nsl = 1;
+  while (nsl < 16 && 2 * nsl * npair <= kGramThreads) nsl *= 2;
+  return nsl;
+}
+
+__global__ void __launch_bounds__(kGramThreads, 2) k_stamp_gram_df(StampParams P) {
   extern __shared__ double shd[];
   __shared__ int s_last;
   const int r = blockIdx.x, split = blockIdx.y, tid = threadIdx.x;
@@ -353,19 +370,17 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
   // design columns: N_d (the basis applied to R, then to I2 with the dual kernel), then R, 1, I2
   const int Nc = P.Nc, Nb = P.Nd;
   const int nblk = (Nc + 3) / 4, npair = nblk * (nblk + 1) / 2;
-  const int nsl = max(1, kGramThreads / npair);
-  const int ncr = nblk * 4;                                        // padded column count
-  float2* acc = reinterpret_cast<float2*>(shd);                   // [nsl][npair][16] df
-  float* Ah = reinterpret_cast<float*>(acc + (size_t)nsl * npair * 16);  // [ncr][chunk]
+  const int nsl = gram_slices(npair);
+  const int ncr = nblk * 4;  // padded column count
+  float* Ah = reinterpret_cast<float*>(shd);  // [ncr][chunk]
   float* Al = Ah + ncr * kGramLd;
-  float* Bh = Al + ncr * kGramLd;                                  // w * A
+  float* Bh = Al + ncr * kGramLd;  // w * A
   float* Bl = Bh + ncr * kGramLd;
   // weights of every pixel this block takes, all computed up front: [chunk t][64]
   const int nchunk = (P.P + kGramChunk - 1) / kGramChunk;
   const int nch = (nchunk - split + kGramSplit - 1) / kGramSplit;
   float* wh = Bl + ncr * kGramLd;
   float* wl = wh + nch * kGramChunk;
-  for (int i = tid; i < nsl * npair * 16; i += kGramThreads) acc[i] = make_float2(0.f, 0.f);
   for (int i = tid; i < nch * kGramChunk; i += kGramThreads) {
     const int t = i / kGramChunk;
     const int pix = (split + t * kGramSplit) * kGramChunk + (i - t * kGramChunk);
@@ -388,90 +403,80 @@ __global__ void __launch_bounds__(kGramThreads) k_stamp_gram_df(StampParams P) {
     wl[i] = wv.lo;
   }
   const float2* Cr = reinterpret_cast<const float2*>(P.C) + (int64_t)r * Nb * P.P;
-  for (int t = 0; t < nch; ++t) {
-    const int base = (split + t * kGramSplit) * kGramChunk;
-    const float* wht = wh + t * kGramChunk;
-    const float* wlt = wl + t * kGramChunk;
-    __syncthreads();
-    for (int i = tid; i < ncr * kGramChunk; i += kGramThreads) {
-      const int c = i / kGramChunk, j = i - c * kGramChunk, pix = base + j;
-      df v = {0.f, 0.f};
-      if (pix < P.P) {
-        if (c < Nb) {
-          const float2 cv = Cr[(int64_t)c * P.P + pix];
-          v = df{cv.x, cv.y};
-        } else if (c < Nc) {
-          const int py = pix / P.sw, px = pix - py * P.sw;
-          const int gx = cx - P.s + px, gy = cy - P.s + py;
-          if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
-            const int64_t o = (int64_t)gy * P.g.pitch + gx;
-            if (c == Nb) v.hi = (P.m1[o] & P.badmask) ? 0.f : P.i1[o];
-            else if (c == Nb + 1) v.hi = 1.f;
-            else v.hi = P.i2[o];
+  double* Gp = P.Gpart + ((int64_t)r * kGramSplit + split) * Nc * Nc;
+  const int nass = npair * nsl, rounds = (nass + kGramThreads - 1) / kGramThreads;
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int pp = rd * kGramThreads + tid;
+    const bool act = pp < nass;
+    const int pr = act ? pp / nsl : 0, sl = pp - (pp / nsl) * nsl;
+    int bi = 0, rem = pr;
+    while (rem >= nblk - bi) {
+      rem -= nblk - bi;
+      ++bi;
+    }
+    const int bj = bi + rem;
+    df s[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) s[e] = df{0.f, 0.f};
+    for (int t = 0; t < nch; ++t) {
+      const int base = (split + t * kGramSplit) * kGramChunk;
+      const float* wht = wh + t * kGramChunk;
+      const float* wlt = wl + t * kGramChunk;
+      __syncthreads();
+      for (int i = tid; i < ncr * kGramChunk; i += kGramThreads) {
+        const int c = i / kGramChunk, j = i - c * kGramChunk, pix = base + j;
+        df v = {0.f, 0.f};
+        if (pix < P.P) {
+          if (c < Nb) {
+            const float2 cv = Cr[(int64_t)c * P.P + pix];
+            v = df{cv.x, cv.y};
+          } else if (c < Nc) {
+            const int py = pix / P.sw, px = pix - py * P.sw;
+            const int gx = cx - P.s + px, gy = cy - P.s + py;
+            if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
+              const int64_t o = (int64_t)gy * P.g.pitch + gx;
+              if (c == Nb) v.hi = (P.m1[o] & P.badmask) ? 0.f : P.i1[o];
+              else if (c == Nb + 1) v.hi = 1.f;
+              else v.hi = P.i2[o];
+            }
           }
         }
+        const df b = df_mul(df{wht[j], wlt[j]}, v);
+        Ah[c * kGramLd + j] = v.hi;
+        Al[c * kGramLd + j] = v.lo;
+        Bh[c * kGramLd + j] = b.hi;
+        Bl[c * kGramLd + j] = b.lo;
       }
-      const df b = df_mul(df{wht[j], wlt[j]}, v);
-      Ah[c * kGramLd + j] = v.hi;
-      Al[c * kGramLd + j] = v.lo;
-      Bh[c * kGramLd + j] = b.hi;
-      Bl[c * kGramLd + j] = b.lo;
-    }
-    __syncthreads();
-    for (int pp = tid; pp < npair * nsl; pp += kGramThreads) {
-      const int pr = pp % npair, sl = pp / npair;
-      int bi = 0, rem = pr;
-      while (rem >= nblk - bi) {
-        rem -= nblk - bi;
-        ++bi;
-      }
-      const int bj = bi + rem;
-      df s[16];
+      __syncthreads();
+      if (act) {
+        for (int j = sl; j < kGramChunk; j += nsl) {
+          df a[4], b[4];
 #pragma unroll
-      for (int e = 0; e < 16; ++e) s[e] = df{0.f, 0.f};
-      for (int j = sl; j < kGramChunk; j += nsl) {
-        df a[4], b[4];
+          for (int e = 0; e < 4; ++e) {
+            a[e] = df{Ah[(bi * 4 + e) * kGramLd + j], Al[(bi * 4 + e) * kGramLd + j]};
+            b[e] = df{Bh[(bj * 4 + e) * kGramLd + j], Bl[(bj * 4 + e) * kGramLd + j]};
+          }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          a[e] = df{Ah[(bi * 4 + e) * kGramLd + j], Al[(bi * 4 + e) * kGramLd + j]};
-          b[e] = df{Bh[(bj * 4 + e) * kGramLd + j], Bl[(bj * 4 + e) * kGramLd + j]};
+          for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) df_fma(s[e * 4 + f], a[e], b[f]);
         }
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-#pragma unroll
-          for (int f = 0; f < 4; ++f) df_fma(s[e * 4 + f], a[e], b[f]);
-      }
-      // accumulators laid out [slice][entry][pair]: the lanes of a warp (consecutive pairs)
-      // touch consecutive words
-      float2* ac = acc + (size_t)sl * 16 * npair + pr;
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        df u = {ac[e * npair].x, ac[e * npair].y};
-        df_acc(u, s[e].hi, s[e].lo);
-        u = df_norm(u);
-        ac[e * npair] = make_float2(u.hi, u.lo);
       }
     }
-  }
-  __syncthreads();
-  double* Gp = P.Gpart + ((int64_t)r * kGramSplit + split) * Nc * Nc;
-  for (int q = tid; q < npair * 16; q += kGramThreads) {
-    const int pq = q / 16, e = (q / 4) % 4, f = q % 4;
-    double v = 0.0;
-    for (int k = 0; k < nsl; ++k) {
-      const float2 a = acc[((size_t)k * 16 + e * 4 + f) * npair + pq];
-      v += (double)a.x + (double)a.y;
-    }
-    int bi2 = 0, rem2 = pq;
-    while (rem2 >= nblk - bi2) {
-      rem2 -= nblk - bi2;
-      ++bi2;
-    }
-    const int bj2 = bi2 + rem2;
-    const int i = bi2 * 4 + e, j = bj2 * 4 + f;
-    if (i < Nc && j < Nc) {
-      Gp[i * Nc + j] = v;
-      Gp[j * Nc + i] = v;
+    // combine the slices (adjacent lanes), in a fixed order
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      df v = df_norm(s[e]);
+      for (int o = 1; o < nsl; o <<= 1) {
+        const df u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = (sl & o) ? df_add(u, v) : df_add(v, u);
+      }
+      const int i = bi * 4 + e / 4, j = bj * 4 + e % 4;
+      if (act && sl == 0 && i < Nc && j < Nc) {
+        const double g = (double)v.hi + (double)v.lo;
+        Gp[i * Nc + j] = g;
+        Gp[j * Nc + i] = g;
+      }
     }
   }
   // publish the partial, then let the last block of this stamp combine them
@@ -910,13 +915,6 @@ constexpr int kNB = 32;
 // followed by iterative refinement with FP64 residuals of the exact FP64 matrix, which brings
 // the solution to FP64 accuracy (the factor only preconditions the correction).
 
-__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
-
-__device__ __forceinline__ df df_add(df a, df b) {
-  df t = a;
-  df_acc(t, b.hi, b.lo);
-  return df_norm(t);
-}
 
 // Panel pipeline: one launch per 32-column panel.  Launch kb applies panel kb to the whole
 // trailing matrix and, in its block 0, finishes the next diagonal block (its update by panel
@@ -1772,10 +1770,8 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   if (prec == PSFM_PREC_F32X2) {
     sm_design = sizeof(float) * ((size_t)p.foot * p.foot + 2 * (size_t)p.foot * p.sw +
                                  2 * (size_t)(p.dmax + 1) * p.w);
-    const int nsl = kGramThreads / npair > 1 ? kGramThreads / npair : 1;
     const int maxch = ((p.P + kGramChunk - 1) / kGramChunk + kGramSplit - 1) / kGramSplit;
-    sm_gram = sizeof(float2) * nsl * npair * 16 +
-              sizeof(float) * (4 * nblk * 4 * kGramLd + 2 * maxch * kGramChunk);
+    sm_gram = sizeof(float) * (4 * nblk * 4 * kGramLd + 2 * maxch * kGramChunk);
   }
   if (sm_design > 200 * 1024 || sm_gram > 200 * 1024) return PSFM_ERR_UNSUPPORTED;
   // TF32 / BF16X3: FP32 design blocks, the Gram on the tensor cores (k_gram_tc.cu)
