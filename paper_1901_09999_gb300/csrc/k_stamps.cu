@@ -57,33 +57,50 @@ __device__ __forceinline__ void warp_hist(uint32_t* h, bool valid, uint32_t bin)
 }
 
 // First pass: keys, bad bits and the histogram of the top 11 key bits.  Rows strided over the
-// grid, one pixel per thread (warp-uniform trip count for the warp-wide votes).
+// grid, two rows per step with all their loads issued first, one pixel per thread
+// (warp-uniform trip count for the warp-wide votes).
 __global__ void __launch_bounds__(256) k_median_keys(HistParams P) {
   __shared__ uint32_t h[2048];
   for (int i = threadIdx.x; i < 2048; i += blockDim.x) h[i] = 0;
   __syncthreads();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int wx = x >> 5;
-  for (int y = blockIdx.y; y < P.H; y += gridDim.y) {
-    bool valid = false, bad = false;
-    uint32_t k = 0;
-    if (x < P.W) {
-      const int64_t o = (int64_t)y * P.pitch + x;
-      bad = ((P.m1[o] | P.m2[o]) & P.badmask) != 0;
-      if (!bad) {
-        const float s = P.i1[o] + P.i2[o];
-        if (!isfinite(s)) {
-          raise_error(P.st, PSFM_ERR_NONFINITE);
-        } else {
-          k = fkey(s);
-          valid = true;
-        }
+  for (int y = blockIdx.y; y < P.H; y += 2 * gridDim.y) {
+    const int yr[2] = {y, y + (int)gridDim.y};
+    float a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
+    uint16_t m[2] = {0, 0};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (x < P.W && yr[q] < P.H) {
+        const int64_t o = (int64_t)yr[q] * P.pitch + x;
+        m[q] = P.m1[o] | P.m2[o];
+        a[q] = P.i1[o];
+        b[q] = P.i2[o];
       }
-      P.keys[(int64_t)y * P.W + x] = k;
     }
-    const uint32_t word = __ballot_sync(0xffffffffu, bad);
-    if ((threadIdx.x & 31) == 0 && wx < P.nwords) P.bits[(int64_t)y * P.nwords + wx] = word;
-    warp_hist(h, valid, k >> 21);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (yr[q] >= P.H) break;  // uniform over the block
+      bool valid = false, bad = false;
+      uint32_t k = 0;
+      if (x < P.W) {
+        bad = (m[q] & P.badmask) != 0;
+        if (!bad) {
+          const float sv = a[q] + b[q];
+          if (!isfinite(sv)) {
+            raise_error(P.st, PSFM_ERR_NONFINITE);
+          } else {
+            k = fkey(sv);
+            valid = true;
+          }
+        }
+        P.keys[(int64_t)yr[q] * P.W + x] = k;
+      }
+      const uint32_t word = __ballot_sync(0xffffffffu, bad);
+      if ((threadIdx.x & 31) == 0 && wx < P.nwords)
+        P.bits[(int64_t)yr[q] * P.nwords + wx] = word;
+      warp_hist(h, valid, k >> 21);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 2048; i += blockDim.x)
@@ -230,20 +247,16 @@ struct DetectParams {
   DevState* st;
 };
 
-__global__ void k_detect(DetectParams P) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (P.st->error) return;
+// The test of one pixel given its key and variances, loaded by the caller.
+__device__ __forceinline__ void detect_pixel(const DetectParams& P, int x, int y, uint32_t key,
+                                             float v1, float v2, float medf) {
   if (x < P.R || x >= P.W - P.R || y < P.R || y >= P.H - P.R) return;
-  const int64_t o = (int64_t)y * P.pitch + x;
-  const uint32_t key = P.keys[(int64_t)y * P.W + x];
   if (key == 0u) return;  // a masked centre fails its own footprint test
   const float s = fkey_inv(key);  // the same FP32 value as I1 + I2
-  const float medf = fkey_inv(P.st->median_key);
   // with thresh >= 0 the threshold is >= 0 (or NaN, which fails too): at or below the median
-  // never passes, and the variances need not be read
+  // never passes
   if (P.thresh_nonneg && !(s > medf)) return;
-  const float v1 = P.v1[o], v2 = P.v2[o];
+  const int64_t o = (int64_t)y * P.pitch + x;
   // FP32 pre-test with a margin far above FP32 rounding: pixels well below the threshold
   // skip the FP64 test (FP64 runs at 1/64 of the FP32 rate here); the decision itself is
   // always the FP64 one
@@ -279,6 +292,29 @@ __global__ void k_detect(DetectParams P) {
   } else {
     raise_error(P.st, PSFM_ERR_WORKSPACE);
   }
+}
+
+// Block 32 x 8 threads covering 32 x 16 pixels: each thread takes rows y and y + 8, and issues
+// the key and variance loads of both before testing either.
+__global__ void __launch_bounds__(256) k_detect(DetectParams P) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y0 = blockIdx.y * 16 + threadIdx.y;
+  if (P.st->error) return;
+  const float medf = fkey_inv(P.st->median_key);
+  uint32_t key[2] = {0u, 0u};
+  float v1[2] = {0.f, 0.f}, v2[2] = {0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int y = y0 + 8 * q;
+    if (x < P.W && y < P.H) {
+      const int64_t o = (int64_t)y * P.pitch + x;
+      key[q] = P.keys[(int64_t)y * P.W + x];
+      v1[q] = P.v1[o];
+      v2[q] = P.v2[o];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) detect_pixel(P, x, y0 + 8 * q, key[q], v1[q], v2[q], medf);
 }
 
 // One CTA per subregion: keep the max_cand best detections, ordered.
@@ -416,7 +452,7 @@ cudaError_t launch_extract(const Plan& p, DevState* st, const SolveBuffers& b, c
   dp.bin_idx = b.bin_idx;
   dp.bin_cnt = b.bin_cnt;
   dp.st = st;
-  k_detect<<<dim3((p.W + 31) / 32, (p.H + 7) / 8), dim3(32, 8), 0, s>>>(dp);
+  k_detect<<<dim3((p.W + 31) / 32, (p.H + 15) / 16), dim3(32, 8), 0, s>>>(dp);
   k_rank_candidates<<<p.nreg, 256, 0, s>>>(b.bin_val, b.bin_idx, b.bin_cnt, p.W, p.max_cand,
                                           b.cand, b.cand_stat, b.cand_chi2, b.ptr, b.have);
   return cudaGetLastError();
