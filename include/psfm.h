@@ -323,6 +323,35 @@ psfm_status psfm_stack_full(int32_t n, const float* const* imgs, const float* co
                             int32_t cov_out_w, psfm_solution* sols, void* workspace,
                             size_t ws_bytes, psfm_stream stream);
 
+/* PSF model of one stack input for the envelope PSF: a flux-normalised mixture
+ * (1 - moffat_frac) Gaussian + moffat_frac Moffat(beta), both components with the same FWHM
+ * along the major and minor axes (pixels). */
+typedef struct {
+  double fwhm_major, fwhm_minor;
+  double moffat_frac;  /* 0 .. 1 */
+  double beta;         /* Moffat exponent, > 1 when moffat_frac > 0 */
+} psfm_psf_model;
+
+#define PSFM_ENVELOPE_MAX_RADIUS 64
+#define PSFM_ENVELOPE_WORKSPACE 256
+
+/* Envelope PSF of a stack's inputs (Sec. 5.1: each input's PSF realised as a circular profile
+ * with a common peak flux, the maximum taken pixel by pixel, and a PSF model fitted to the
+ * result).  Readings: the circular version of an input has FWHM sqrt(major * minor) and the
+ * same profile mixture; the pixels are the offsets |u|, |v| <= R from the centre; the fitted
+ * model is a circular Gaussian A exp(-r^2 / (2 s^2)), A and s by least squares, with s searched
+ * between 0.2 of the narrowest and 4 times the widest input's Gaussian width.  Writes its FWHM
+ * (2 sqrt(2 ln 2) s), the target_fwhm of psfm_stack and psfm_stack_full, to *fwhm (host).
+ *   n: 1 .. PSFM_STACK_FULL_MAX models (host array);
+ *   radius: R, 1 .. PSFM_ENVELOPE_MAX_RADIUS, or 0 for ceil(3 x the widest circular FWHM);
+ *   workspace: PSFM_ENVELOPE_WORKSPACE bytes of 256-byte-aligned device memory.
+ * Synchronises `stream`.  Errors: BAD_ARG (n, NULL pointers, a FWHM that is not positive and
+ * finite, moffat_frac outside [0, 1], beta <= 1 with moffat_frac > 0, radius out of range or
+ * an automatic radius above the maximum), WORKSPACE, CUDA. */
+psfm_status psfm_envelope_fwhm(int32_t n, const psfm_psf_model* models, int32_t radius,
+                               double* fwhm, void* workspace, size_t ws_bytes,
+                               psfm_stream stream);
+
 /* Batched subtraction (Sec. 3, Sec. 4 applied chip by chip; the batching itself has no
  * counterpart in the paper).  A batch is n chips, each with its own shape, basis (size, degrees,
  * spatial order) and buffers; the configuration is shared.  psfm_batch_create lays out one

@@ -959,6 +959,55 @@ def subtract(I1, I2, V1, V2, m1, m2, sol: Solution, cfg: Config, C1=None, C2=Non
 # Stacking (Sec. 5.1)
 # ----------------------------------------------------------------------------------------
 
+def psf_profile_circular(r2, fwhm, moffat_frac, beta):
+    """Circular PSF profile scaled to peak 1: the flux-normalised mixture (1 - a) Gaussian +
+    a Moffat(beta) with a common FWHM, divided by its central value."""
+    sig = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    g0 = 1.0 / (2.0 * math.pi * sig * sig)
+    g = g0 * np.exp(-0.5 * r2 / (sig * sig))
+    m = np.zeros_like(r2, dtype=np.float64)
+    m0 = 0.0
+    if moffat_frac > 0:
+        al2 = fwhm * fwhm / (4.0 * (2.0 ** (1.0 / beta) - 1.0))
+        m0 = (beta - 1.0) / (math.pi * al2)
+        m = m0 * (1.0 + r2 / al2) ** (-beta)
+    a = moffat_frac
+    return ((1.0 - a) * g + a * m) / ((1.0 - a) * g0 + a * m0)
+
+
+def envelope_fwhm(models, radius=0):
+    """Envelope PSF of stack inputs (Sec. 5.1): each input's PSF realised as a circular profile
+    with a common peak (readings: circular FWHM sqrt(major * minor), the same mixture), the
+    maximum taken pixel by pixel over the offsets |u|, |v| <= R, and a circular Gaussian
+    A exp(-r^2 / 2 s^2) fitted to it by least squares (A, s); returns 2 sqrt(2 ln 2) s.
+    R = radius, or ceil(3 x the widest circular FWHM) when 0.  The fit: A eliminated
+    (A = sum E g / sum g^2), s maximising (sum E g)^2 / sum g^2 over [0.2 s_min, 4 s_max]
+    (the input Gaussian widths) by a dense scan then a bounded scalar minimisation."""
+    from scipy.optimize import minimize_scalar
+    fw = [math.sqrt(m[0] * m[1]) for m in models]
+    R = radius if radius else int(math.ceil(3.0 * max(fw)))
+    u = np.arange(-R, R + 1, dtype=np.float64)
+    U, V = np.meshgrid(u, u)
+    r2 = U * U + V * V
+    E = np.zeros_like(r2)
+    for f, (_, _, a, beta) in zip(fw, models):
+        E = np.maximum(E, psf_profile_circular(r2, f, a, beta))
+    k = 2.0 * math.sqrt(2.0 * math.log(2.0))
+
+    def neg_h(s):
+        g = np.exp(-0.5 * r2 / (s * s))
+        return -float(np.sum(E * g)) ** 2 / float(np.sum(g * g))
+
+    lo, hi = 0.2 * min(fw) / k, 4.0 * max(fw) / k
+    grid = lo * (hi / lo) ** np.linspace(0.0, 1.0, 2001)
+    vals = [neg_h(s) for s in grid]
+    j = int(np.argmin(vals))
+    a, b = grid[max(0, j - 1)], grid[min(len(grid) - 1, j + 1)]
+    res = minimize_scalar(neg_h, bounds=(a, b), method="bounded",
+                          options={"xatol": 1e-12 * b})
+    return k * float(res.x)
+
+
 def render_target(W, H, sources, fwhm, radius=None):
     """Fake target image (Sec. 5.1): circular Gaussian of the given FWHM at each source
     position, sampled at pixel centres, flux-normalised, on a zero background."""

@@ -563,6 +563,33 @@ def psfm_gram(cols, weights, precision, stream=None):
     return G
 
 
+class psfm_psf_model(C.Structure):
+    _fields_ = [("fwhm_major", C.c_double), ("fwhm_minor", C.c_double),
+                ("moffat_frac", C.c_double), ("beta", C.c_double)]
+
+
+ENVELOPE_MAX_RADIUS = 64
+
+
+def psfm_envelope_fwhm(models, radius=0, device=None, stream=None):
+    """FWHM of the envelope PSF of stack inputs (C: psfm_envelope_fwhm).  ``models`` is a list of
+    (fwhm_major, fwhm_minor, moffat_frac, beta) tuples; returns the target FWHM (float)."""
+    torch = _torch()
+    lib = load()
+    lib.psfm_envelope_fwhm.argtypes = [C.c_int32, C.POINTER(psfm_psf_model), C.c_int32,
+                                       C.POINTER(C.c_double), C.c_void_p, C.c_size_t, C.c_void_p]
+    lib.psfm_envelope_fwhm.restype = C.c_int32
+    arr = (psfm_psf_model * max(1, len(models)))(*[psfm_psf_model(*map(float, m)) for m in models])
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    ws = torch.empty(256, dtype=torch.uint8, device=dev)
+    out = C.c_double(0.0)
+    st = lib.psfm_envelope_fwhm(len(models), arr, int(radius), C.byref(out), _ptr(ws), 256,
+                                _stream(stream))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_envelope_fwhm")
+    return out.value
+
+
 # ------------------------------------------------------------------------ instrumentation
 
 def _prof_types(lib):

@@ -388,7 +388,8 @@ def skycell_warps(seed: int = 5, n_warps: int = 16, size: int = 6000, n_stars: i
             m[by:by + bh, bx:bx + bw] |= MASK_BAD
         img[m != 0] = 0.0
         warps.append(dict(image=img.astype(np.float32), var=np.maximum(img, 1.0).astype(np.float32),
-                          mask=m, fwhm=fw, masked_frac=float(np.mean(m != 0))))
+                          mask=m, fwhm=fw, masked_frac=float(np.mean(m != 0)),
+                          psf_model=(fw, fw, frac_moffat, 3.0)))
     return warps, np.stack([xs, ys, fl], 1)
 
 

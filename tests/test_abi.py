@@ -61,3 +61,19 @@ def test_argument_errors_are_caught_on_the_host(lib):
                            C.byref(sol.c), None, 1, None, 0, None, None, None, None, 0, None, 0,
                            None)
     assert st == 9
+
+
+def test_envelope_argument_errors_are_caught_on_the_host(lib):
+    """psfm_envelope_fwhm validates the models and sizes before any CUDA call."""
+    lib.psfm_envelope_fwhm.argtypes = [C.c_int32, C.POINTER(P.psfm_psf_model), C.c_int32,
+                                       C.POINTER(C.c_double), C.c_void_p, C.c_size_t, C.c_void_p]
+    lib.psfm_envelope_fwhm.restype = C.c_int32
+    out = C.c_double(0.0)
+    ok = (P.psfm_psf_model * 1)(P.psfm_psf_model(4.0, 4.0, 0.0, 3.0))
+    assert lib.psfm_envelope_fwhm(0, ok, 0, C.byref(out), None, 0, None) == 1
+    assert lib.psfm_envelope_fwhm(1, ok, 0, C.byref(out), None, 0, None) == 8  # no workspace
+    fake_ws = C.c_void_p(256)  # never dereferenced: the models are rejected first
+    for m, r in (((4.0, 0.0, 0.0, 3.0), 0), ((4.0, 4.0, -0.1, 3.0), 0), ((4.0, 4.0, 0.2, 0.9), 0),
+                 ((4.0, 4.0, 0.0, 3.0), 65), ((40.0, 40.0, 0.0, 3.0), 0)):
+        arr = (P.psfm_psf_model * 1)(P.psfm_psf_model(*m))
+        assert lib.psfm_envelope_fwhm(1, arr, r, C.byref(out), fake_ws, 256, None) == 1

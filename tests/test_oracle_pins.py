@@ -686,3 +686,47 @@ def test_dual_kernel_matches_orthogonal_elongations_better():
     dual = O.solve_kernel(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, ob,
                           O.Config(grid_nx=3, grid_ny=3, badmask=synth.BADMASK, dual=True))
     assert dual.chi2_mean < single.chi2_mean
+
+
+# ---------------------------------------------------------------- envelope PSF (Sec. 5.1)
+
+def test_envelope_of_gaussians_is_the_widest():
+    """Circular Gaussians with a common peak: the pixel-wise maximum is the widest one, which
+    the Gaussian fit reproduces exactly (zero residual)."""
+    for models in ([(4.0, 4.0, 0.0, 3.0), (6.2, 6.2, 0.0, 3.0), (5.0, 5.0, 0.0, 3.0)],
+                   [(3.5, 3.5, 0.0, 2.0)]):
+        top = max(m[0] for m in models)
+        assert abs(O.envelope_fwhm(models) - top) <= 2e-7 * top
+
+
+def test_envelope_circularises_elliptical_inputs():
+    """An elliptical input enters as the circular profile of FWHM sqrt(major * minor)."""
+    assert abs(O.envelope_fwhm([(6.0, 4.0, 0.0, 3.0)]) - math.sqrt(24.0)) <= 1e-7
+
+
+def test_envelope_order_and_duplicates():
+    m1, m2, m3 = (4.0, 4.5, 0.3, 3.0), (6.0, 5.0, 0.8, 2.5), (5.5, 5.5, 1.0, 4.0)
+    ref = O.envelope_fwhm([m1, m2, m3], radius=20)
+    assert abs(O.envelope_fwhm([m3, m1, m2], radius=20) - ref) <= 1e-9 * ref
+    assert abs(O.envelope_fwhm([m2, m3, m1, m2], radius=20) - ref) <= 1e-9 * ref
+
+
+def test_envelope_moffat_limit_is_gaussian():
+    """Moffat(beta) tends to the Gaussian of the same FWHM as beta grows."""
+    assert abs(O.envelope_fwhm([(5.0, 5.0, 1.0, 1e5)]) - 5.0) <= 1e-3
+
+
+def test_envelope_fit_equals_two_parameter_least_squares():
+    """Eliminating the amplitude gives the same fit as a direct two-parameter least squares
+    (scipy) on the realised envelope."""
+    from scipy.optimize import least_squares
+    models = [(4.0, 4.5, 0.3, 3.0), (6.0, 5.0, 0.8, 2.5)]
+    R = 18
+    u = np.arange(-R, R + 1, dtype=np.float64)
+    U, V = np.meshgrid(u, u)
+    r2 = U * U + V * V
+    E = np.max([O.psf_profile_circular(r2, math.sqrt(a * b), f, be) for a, b, f, be in models], 0)
+    fit = least_squares(lambda p: (p[0] * np.exp(-0.5 * r2 / p[1] ** 2) - E).ravel(), [1.0, 2.0],
+                        xtol=1e-14, ftol=1e-14, gtol=1e-14)
+    k = 2.0 * math.sqrt(2.0 * math.log(2.0))
+    assert abs(O.envelope_fwhm(models, radius=R) - k * abs(fit.x[1])) <= 1e-6 * k * fit.x[1]
