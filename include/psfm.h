@@ -289,6 +289,21 @@ psfm_status psfm_bin(const float* img, const float* var, const uint16_t* mask, p
                      double* cov_out, int32_t cov_out_w, void* workspace, size_t ws_bytes,
                      psfm_stream stream);
 
+/* Pseudo-matrix of an image resampled by a non-integer scale (Sec. 4.4: the pseudo-matrix is
+ * resampled by bilinear interpolation, and the total covariance excluding the variance is
+ * kept).  scale s > 0 is the output pixel size in input pixels.  Output lag D (output pixels)
+ * takes the bilinear interpolation of cov_in at the input lag s D (zero beyond cov_in's
+ * extent); the entries off the centre are then multiplied by one factor so that their sum
+ * equals cov_in's sum off the centre (left as interpolated when their sum is 0).  Readings: the
+ * centre (the variance term) is cov_in's; the output radius is floor(r_in / s), the ratio
+ * rounded to 1e-9.  cov_in: device [w_in][w_in] double, w_in odd, at most
+ * PSFM_RESAMPLE_COV_MAX; cov_out: device [w][w], w = psfm_resample_cov_width(w_in, s).
+ * Asynchronous on `stream`; errors: BAD_ARG (sizes, scale not positive and finite, NULL), CUDA. */
+#define PSFM_RESAMPLE_COV_MAX 513
+int32_t psfm_resample_cov_width(int32_t cov_in_w, double scale);
+psfm_status psfm_resample_cov(const double* cov_in, int32_t cov_in_w, double scale,
+                              double* cov_out, int32_t cov_out_w, psfm_stream stream);
+
 /* PSF-homogenised stack with outlier rejection and the unconvolved companion stack (Sec. 5.1:
  * outliers are identified once the inputs share a PSF, carried back to the unconvolved inputs
  * by a matched filter, and the same rejection list serves a stack without convolution).

@@ -959,6 +959,38 @@ def subtract(I1, I2, V1, V2, m1, m2, sol: Solution, cfg: Config, C1=None, C2=Non
 # Stacking (Sec. 5.1)
 # ----------------------------------------------------------------------------------------
 
+def resample_pseudo(C_in, scale):
+    """Pseudo-matrix of an image resampled by a non-integer scale (Sec. 4.4): bilinear
+    interpolation of C_in at the input lags scale * D for output lags D (zero beyond C_in),
+    then the entries off the centre scaled so that their sum is C_in's sum off the centre (the
+    total covariance excluding the variance is kept).  Readings: the centre is C_in's; the
+    output radius is floor(r_in / scale) (ratio rounded to 1e-9)."""
+    C_in = np.asarray(C_in, np.float64)
+    w_in = C_in.shape[0]
+    r_in = (w_in - 1) // 2
+    r = int(math.floor(r_in / scale + 1e-9))
+    w = 2 * r + 1
+    out = np.zeros((w, w))
+
+    def at(x, y):
+        return C_in[y, x] if 0 <= x < w_in and 0 <= y < w_in else 0.0
+
+    for j in range(w):
+        for i in range(w):
+            px, py = scale * (i - r) + r_in, scale * (j - r) + r_in
+            x0, y0 = int(math.floor(px)), int(math.floor(py))
+            fx, fy = px - x0, py - y0
+            out[j, i] = ((1 - fy) * ((1 - fx) * at(x0, y0) + fx * at(x0 + 1, y0)) +
+                         fy * ((1 - fx) * at(x0, y0 + 1) + fx * at(x0 + 1, y0 + 1)))
+    off = np.ones((w, w), bool)
+    off[r, r] = False
+    s_out = float(out[off].sum())
+    s_in = float(C_in.sum() - C_in[r_in, r_in])
+    if s_out != 0.0:
+        out[off] *= s_in / s_out
+    return out
+
+
 def psf_profile_circular(r2, fwhm, moffat_frac, beta):
     """Circular PSF profile scaled to peak 1: the flux-normalised mixture (1 - a) Gaussian +
     a Moffat(beta) with a common FWHM, divided by its central value."""

@@ -8,6 +8,8 @@
 //   P(D) = sum_u (b - |u_x|)(b - |u_y|) C(D + u),   |u_x|, |u_y| < b,
 // (the autocorrelation of the box is the triangle), sampled at lags that are multiples of b
 // and normalised to centre 1.  Partial blocks at the far edges are dropped.
+#include <cmath>
+
 #include "psfm_internal.h"
 
 namespace psfm {
@@ -113,6 +115,87 @@ psfm_status psfm_bin(const float* img, const float* var, const uint16_t* mask, p
   psfm::k_bin_planes<<<dim3((Wb + 127) / 128, Hb), 128, 0, s>>>(
       img, var, mask, shape.pitch, b, badmask, Wb, Hb, (float)f, out, out_var, out_mask,
       out_shape.pitch);
+  return cudaGetLastError() == cudaSuccess ? PSFM_OK : PSFM_ERR_CUDA;
+}
+
+}  // extern "C"
+
+// ---- Resampling of a pseudo-matrix by a non-integer scale (Sec. 4.4) ----
+//
+// Output lag D (in output pixels) samples the input pseudo-matrix at the input lag s D by
+// bilinear interpolation (zero beyond the input's extent); the entries off the centre are then
+// scaled so that their sum equals the input's sum off the centre (the total covariance
+// excluding the variance is preserved; the centre, the variance term, is the interpolated
+// centre, i.e. the input's).  One CTA; sums in FP64 in a fixed order.
+namespace psfm {
+namespace {
+
+constexpr int kResThreads = 256;
+
+__global__ void __launch_bounds__(kResThreads) k_resample_cov(const double* cin, int win,
+                                                              double scale, double* cout,
+                                                              int wout) {
+  __shared__ double red[2][kResThreads / 32];
+  const int tid = threadIdx.x, rin = (win - 1) / 2, rout = (wout - 1) / 2;
+  double s_in = 0.0, s_out = 0.0;
+  for (int i = tid; i < win * win; i += kResThreads)
+    if (i != rin * win + rin) s_in += cin[i];
+  for (int i = tid; i < wout * wout; i += kResThreads) {
+    const int dy = i / wout - rout, dx = i % wout - rout;
+    const double px = scale * dx + rin, py = scale * dy + rin;
+    const double fx0 = floor(px), fy0 = floor(py);
+    const int x0 = (int)fx0, y0 = (int)fy0;
+    const double fx = px - fx0, fy = py - fy0;
+    auto at = [&](int x, int y) {
+      return (x >= 0 && x < win && y >= 0 && y < win) ? cin[y * win + x] : 0.0;
+    };
+    const double v = (1.0 - fy) * ((1.0 - fx) * at(x0, y0) + fx * at(x0 + 1, y0)) +
+                     fy * ((1.0 - fx) * at(x0, y0 + 1) + fx * at(x0 + 1, y0 + 1));
+    cout[i] = v;
+    if (dx != 0 || dy != 0) s_out += v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s_in += __shfl_xor_sync(0xffffffffu, s_in, o);
+    s_out += __shfl_xor_sync(0xffffffffu, s_out, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = s_in;
+    red[1][tid >> 5] = s_out;
+  }
+  __syncthreads();
+  double a = 0.0, b = 0.0;
+  for (int w = 0; w < kResThreads / 32; ++w) {
+    a += red[0][w];
+    b += red[1][w];
+  }
+  const double f = b != 0.0 ? a / b : 1.0;
+  for (int i = tid; i < wout * wout; i += kResThreads)
+    if (i != rout * wout + rout) cout[i] *= f;
+}
+
+}  // namespace
+}  // namespace psfm
+
+extern "C" {
+
+int32_t psfm_resample_cov_width(int32_t cov_in_w, double scale) {
+  if (cov_in_w < 1 || cov_in_w % 2 == 0 || cov_in_w > PSFM_RESAMPLE_COV_MAX) return -1;
+  if (!(scale > 0.0) || !std::isfinite(scale)) return -1;
+  const int rin = (cov_in_w - 1) / 2;
+  const double r = std::floor(rin / scale + 1e-9);
+  return 2 * (int32_t)r + 1;
+}
+
+psfm_status psfm_resample_cov(const double* cov_in, int32_t cov_in_w, double scale,
+                              double* cov_out, int32_t cov_out_w, psfm_stream stream) {
+  using namespace psfm;
+  const int32_t w = psfm_resample_cov_width(cov_in_w, scale);
+  if (w < 0 || !cov_in || !cov_out || cov_out_w != w) return PSFM_ERR_BAD_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  prof_begin("resample_cov", st);
+  k_resample_cov<<<1, kResThreads, 0, st>>>(cov_in, cov_in_w, scale, cov_out, cov_out_w);
+  prof_end("resample_cov", st, 1);
   return cudaGetLastError() == cudaSuccess ? PSFM_OK : PSFM_ERR_CUDA;
 }
 

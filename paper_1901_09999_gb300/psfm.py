@@ -563,6 +563,28 @@ def psfm_gram(cols, weights, precision, stream=None):
     return G
 
 
+def psfm_resample_cov(cov_in, scale, stream=None):
+    """Pseudo-matrix of an image resampled by a non-integer scale (C: psfm_resample_cov).
+    ``cov_in`` is a square float64 CUDA tensor of odd width; returns the resampled one."""
+    torch = _torch()
+    lib = load()
+    lib.psfm_resample_cov_width.argtypes = [C.c_int32, C.c_double]
+    lib.psfm_resample_cov_width.restype = C.c_int32
+    lib.psfm_resample_cov.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_int32,
+                                      C.c_void_p]
+    lib.psfm_resample_cov.restype = C.c_int32
+    cov_in = cov_in.contiguous()
+    w_in = int(cov_in.shape[0])
+    w = lib.psfm_resample_cov_width(w_in, float(scale))
+    if w < 0:
+        raise PsfmError(1, "psfm_resample_cov_width")
+    out = torch.empty((w, w), dtype=torch.float64, device=cov_in.device)
+    st = lib.psfm_resample_cov(_ptr(cov_in), w_in, float(scale), _ptr(out), w, _stream(stream))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_resample_cov")
+    return out
+
+
 class psfm_psf_model(C.Structure):
     _fields_ = [("fwhm_major", C.c_double), ("fwhm_minor", C.c_double),
                 ("moffat_frac", C.c_double), ("beta", C.c_double)]

@@ -730,3 +730,61 @@ def test_envelope_fit_equals_two_parameter_least_squares():
                         xtol=1e-14, ftol=1e-14, gtol=1e-14)
     k = 2.0 * math.sqrt(2.0 * math.log(2.0))
     assert abs(O.envelope_fwhm(models, radius=R) - k * abs(fit.x[1])) <= 1e-6 * k * fit.x[1]
+
+
+# ---------------------------------------------------------------- pseudo-matrix resampling
+
+def _gauss_pseudo(w, sig):
+    r = (w - 1) // 2
+    u = np.arange(-r, r + 1, dtype=np.float64)
+    U, V = np.meshgrid(u, u)
+    return np.exp(-(U * U + V * V) / (4.0 * sig * sig))
+
+
+def test_resample_pseudo_identity_and_white():
+    C = _gauss_pseudo(21, 2.0)
+    assert np.allclose(O.resample_pseudo(C, 1.0), C, rtol=0, atol=1e-15)
+    d = np.zeros((9, 9))
+    d[4, 4] = 1.0
+    for s in (0.6, 1.7, 3.0):
+        out = O.resample_pseudo(d, s)
+        c = (out.shape[0] - 1) // 2
+        assert out[c, c] == 1.0 and np.count_nonzero(out) == 1
+
+
+def test_resample_pseudo_integer_scale_is_subsampling():
+    """An integer scale b samples the input at lags b D exactly (no interpolation); the off-centre
+    entries then carry the input's off-centre total."""
+    C = _gauss_pseudo(31, 3.0)
+    for b in (2, 3, 5):
+        out = O.resample_pseudo(C, float(b))
+        r = (out.shape[0] - 1) // 2
+        sub = C[15 - r * b:15 + r * b + 1:b, 15 - r * b:15 + r * b + 1:b].copy()
+        off = np.ones(sub.shape, bool)
+        off[r, r] = False
+        sub[off] *= (C.sum() - 1.0) / sub[off].sum()
+        assert np.allclose(out, sub, rtol=1e-13, atol=0)
+
+
+def test_resample_pseudo_interpolation_matches_library():
+    """Before the off-centre rescaling, the values are scipy's linear grid interpolation (zero
+    outside); afterwards the centre is the input's and the off-centre total is the input's."""
+    from scipy.interpolate import RegularGridInterpolator
+    rng = np.random.default_rng(3)
+    C = _gauss_pseudo(25, 2.5) * (1 + 0.05 * rng.standard_normal((25, 25)))
+    C = 0.5 * (C + C[::-1, ::-1])
+    C[12, 12] = 1.0
+    for s in (0.65, 1.4, 2.3):
+        out = O.resample_pseudo(C, s)
+        r = (out.shape[0] - 1) // 2
+        g = np.arange(25, dtype=np.float64)
+        f = RegularGridInterpolator((g, g), C, method="linear", bounds_error=False, fill_value=0.0)
+        D = np.arange(-r, r + 1) * s + 12
+        Y, X = np.meshgrid(D, D, indexing="ij")
+        ref = f(np.stack([Y.ravel(), X.ravel()], 1)).reshape(out.shape)
+        off = np.ones(out.shape, bool)
+        off[r, r] = False
+        ref[off] *= (C.sum() - C[12, 12]) / ref[off].sum()
+        assert np.allclose(out, ref, rtol=1e-12, atol=1e-15)
+        assert out[r, r] == C[12, 12]
+        assert abs(out[off].sum() - (C.sum() - C[12, 12])) <= 1e-12 * C.sum()
