@@ -232,7 +232,9 @@ def host_cores():
 def cpu_baseline(reps, path, cores):
     res, wall = run_oracle_parallel(reps, cores, path)
     busy = sum(b for r in res for _, b in r)
+    single, _ = run_oracle_parallel(2, 1, path)
     return {"value": oracle_rate(res), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "single_thread": oracle_rate(single),
             "sample": f"{reps} x {ORACLE_CUT}x{ORACLE_CUT} centre cut-out of the first full chip per "
                       f"process, {cores} concurrent single-threaded processes (S=2, 49 terms, 2x2 "
                       f"stamp grid), solve+convolve+variance+mask+covariance, FP64 numpy; "
