@@ -378,12 +378,13 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_stamp_gram_df(StampParams P
   float* Bl = Bh + ncr * kGramLd;
   // weights of every pixel this block takes, all computed up front: [chunk t][64]
   const int nchunk = (P.P + kGramChunk - 1) / kGramChunk;
-  const int nch = (nchunk - split + kGramSplit - 1) / kGramSplit;
+  const int nsplit = kGramSplit;  // gridDim.y
+  const int nch = (nchunk - split + nsplit - 1) / nsplit;
   float* wh = Bl + ncr * kGramLd;
   float* wl = wh + nch * kGramChunk;
   for (int i = tid; i < nch * kGramChunk; i += kGramThreads) {
     const int t = i / kGramChunk;
-    const int pix = (split + t * kGramSplit) * kGramChunk + (i - t * kGramChunk);
+    const int pix = (split + t * nsplit) * kGramChunk + (i - t * kGramChunk);
     df wv = {0.f, 0.f};
     if (pix < P.P) {
       const int py = pix / P.sw, px = pix - py * P.sw;
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_stamp_gram_df(StampParams P
 #pragma unroll
     for (int e = 0; e < 16; ++e) s[e] = df{0.f, 0.f};
     for (int t = 0; t < nch; ++t) {
-      const int base = (split + t * kGramSplit) * kGramChunk;
+      const int base = (split + t * nsplit) * kGramChunk;
       const float* wht = wh + t * kGramChunk;
       const float* wlt = wl + t * kGramChunk;
       __syncthreads();
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_stamp_gram_df(StampParams P
   // publish the partial, then let the last block of this stamp combine them
   __threadfence();
   __syncthreads();
-  if (tid == 0) s_last = atomicAdd(&P.gram_count[r], 1) == kGramSplit - 1;
+  if (tid == 0) s_last = atomicAdd(&P.gram_count[r], 1) == nsplit - 1;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_stamp_gram_df(StampParams P
   const double* Gp0 = P.Gpart + (int64_t)r * kGramSplit * Nc * Nc;
   for (int q = tid; q < Nc * Nc; q += kGramThreads) {
     double v = 0.0;
-    for (int k = 0; k < kGramSplit; ++k) v += __ldcg(Gp0 + (int64_t)k * Nc * Nc + q);
+    for (int k = 0; k < nsplit; ++k) v += __ldcg(Gp0 + (int64_t)k * Nc * Nc + q);
     Gr[q] = v;
   }
   __syncthreads();
@@ -696,11 +697,8 @@ __global__ void __launch_bounds__(1024) k_norm(SysParams P) {
   for (int r = threadIdx.x; r < P.nreg; r += blockDim.x) {
     int cx, cy;
     double* gr = P.gv + (int64_t)r * P.b.Ns;
-    const int N1 = P.b.Ns + 1;
-    double* gq = P.gp + (int64_t)r * N1 * N1;
     if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) {
       for (int s = 0; s < P.b.Ns; ++s) gr[s] = 0.0;
-      for (int s = 0; s < N1 * N1; ++s) gq[s] = 0.0;
       continue;
     }
     n += 1.0;
@@ -716,15 +714,27 @@ __global__ void __launch_bounds__(1024) k_norm(SysParams P) {
       }
       xp *= xt;
     }
-    for (int a = 0; a < N1; ++a)
-      for (int c = 0; c < N1; ++c)
-        gq[a * N1 + c] = (a < P.b.Ns ? gr[a] : 1.0) * (c < P.b.Ns ? gr[c] : 1.0);
     const double F1 = P.footsum[4 * r], F2 = P.footsum[4 * r + 1], nf = P.footsum[4 * r + 2];
     s11 += F1 * F1;
     s12 += F1 * nf;
     s22 += nf * nf;
     t1 += F1 * F2;
     t2 += nf * F2;
+  }
+  __syncthreads();
+  // pairwise products, one per thread (index Ns stands for 1; zero for an inactive region)
+  {
+    const int N1 = P.b.Ns + 1;
+    for (int q = threadIdx.x; q < P.nreg * N1 * N1; q += blockDim.x) {
+      const int r = q / (N1 * N1), e = q - r * N1 * N1, a = e / N1, c = e - a * N1;
+      int cx, cy;
+      double g = 0.0;
+      if (region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) {
+        const double* gr = P.gv + (int64_t)r * P.b.Ns;
+        g = (a < P.b.Ns ? gr[a] : 1.0) * (c < P.b.Ns ? gr[c] : 1.0);
+      }
+      P.gp[q] = g;
+    }
   }
   n = block_sum(n, sh);
   s11 = block_sum(s11, sh);
