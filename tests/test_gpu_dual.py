@@ -120,3 +120,54 @@ def test_dual_requires_double_float(dev):
         P.psfm_solve_kernel(t["sci"], t["ref"], t["var_sci"], t["var_ref"], t["mask_sci"],
                             t["mask_ref"], b, c)
     assert e.value.code == 9
+
+
+def test_dual_batch_matches_single_calls(dev):
+    """The batch API with the dual kernel gives the same results as psfm_subtract per chip."""
+    import torch
+    fields = [synth.elongated_pair(8, 256, 120), synth.elongated_pair(10, 200, 90)]
+    chips = []
+    for f in fields:
+        t = upload(f, dev)
+        chips.append(dict(img=t["sci"], ref=t["ref"], var_img=t["var_sci"], var_ref=t["var_ref"],
+                          mask_img=t["mask_sci"], mask_ref=t["mask_ref"]))
+    b = P.basis_spec((0.8, 1.6, 3.0), (4, 2, 2), 8, 1)
+    c = P.config(badmask=synth.BADMASK, grid_nx=3, grid_ny=3, precision=P.PREC_F32X2, dual=1)
+    ref = [P.psfm_subtract(ch["img"], ch["ref"], ch["var_img"], ch["var_ref"], ch["mask_img"],
+                           ch["mask_ref"], b, c) for ch in chips]
+    batch = P.Batch(chips, [b, b], c, n_streams=2, want_cov=True)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        batch.run(s)
+        batch.run(s)
+        sols = batch.solutions(s)
+    for i, (D, V, M, cov, sol) in enumerate(ref):
+        assert np.array_equal(host(batch.diff[i]), host(D))
+        assert np.array_equal(host(batch.diff_var[i]), host(V))
+        assert np.array_equal(host(batch.diff_mask[i]), host(M))
+        assert np.allclose(batch.cov[i].cpu().numpy(), cov.cpu().numpy(), rtol=1e-12, atol=1e-15)
+        assert np.array_equal(sols[i].coeff, sol.coeff) and sols[i].b0 == sol.b0
+    batch.close()
+
+
+def test_dual_unsupported_paths(dev):
+    """The workspace-free convolution and the stacks refuse the dual kernel."""
+    f = synth.elongated_pair(8, 128, 40)
+    t = upload(f, dev)
+    b = P.basis_spec((0.8, 1.6), (2, 2), 6, 0)
+    c = P.config(badmask=synth.BADMASK, grid_nx=2, grid_ny=2, precision=P.PREC_F32X2, dual=1)
+    n = P.basis_size(b) * P.spatial_size(b) * 2
+    sol = P.Solution.from_values(1.0, 0.0, np.zeros(n), 1)
+    with pytest.raises(P.PsfmError) as e:
+        P.psfm_convolve_noalloc(t["ref"], t["var_ref"], t["mask_ref"], b, c, sol, img=t["sci"],
+                                var_img=t["var_sci"], mask_img=t["mask_sci"])
+    assert e.value.code == 9
+    import torch
+    src = np.array([[40.0, 40.0, 1000.0], [90.0, 70.0, 2000.0]])
+    img = t["sci"].contiguous()
+    var = t["var_sci"].contiguous()
+    msk = t["mask_sci"].contiguous()
+    with pytest.raises(P.PsfmError) as e:
+        P.psfm_stack([img], [var], [msk], [src], 6.0, [b], c)
+    assert e.value.code == 9
+    assert torch.cuda.is_available()
