@@ -65,7 +65,9 @@ void carve_apply(const Plan& p, Workspace& ws, ApplyBuffers& b) {
   b.kern = ws.take<double>((size_t)ns * p.w * p.w);
   b.kern_t = ws.take<double>((size_t)ns * wt * wt);
   b.kern_s2 = ws.take<double>(ns);
-  b.cov_acc = ws.take<double>((size_t)nconv * nconv);
+  b.kern_f = ws.take<float2>((size_t)ns * p.w * p.w);
+  b.kern_tf = ws.take<float2>((size_t)ns * wt * wt);
+  b.cov_acc = ws.take<double>((size_t)ns * nconv * nconv);
   b.cov_tmp = ws.take<double>((size_t)(2 * p.w - 1) * (2 * p.w - 1));
 }
 

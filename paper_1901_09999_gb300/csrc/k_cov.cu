@@ -6,7 +6,10 @@
 // ((i + 1/2) W / n, (j + 1/2) H / n), divided by its centre value (the covariance factor
 // has already gone into the variance map, patch by patch).  For a difference image it is
 // averaged with the science image's pseudo-matrix, weighted by the two mean variances
-// (Sec. 4.4).  All in FP64: 25 kernels of 31 x 31 cost about 23 M FMAs.
+// (Sec. 4.4).  Kernels and T in FP64, written also as FP32 pairs; the double sum over a and D
+// (25 kernels of 31 x 31: about 50 M products) runs in double-float on the FP32 pipes (FP64
+// runs at 1/64 of their rate here), one partial pseudo-matrix per sample kernel, and the
+// samples are added in a fixed order.
 #include "psfm_internal.h"
 
 namespace psfm {
@@ -16,11 +19,30 @@ __device__ __forceinline__ int sp_idx(int l, int m, int S) {
   return l * (S + 1) - (l * (l - 1)) / 2 + m;
 }
 
+// double-float (FP32 pair) helpers: exact products by FMA, sums by TwoSum
+__device__ __forceinline__ float2 split2(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+// acc += a * b
+__device__ __forceinline__ void fma2(float2& acc, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float s = __fadd_rn(acc.x, p);
+  const float bb = __fsub_rn(s, acc.x);
+  const float err = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  acc.x = s;
+  acc.y = __fadd_rn(acc.y, __fadd_rn(err, e));
+}
+
 // One CTA per sample kernel: realise K_i (FP64), sum K_i^2, and T_i = K_i (x) C_in.
 __global__ void k_cov_kernels(BasisDev b, ImgGeom g, int n, const double* f1d64,
                               const double* psi, const double* sk, const double* dsol,
                               const double* cov_in, int c, double* kern, double* kern_t,
-                              double* kern_s2) {
+                              double* kern_s2, float2* kern_f, float2* kern_tf) {
   extern __shared__ double sh[];
   const int W = b.w, h = b.h;
   double* ak = sh;                 // [Nb]
@@ -69,6 +91,7 @@ __global__ void k_cov_kernels(BasisDev b, ImgGeom g, int n, const double* f1d64,
     if (u == h && v == h) kv += s_dc;
     Kk[j] = kv;
     kern[(size_t)i * W * W + j] = kv;
+    kern_f[(size_t)i * W * W + j] = split2(kv);
     s2 += kv * kv;
   }
 #pragma unroll
@@ -99,37 +122,53 @@ __global__ void k_cov_kernels(BasisDev b, ImgGeom g, int n, const double* f1d64,
       t = Kk[j];
     }
     kern_t[(size_t)i * wt * wt + j] = t;
+    kern_tf[(size_t)i * wt * wt + j] = split2(t);
   }
 }
 
 // grid (n_samples, n_out): one CTA per output row of one sample; thread per output column.
-// C(D) = sum_a K(a) T(D + a), accumulated into acc / (sum K^2 * n_samples).
-__global__ void k_cov_rows(int W, int c, int nsamp, const double* kern, const double* kern_t,
-                           const double* kern_s2, double* acc) {
+// part[i](D) = sum_a K_i(a) T_i(D + a) / (sum K_i^2 * n_samples), in double-float.
+__global__ void k_cov_rows(int W, int c, int nsamp, const float2* kern_f, const float2* kern_tf,
+                           const double* kern_s2, double* part) {
   const int i = blockIdx.x, oy = blockIdx.y;
   const int wt = W + c - 1, nout = 2 * W + c - 2;
   const int ox = threadIdx.x;
   if (ox >= nout) return;
   // out index o <-> D = o - (nout-1)/2; T index t <-> e = t - (wt-1)/2; K index k <-> a = k - h
   // e = D + a  =>  t = o + k - (W - 1)
-  const double* K = kern + (size_t)i * W * W;
-  const double* T = kern_t + (size_t)i * wt * wt;
-  double s = 0.0;
+  const float2* K = kern_f + (size_t)i * W * W;
+  const float2* T = kern_tf + (size_t)i * wt * wt;
+  float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+  const int kx0 = max(0, (W - 1) - ox), kx1 = min(W, wt + (W - 1) - ox);
   for (int ky = 0; ky < W; ++ky) {
     const int ty = oy + ky - (W - 1);
     if (ty < 0 || ty >= wt) continue;
-    for (int kx = 0; kx < W; ++kx) {
-      const int tx = ox + kx - (W - 1);
-      if (tx < 0 || tx >= wt) continue;
-      s += K[ky * W + kx] * T[ty * wt + tx];
+    const float2* Kr = K + ky * W;
+    const float2* Tr = T + ty * wt + ox - (W - 1);
+    int kx = kx0;
+    for (; kx + 3 < kx1; kx += 4) {
+      fma2(s0, Kr[kx], Tr[kx]);
+      fma2(s1, Kr[kx + 1], Tr[kx + 1]);
+      fma2(s2, Kr[kx + 2], Tr[kx + 2]);
+      fma2(s3, Kr[kx + 3], Tr[kx + 3]);
     }
+    for (; kx < kx1; ++kx) fma2(s0, Kr[kx], Tr[kx]);
   }
-  atomicAdd(&acc[oy * nout + ox], s / (kern_s2[i] * nsamp));
+  const double v = (((double)s0.x + (double)s0.y) + ((double)s1.x + (double)s1.y)) +
+                   (((double)s2.x + (double)s2.y) + ((double)s3.x + (double)s3.y));
+  part[((size_t)i * nout + oy) * nout + ox] = v / (kern_s2[i] * nsamp);
 }
 
-__global__ void k_cov_final(int nconv, const double* acc, const double* cov_img, int cimg,
-                            const DevState* st, double* out, int nout) {
-  const double centre = acc[(nconv / 2) * nconv + nconv / 2];
+// The samples' partial pseudo-matrices added in sample order, normalised to the centre, and
+// combined with the science image's.
+__global__ void k_cov_final(int nconv, int nsamp, const double* part, const double* cov_img,
+                            int cimg, const DevState* st, double* out, int nout) {
+  auto acc_at = [&](int q) {
+    double v = 0.0;
+    for (int i = 0; i < nsamp; ++i) v += part[(size_t)i * nconv * nconv + q];
+    return v;
+  };
+  const double centre = acc_at((nconv / 2) * nconv + nconv / 2);
   double w1 = 1.0, w2 = 0.0;
   if (cimg > 0 && st->n_unmasked > 0.0) {
     w1 = st->sum_var_conv / st->n_unmasked;
@@ -140,11 +179,12 @@ __global__ void k_cov_final(int nconv, const double* acc, const double* cov_img,
     w2 = 0.0;
   }
   const int oc = (nout - nconv) / 2, oi = (nout - cimg) / 2;
-  for (int j = threadIdx.x; j < nout * nout; j += blockDim.x) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;  // one output entry per thread
+  if (j < nout * nout) {
     const int y = j / nout, x = j - y * nout;
     double v = 0.0;
     if (y >= oc && y < oc + nconv && x >= oc && x < oc + nconv)
-      v += w1 * acc[(y - oc) * nconv + (x - oc)] / centre;
+      v += w1 * acc_at((y - oc) * nconv + (x - oc)) / centre;
     if (cimg > 0 && y >= oi && y < oi + cimg && x >= oi && x < oi + cimg) {
       const double ci = cov_img ? cov_img[(y - oi) * cimg + (x - oi)] : 1.0;
       v += w2 * ci;
@@ -167,13 +207,13 @@ cudaError_t launch_cov(const Plan& p, const ApplyBuffers& b, const double* cov_i
   if (e != cudaSuccess) return e;
   k_cov_kernels<<<ns, 256, smem, st>>>(basis_dev(p), ImgGeom{p.W, p.H, p.pitch}, n, b.tab.f1d64,
                                        b.tab.psi, b.tab.sk, b.dsol, cov_in, c, b.kern, b.kern_t,
-                                       b.kern_s2);
-  e = cudaMemsetAsync(b.cov_acc, 0, sizeof(double) * nconv * nconv, st);
-  if (e != cudaSuccess) return e;
-  k_cov_rows<<<dim3(ns, nconv), ((nconv + 31) / 32) * 32, 0, st>>>(p.w, c, ns, b.kern, b.kern_t,
-                                                                  b.kern_s2, b.cov_acc);
+                                       b.kern_s2, b.kern_f, b.kern_tf);
+  k_cov_rows<<<dim3(ns, nconv), ((nconv + 31) / 32) * 32, 0, st>>>(p.w, c, ns, b.kern_f,
+                                                                  b.kern_tf, b.kern_s2,
+                                                                  b.cov_acc);
   // cov_img_w: 0 when not subtracting; a white science image is width 1 with no data
-  k_cov_final<<<1, 256, 0, st>>>(nconv, b.cov_acc, cov_img, cov_img_w, b.st, cov_out, cov_out_w);
+  k_cov_final<<<(cov_out_w * cov_out_w + 127) / 128 + 1, 128, 0, st>>>(
+      nconv, ns, b.cov_acc, cov_img, cov_img_w, b.st, cov_out, cov_out_w);
   return cudaGetLastError();
 }
 

@@ -126,7 +126,9 @@ struct ApplyBuffers {
   double* kern;        // [n_cov][w*w] sample kernels
   double* kern_t;      // [n_cov][(w+c-1)^2] K (x) C_in
   double* kern_s2;     // [n_cov] sum K^2
-  double* cov_acc;     // [n_out^2]
+  float2* kern_f;      // the sample kernels as FP32 pairs
+  float2* kern_tf;     // K (x) C_in as FP32 pairs
+  double* cov_acc;     // [n_cov][n_out^2] per-sample partial pseudo-matrices
   double* cov_tmp;     // [(2w-1)^2] pseudo-matrix of the dual kernel's first part
 };
 
