@@ -1657,6 +1657,8 @@ void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b) {
   b.hist = ws.take<uint32_t>(3 * 2048);
   b.badbits = ws.take<uint32_t>((size_t)p.H * nwords);
   b.keys = ws.take<uint32_t>((size_t)p.H * p.W);
+  b.over = ws.take<int32_t>((size_t)over_capacity(p));
+  b.n_over = ws.take<int32_t>(1);
   b.bin_val = ws.take<float>((size_t)p.nreg * kBinCap);
   b.bin_idx = ws.take<int32_t>((size_t)p.nreg * kBinCap);
   b.bin_cnt = ws.take<int32_t>(p.nreg);

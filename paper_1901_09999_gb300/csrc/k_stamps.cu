@@ -244,58 +244,33 @@ struct DetectParams {
   float* bin_val;
   int32_t* bin_idx;
   int32_t* bin_cnt;
+  int32_t* over;      // [cap] linear indices of the pixels above the threshold
+  int32_t* n_over;    // their count
+  int64_t over_cap;
   DevState* st;
 };
 
-// The test of one pixel given its key and variances, loaded by the caller.
-__device__ __forceinline__ void detect_pixel(const DetectParams& P, int x, int y, uint32_t key,
-                                             float v1, float v2, float medf) {
-  if (x < P.R || x >= P.W - P.R || y < P.R || y >= P.H - P.R) return;
-  if (key == 0u) return;  // a masked centre fails its own footprint test
+// Phase 1 of the detection: the threshold test of one pixel given its key and variances,
+// loaded by the caller; true when the pixel goes on to the peak and footprint tests.
+__device__ __forceinline__ bool above_threshold(const DetectParams& P, int x, int y,
+                                                uint32_t key, float v1, float v2, float medf) {
+  if (x < P.R || x >= P.W - P.R || y < P.R || y >= P.H - P.R) return false;
+  if (key == 0u) return false;  // a masked centre fails its own footprint test
   const float s = fkey_inv(key);  // the same FP32 value as I1 + I2
   // with thresh >= 0 the threshold is >= 0 (or NaN, which fails too): at or below the median
   // never passes
-  if (P.thresh_nonneg && !(s > medf)) return;
-  const int64_t o = (int64_t)y * P.pitch + x;
+  if (P.thresh_nonneg && !(s > medf)) return false;
   // FP32 pre-test with a margin far above FP32 rounding: pixels well below the threshold
   // skip the FP64 test (FP64 runs at 1/64 of the FP32 rate here); the decision itself is
   // always the FP64 one
   const float t32 = P.thresh32 * sqrtf(v1 + v2);
-  if (isfinite(t32) && isfinite(s) && s - medf < 0.999f * t32) return;
-  const double med = (double)medf;
+  if (isfinite(t32) && isfinite(s) && s - medf < 0.999f * t32) return false;
   const double thr = P.thresh * sqrt((double)v1 + (double)v2);
-  if (!((double)s - med > thr)) return;
-  const int64_t idx = (int64_t)y * P.W + x;
-  for (int dy = -1; dy <= 1; ++dy)
-    for (int dx = -1; dx <= 1; ++dx) {
-      if (dx == 0 && dy == 0) continue;
-      const int64_t on = o + (int64_t)dy * P.pitch + dx;
-      const float sn = P.i1[on] + P.i2[on];
-      const int64_t nidx = idx + (int64_t)dy * P.W + dx;
-      if (!(s > sn || (s == sn && idx < nidx))) return;
-    }
-  for (int yy = y - P.R; yy <= y + P.R; ++yy)
-    if (!row_clean(P.bits + (int64_t)yy * P.nwords, x - P.R, x + P.R)) return;
-  int rx = (int)(((int64_t)x * P.nx) / P.W);
-  rx = min(P.nx - 1, max(0, rx));
-  while (rx > 0 && x < (int)(((int64_t)rx * P.W) / P.nx)) --rx;
-  while (rx < P.nx - 1 && x >= (int)(((int64_t)(rx + 1) * P.W) / P.nx)) ++rx;
-  int ry = (int)(((int64_t)y * P.ny) / P.H);
-  ry = min(P.ny - 1, max(0, ry));
-  while (ry > 0 && y < (int)(((int64_t)ry * P.H) / P.ny)) --ry;
-  while (ry < P.ny - 1 && y >= (int)(((int64_t)(ry + 1) * P.H) / P.ny)) ++ry;
-  const int r = ry * P.nx + rx;
-  const int slot = atomicAdd(&P.bin_cnt[r], 1);
-  if (slot < kBinCap) {
-    P.bin_val[(int64_t)r * kBinCap + slot] = s;
-    P.bin_idx[(int64_t)r * kBinCap + slot] = (int32_t)idx;
-  } else {
-    raise_error(P.st, PSFM_ERR_WORKSPACE);
-  }
+  return (double)s - (double)medf > thr;
 }
 
-// Block 32 x 8 threads covering 32 x 16 pixels: each thread takes rows y and y + 8, and issues
-// the key and variance loads of both before testing either.
+// Block 32 x 8 threads covering 32 x 16 pixels: each thread tests rows y and y + 8 (all loads
+// issued first); the pixels that pass are appended to the candidate list, one atomic per warp.
 __global__ void __launch_bounds__(256) k_detect(DetectParams P) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y0 = blockIdx.y * 16 + threadIdx.y;
@@ -313,8 +288,68 @@ __global__ void __launch_bounds__(256) k_detect(DetectParams P) {
       v2[q] = P.v2[o];
     }
   }
+  const int lane = threadIdx.x;
 #pragma unroll
-  for (int q = 0; q < 2; ++q) detect_pixel(P, x, y0 + 8 * q, key[q], v1[q], v2[q], medf);
+  for (int q = 0; q < 2; ++q) {
+    const int y = y0 + 8 * q;
+    const bool pass = above_threshold(P, x, y, key[q], v1[q], v2[q], medf);
+    const unsigned bal = __ballot_sync(0xffffffffu, pass);
+    if (!bal) continue;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(P.n_over, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (pass) {
+      const int64_t slot = base + __popc(bal & ((1u << lane) - 1u));
+      if (slot < P.over_cap)
+        P.over[slot] = y * P.W + x;
+      else
+        raise_error(P.st, PSFM_ERR_WORKSPACE);
+    }
+  }
+}
+
+// Phase 2: one warp per candidate.  Lanes 0..7 compare the 8 neighbours (strict peak under
+// (value, -index)), all lanes check rows of the footprint for bad bits, and lane 0 puts a
+// peak with a clean footprint in its subregion's bin.
+__global__ void __launch_bounds__(256) k_detect_peaks(DetectParams P) {
+  if (P.st->error) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int n = min((int64_t)*P.n_over, P.over_cap);
+  for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n; c += nw) {
+    const int idx = P.over[c];
+    const int y = idx / P.W, x = idx - y * P.W;
+    const int64_t o = (int64_t)y * P.pitch + x;
+    const float s = P.i1[o] + P.i2[o];
+    bool ok = true;
+    if (lane < 8) {
+      const int d = lane < 4 ? lane : lane + 1;  // skip the centre of the 3 x 3
+      const int dy = d / 3 - 1, dx = d % 3 - 1;
+      const int64_t on = o + (int64_t)dy * P.pitch + dx;
+      const float sn = P.i1[on] + P.i2[on];
+      const int64_t nidx = (int64_t)idx + (int64_t)dy * P.W + dx;
+      ok = s > sn || (s == sn && idx < nidx);
+    }
+    for (int yy = y - P.R + lane; yy <= y + P.R; yy += 32)
+      ok = ok && row_clean(P.bits + (int64_t)yy * P.nwords, x - P.R, x + P.R);
+    if (!__all_sync(0xffffffffu, ok) || lane != 0) continue;
+    int rx = (int)(((int64_t)x * P.nx) / P.W);
+    rx = min(P.nx - 1, max(0, rx));
+    while (rx > 0 && x < (int)(((int64_t)rx * P.W) / P.nx)) --rx;
+    while (rx < P.nx - 1 && x >= (int)(((int64_t)(rx + 1) * P.W) / P.nx)) ++rx;
+    int ry = (int)(((int64_t)y * P.ny) / P.H);
+    ry = min(P.ny - 1, max(0, ry));
+    while (ry > 0 && y < (int)(((int64_t)ry * P.H) / P.ny)) --ry;
+    while (ry < P.ny - 1 && y >= (int)(((int64_t)(ry + 1) * P.H) / P.ny)) ++ry;
+    const int r = ry * P.nx + rx;
+    const int slot = atomicAdd(&P.bin_cnt[r], 1);
+    if (slot < kBinCap) {
+      P.bin_val[(int64_t)r * kBinCap + slot] = s;
+      P.bin_idx[(int64_t)r * kBinCap + slot] = idx;
+    } else {
+      raise_error(P.st, PSFM_ERR_WORKSPACE);
+    }
+  }
 }
 
 // One CTA per subregion: keep the max_cand best detections, ordered.
@@ -407,6 +442,8 @@ cudaError_t launch_extract(const Plan& p, DevState* st, const SolveBuffers& b, c
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(b.bin_cnt, 0, sizeof(int32_t) * p.nreg, s);
   if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(b.n_over, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
   const int nwords = (p.W + 31) / 32;
   HistParams hp;
   hp.i1 = ref;
@@ -452,7 +489,11 @@ cudaError_t launch_extract(const Plan& p, DevState* st, const SolveBuffers& b, c
   dp.bin_idx = b.bin_idx;
   dp.bin_cnt = b.bin_cnt;
   dp.st = st;
+  dp.over = b.over;
+  dp.n_over = b.n_over;
+  dp.over_cap = over_capacity(p);
   k_detect<<<dim3((p.W + 31) / 32, (p.H + 15) / 16), dim3(32, 8), 0, s>>>(dp);
+  k_detect_peaks<<<1216, 256, 0, s>>>(dp);
   k_rank_candidates<<<p.nreg, 256, 0, s>>>(b.bin_val, b.bin_idx, b.bin_cnt, p.W, p.max_cand,
                                           b.cand, b.cand_stat, b.cand_chi2, b.ptr, b.have);
   return cudaGetLastError();

@@ -14,6 +14,8 @@ struct SolveBuffers {
   uint32_t* hist;     // [3][2048] radix-select histograms of the detection image
   uint32_t* badbits;  // [H][nwords] bad bits of mask_ref | mask_img
   uint32_t* keys;     // [H][W] order-preserving keys of the detection image, 0 where masked
+  int32_t* over;      // [over_capacity] pixels above the detection threshold (linear index)
+  int32_t* n_over;    // their count
   float* bin_val;     // [nreg][kBinCap] detections per subregion
   int32_t* bin_idx;   // [nreg][kBinCap] their linear index y * W + x
   int32_t* bin_cnt;   // [nreg]
@@ -51,6 +53,10 @@ struct SolveBuffers {
 };
 
 void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b);
+
+// Pixels above the detection threshold the extractor can list (a quarter of the image; more
+// is reported as PSFM_ERR_WORKSPACE).
+inline int64_t over_capacity(const Plan& p) { return (int64_t)p.W * p.H / 4 + 1024; }
 
 // Tensor-core weighted Gram of caller column blocks (TF32 mode 0, BF16 hi/lo mode 1):
 // G[b] = cols[b] diag(w[b]) cols[b]^T, cols [n_blocks][n_cols][n_pix], n_cols <= 128; a wait
