@@ -17,6 +17,7 @@
 //            subregion (Sec. 3.3); finish when nothing is rejected or after max_iter solves.
 // The design block stores C without psi and without the delta: the Gram is accumulated on
 // the raw separable convolutions and psi / s_k are applied when the system is assembled.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -687,10 +688,39 @@ __device__ double block_sum(double v, double* sh) {
   return sh[32];
 }
 
+// K block sums at once, in a fixed order for a given launch shape: warp trees, then warp 0
+// adds the warp partials; one pair of barriers for all K (FP64 is slow on this GPU, so few
+// FP64 operations and few barriers).  sh: at least 33 * K doubles.  Every thread gets the sums.
+template <int K>
+__device__ void block_sums(double (&v)[K], double* sh) {
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k * 32 + w] = v[k];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double t = lane < nw ? sh[k * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) sh[32 * K + k] = t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = sh[32 * K + k];
+}
+
 // Active count, spatial factors, and (SEPARATE) b0, d0 from the unweighted regression of
 // footprint sums (Sec. 3.2).  One CTA of 1024 threads.
 __global__ void __launch_bounds__(1024) k_norm(SysParams P) {
-  __shared__ double sh[33];
+  __shared__ double sh[33 * 6];
   if (P.st->error || P.st->done) return;
   double n = 0, s11 = 0, s12 = 0, s22 = 0, t1 = 0, t2 = 0;
   const double xs = P.g.W > 1 ? 2.0 / (P.g.W - 1) : 0.0, ys = P.g.H > 1 ? 2.0 / (P.g.H - 1) : 0.0;
@@ -736,12 +766,14 @@ __global__ void __launch_bounds__(1024) k_norm(SysParams P) {
       P.gp[q] = g;
     }
   }
-  n = block_sum(n, sh);
-  s11 = block_sum(s11, sh);
-  s12 = block_sum(s12, sh);
-  s22 = block_sum(s22, sh);
-  t1 = block_sum(t1, sh);
-  t2 = block_sum(t2, sh);
+  double sums[6] = {n, s11, s12, s22, t1, t2};
+  block_sums<6>(sums, sh);
+  n = sums[0];
+  s11 = sums[1];
+  s12 = sums[2];
+  s22 = sums[3];
+  t1 = sums[4];
+  t2 = sums[5];
   if (threadIdx.x != 0) return;
   P.st->n_active = (int)n;
   P.st->chol_fail = 0;
@@ -1576,7 +1608,7 @@ __global__ void __launch_bounds__(1024) k_reject(int nreg, int max_cand, int max
                                                  double nsig, const int32_t* cand, int32_t* ptr,
                                                  int32_t* cand_stat, const double* chi2,
                                                  int32_t* fresh, int32_t* removed, DevState* st) {
-  __shared__ double sh[33];
+  __shared__ double sh[33 * 2];
   __shared__ int s_finish;
   if (st->error || st->done) return;
   // every thread reads the iteration count before the first barrier; thread 0 advances it
@@ -1591,8 +1623,10 @@ __global__ void __launch_bounds__(1024) k_reject(int nreg, int max_cand, int max
     sum += chi2[r];
     n += 1.0;
   }
-  n = block_sum(n, sh);
-  sum = block_sum(sum, sh);
+  double ns[2] = {n, sum};
+  block_sums<2>(ns, sh);
+  n = ns[0];
+  sum = ns[1];
   const double mu = sum / n;
   double ss = 0.0;
   for (int r = threadIdx.x; r < nreg; r += blockDim.x) {
@@ -1803,6 +1837,9 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   const int64_t nthr = (int64_t)N * N;
   const int N1 = p.Ns + 1;
   const int asm_chunk = (40 * 1024) / (N1 * N1 * (int)sizeof(double));
+  // the rejection kernel works per region: one thread each (FP64 reductions over idle warps
+  // cost as much as useful ones here)
+  const int reject_threads = std::min(1024, std::max(32, (p.nreg + 31) / 32 * 32));
   const size_t sm_asm = (sizeof(double) * N1 * N1 + sizeof(int)) * (size_t)asm_chunk;
   const int npanel = (N + kNB - 1) / kNB;
   const size_t sm_solve = sizeof(float2) * ((size_t)N + 32 * 33 + 32);
@@ -1855,7 +1892,7 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
     prof_end("cholesky", s, npanel + 7);
     prof_begin("chi2_reject", s);
     chi2<<<p.nreg, 256, (sizeof(double) + sizeof(float2)) * p.Nd + 16, s>>>(cq);
-    k_reject<<<1, 1024, 0, s>>>(p.nreg, p.max_cand, p.cfg.max_iter, p.cfg.reject_nsigma, b.cand,
+    k_reject<<<1, reject_threads, 0, s>>>(p.nreg, p.max_cand, p.cfg.max_iter, p.cfg.reject_nsigma, b.cand,
                                 b.ptr, b.cand_stat, b.chi2, b.fresh, b.removed, st);
     k_system_delta<<<(unsigned)((nthr + 255) / 256), 256, sm_asm, s>>>(sy, 1, asm_chunk);
     prof_end("chi2_reject", s, 3);
