@@ -143,16 +143,17 @@ __global__ void k_cov_rows(int W, int c, int nsamp, const float2* kern_f, const 
   for (int ky = 0; ky < W; ++ky) {
     const int ty = oy + ky - (W - 1);
     if (ty < 0 || ty >= wt) continue;
-    const float2* Kr = K + ky * W;
-    const float2* Tr = T + ty * wt + ox - (W - 1);
-    int kx = kx0;
-    for (; kx + 3 < kx1; kx += 4) {
-      fma2(s0, Kr[kx], Tr[kx]);
-      fma2(s1, Kr[kx + 1], Tr[kx + 1]);
-      fma2(s2, Kr[kx + 2], Tr[kx + 2]);
-      fma2(s3, Kr[kx + 3], Tr[kx + 3]);
+    const float2* Kr = K + ky * W + kx0;
+    const float2* Tr = T + ty * wt + (ox + kx0 - (W - 1));  // tx = ox + kx - (W - 1) >= 0
+    const int m = kx1 - kx0;
+    int k = 0;
+    for (; k + 3 < m; k += 4) {
+      fma2(s0, Kr[k], Tr[k]);
+      fma2(s1, Kr[k + 1], Tr[k + 1]);
+      fma2(s2, Kr[k + 2], Tr[k + 2]);
+      fma2(s3, Kr[k + 3], Tr[k + 3]);
     }
-    for (; kx < kx1; ++kx) fma2(s0, Kr[kx], Tr[kx]);
+    for (; k < m; ++k) fma2(s0, Kr[k], Tr[k]);
   }
   const double v = (((double)s0.x + (double)s0.y) + ((double)s1.x + (double)s1.y)) +
                    (((double)s2.x + (double)s2.y) + ((double)s3.x + (double)s3.y));

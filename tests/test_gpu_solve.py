@@ -102,6 +102,19 @@ def test_caller_stamps(dev, prec):
     _check_solution(sol, osol, ob, 256, 256)
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_solve_largest_half_width(dev, prec):
+    """The largest supported kernel half width (h = 24, 49 x 49 kernel) with the extractor."""
+    f = synth.small_gaussian_field(21, size=400, n_stars=120, bad_col_frac=0.002)
+    b, c, ob, oc = specs((1.0, 2.5), (2, 1), 24, 1, badmask=synth.BADMASK, grid_nx=2,
+                         grid_ny=2, precision=prec)
+    t = upload(f, dev)
+    sol = P.psfm_solve_kernel(t["sci"], t["ref"], t["var_sci"], t["var_ref"], t["mask_sci"],
+                              t["mask_ref"], b, c)
+    osol = O.solve_kernel(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, ob, oc)
+    _check_solution(sol, osol, ob, 400, 400)
+
+
 def test_subtract_end_to_end_small(dev):
     f = synth.small_gaussian_field(1)
     b, c, ob, oc = specs((0.7, 1.5, 3.0), (4, 2, 2), 10, 0, badmask=synth.BADMASK)
