@@ -54,9 +54,9 @@ struct SolveBuffers {
 
 void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b);
 
-// Pixels above the detection threshold the extractor can list (a quarter of the image; more
-// is reported as PSFM_ERR_WORKSPACE).
-inline int64_t over_capacity(const Plan& p) { return (int64_t)p.W * p.H / 4 + 1024; }
+// Pixels above the detection threshold the extractor can list: every pixel, so the list never
+// overflows (the guard in the kernel stays).
+inline int64_t over_capacity(const Plan& p) { return (int64_t)p.W * p.H; }
 
 // Tensor-core weighted Gram of caller column blocks (TF32 mode 0, BF16 hi/lo mode 1):
 // G[b] = cols[b] diag(w[b]) cols[b]^T, cols [n_blocks][n_cols][n_pix], n_cols <= 128; a wait
