@@ -115,6 +115,22 @@ def test_solve_largest_half_width(dev, prec):
     _check_solution(sol, osol, ob, 400, 400)
 
 
+def test_half_bright_field(dev):
+    """Half of the field on a much brighter background: most of that half lies above the
+    detection threshold (the median sits between the halves), so the detection lists a large
+    share of the image; stamps and the solution still match the oracle."""
+    f = synth.small_gaussian_field(5, size=256, n_stars=80, bad_col_frac=0.005)
+    for a in (f.ref, f.sci, f.var_ref, f.var_sci):
+        a[:, 128:] += 4000.0
+    b, c, ob, oc = specs((0.7, 1.5, 3.0), (2, 2, 1), 8, 1, badmask=synth.BADMASK, grid_nx=3,
+                         grid_ny=3, precision=P.PREC_F32X2)
+    t = upload(f, dev)
+    sol = P.psfm_solve_kernel(t["sci"], t["ref"], t["var_sci"], t["var_ref"], t["mask_sci"],
+                              t["mask_ref"], b, c)
+    osol = O.solve_kernel(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, ob, oc)
+    _check_solution(sol, osol, ob, 256, 256)
+
+
 def test_subtract_end_to_end_small(dev):
     f = synth.small_gaussian_field(1)
     b, c, ob, oc = specs((0.7, 1.5, 3.0), (4, 2, 2), 10, 0, badmask=synth.BADMASK)
