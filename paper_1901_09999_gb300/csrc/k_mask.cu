@@ -182,14 +182,24 @@ __global__ void k_rbad(BasisDev b, const double* f1d64, const double* psi, const
     Kc[i] = kv;
   }
   __syncthreads();
-  // energy per Chebyshev ring, then outside(r) = sum of the rings beyond r
+  // energy per Chebyshev ring (thread c walks ring c in a fixed order, so the result does not
+  // depend on scheduling), then outside(r) = sum of the rings beyond r
   double* ring = part + h + 2;  // [h+1]
-  for (int r = tid; r <= h; r += blockDim.x) ring[r] = 0.0;
-  __syncthreads();
-  for (int i = tid; i < W * W; i += blockDim.x) {
-    const int v = i / W - h, u = i % W - h;
-    const int c = max(v < 0 ? -v : v, u < 0 ? -u : u);
-    atomicAdd(&ring[c], K2[i]);
+  for (int c = tid; c <= h; c += blockDim.x) {
+    double e = 0.0;
+    if (c == 0) {
+      e = K2[h * W + h];
+    } else {
+      for (int t = -c; t <= c; ++t) {
+        e += K2[(h - c) * W + h + t];  // top row
+        e += K2[(h + c) * W + h + t];  // bottom row
+      }
+      for (int t = -c + 1; t <= c - 1; ++t) {
+        e += K2[(h + t) * W + h - c];  // left column
+        e += K2[(h + t) * W + h + c];  // right column
+      }
+    }
+    ring[c] = e;
   }
   __syncthreads();
   if (tid == 0) {
