@@ -69,6 +69,9 @@ void carve_apply(const Plan& p, Workspace& ws, ApplyBuffers& b) {
   b.kern_tf = ws.take<float2>((size_t)ns * wt * wt);
   b.cov_acc = ws.take<double>((size_t)ns * nconv * nconv);
   b.cov_tmp = ws.take<double>((size_t)(2 * p.w - 1) * (2 * p.w - 1));
+  const size_t npatch =
+      (size_t)((p.W + kVarTile - 1) / kVarTile) * (size_t)((p.H + kVarTile - 1) / kVarTile);
+  b.var_part = ws.take<double>(3 * npatch);
 }
 
 bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
@@ -146,10 +149,10 @@ psfm_status run_apply_dual(const Plan& p, const Head& h, const ApplyBuffers& b,
   if (out_var || stats) {
     prof_begin("variance", st);
     e = launch_variance(p, t, h.dsol, var_ref, mask_ref, nullptr, nullptr, 1, nullptr, out_var,
-                        h.st, st);
+                        h.st, nullptr, st);
     if (e == cudaSuccess)
       e = launch_variance(p, t, h.dsol3, var_img, mask_img, out_var, nullptr, 1,
-                          stats ? mask_dst : nullptr, out_var, h.st, st);
+                          stats ? mask_dst : nullptr, out_var, h.st, b.var_part, st);
     prof_end("variance", st, 2);
     if (e != cudaSuccess) return PSFM_ERR_CUDA;
   }
@@ -200,7 +203,8 @@ psfm_status run_apply(const Plan& p, const Head& h, const ApplyBuffers& b, const
   if (out_var || stats) {
     prof_begin("variance", st);
     e = launch_variance(p, t, h.dsol, var_ref, mask_ref, diff ? var_img : nullptr,
-                        cov_ref, c_ref, stats ? mask_dst : nullptr, out_var, h.st, st);
+                        cov_ref, c_ref, stats ? mask_dst : nullptr, out_var, h.st, b.var_part,
+                        st);
     prof_end("variance", st, 1);
     if (e != cudaSuccess) return PSFM_ERR_CUDA;
   }

@@ -31,6 +31,7 @@ struct VarParams {
   int cov_in_w;
   double xscale, yscale;
   DevState* st;
+  double* part;  // [patches][3] per-patch statistics, added in a fixed order afterwards
   uint16_t badmask, okmask;
   int want_stats;
 };
@@ -220,10 +221,42 @@ __global__ void __launch_bounds__(256) k_variance(VarParams P) {
         b += red[i][1];
         c += red[i][2];
       }
-      atomicAdd(&P.st->sum_var_conv, a);
-      atomicAdd(&P.st->sum_var_img, b);
-      atomicAdd(&P.st->n_unmasked, c);
+      double* pp = P.part + 3 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+      pp[0] = a;
+      pp[1] = b;
+      pp[2] = c;
     }
+  }
+}
+
+// The per-patch statistics added in a fixed order (strided per thread, then a fixed tree).
+__global__ void __launch_bounds__(256) k_var_stats(const double* part, int n, DevState* st) {
+  __shared__ double red[8][3];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    a += part[3 * i];
+    b += part[3 * i + 1];
+    c += part[3 * i + 2];
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = a;
+    red[threadIdx.x >> 5][1] = b;
+    red[threadIdx.x >> 5][2] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      s0 += red[w][0];
+      s1 += red[w][1];
+      s2 += red[w][2];
+    }
+    st->sum_var_conv = s0;
+    st->sum_var_img = s1;
+    st->n_unmasked = s2;
   }
 }
 
@@ -237,6 +270,7 @@ cudaError_t launch_hw(const VarParams& P, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   dim3 grid((P.g.W + kVarTile - 1) / kVarTile, (P.g.H + kVarTile - 1) / kVarTile);
   k_variance<HW><<<grid, 256, smem, st>>>(P);
+  if (P.want_stats) k_var_stats<<<1, 256, 0, st>>>(P.part, (int)(grid.x * grid.y), P.st);
   return cudaGetLastError();
 }
 
@@ -245,7 +279,7 @@ cudaError_t launch_hw(const VarParams& P, cudaStream_t st) {
 cudaError_t launch_variance(const Plan& p, const DevTables& t, const double* dsol,
                             const float* var_ref, const uint16_t* mref, const float* var_img,
                             const double* cov_in, int cov_in_w, const uint16_t* omask,
-                            float* out_var, DevState* ds, cudaStream_t st) {
+                            float* out_var, DevState* ds, double* stats_part, cudaStream_t st) {
   VarParams P;
   P.b = basis_dev(p);
   P.g = ImgGeom{p.W, p.H, p.pitch};
@@ -266,6 +300,8 @@ cudaError_t launch_variance(const Plan& p, const DevTables& t, const double* dso
   P.badmask = p.cfg.badmask;
   P.okmask = (uint16_t)(p.cfg.badmask | p.cfg.conv_bad);
   P.want_stats = omask != nullptr;
+  P.part = stats_part;
+  if (P.want_stats && !stats_part) return cudaErrorInvalidValue;
   switch (p.h) {
 #define PSFM_CASE(n) \
   case n:            \

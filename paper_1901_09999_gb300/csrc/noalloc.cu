@@ -137,7 +137,7 @@ extern "C" psfm_status psfm_convolve_noalloc(
   if (out_var) {
     prof_begin("variance", st);
     e = launch_variance(p, tab, dsol, var_ref, mask_ref, diff ? var_img : nullptr, nullptr, 1,
-                        nullptr, out_var, dst, st);
+                        nullptr, out_var, dst, nullptr, st);
     prof_end("variance", st, 1);
     if (e != cudaSuccess) return PSFM_ERR_CUDA;
   }

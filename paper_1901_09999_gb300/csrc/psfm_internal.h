@@ -130,6 +130,7 @@ struct ApplyBuffers {
   float2* kern_tf;     // K (x) C_in as FP32 pairs
   double* cov_acc;     // [n_cov][n_out^2] per-sample partial pseudo-matrices
   double* cov_tmp;     // [(2w-1)^2] pseudo-matrix of the dual kernel's first part
+  double* var_part;    // [variance patches][3] per-patch statistics for the combination weights
 };
 
 BasisDev basis_dev(const Plan& p);
@@ -187,7 +188,7 @@ cudaError_t launch_conv_image(const Plan& p, const DevTables& t, const double* d
 cudaError_t launch_variance(const Plan& p, const DevTables& t, const double* dsol,
                             const float* var_ref, const uint16_t* mref, const float* var_img,
                             const double* cov_in, int cov_in_w, const uint16_t* omask,
-                            float* out_var, DevState* ds, cudaStream_t st);
+                            float* out_var, DevState* ds, double* stats_part, cudaStream_t st);
 // dual_pass 0: the single kernel; 1: the dual kernel's first pass (proximity flags of the
 // reference's bad pixels only); 2: its second pass (the science image's bad pixels dilated by
 // r_bad2, combined with the first pass's flags into the output mask)
