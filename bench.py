@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -107,7 +108,9 @@ class ClockSampler:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to PSFM_CLOCKS_DIR (default: the system temporary directory)
+        d = os.environ.get("PSFM_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"psfm_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -242,7 +245,6 @@ def cpu_baseline(reps, path, cores):
 
 
 def reference_arm(args):
-    import tempfile
     cores = host_cores()
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "oracle_cut.npz")
@@ -633,7 +635,6 @@ def main():
         return 0
     cpu = None
     if not args.no_cpu_baseline:
-        import tempfile
         try:
             with tempfile.TemporaryDirectory() as d:
                 path = os.path.join(d, "oracle_cut.npz")
