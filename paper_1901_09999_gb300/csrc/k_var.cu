@@ -47,7 +47,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 template <int HW>
-__global__ void __launch_bounds__(256) k_variance(VarParams P) {
+__global__ void __launch_bounds__(256, 5) k_variance(VarParams P) {
   constexpr int T = kVarTile, W = 2 * HW + 1, VR = T + 2 * HW, VS = VR;
   extern __shared__ float4 smem4[];
   float* Vs = reinterpret_cast<float*>(smem4);          // VR * VS
@@ -182,7 +182,10 @@ __global__ void __launch_bounds__(256) k_variance(VarParams P) {
     }
   }
   const float f = s_f;
-  double s_conv = 0.0, s_img = 0.0, s_n = 0.0;
+  // per-thread partials of 16 pixels in FP32 (the FP64 pipe is 1/64 of the FP32 rate), then
+  // warp and block sums in FP64
+  float t_conv = 0.f, t_img = 0.f;
+  int t_n = 0;
   const int gx = x0 + col;
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
@@ -198,16 +201,16 @@ __global__ void __launch_bounds__(256) k_variance(VarParams P) {
       }
       if (P.out) P.out[off] = o;
       if (P.want_stats && !(P.omask[off] & P.okmask)) {
-        s_conv += vp;
-        s_img += v2;
-        s_n += 1.0;
+        t_conv += vp;
+        t_img += v2;
+        ++t_n;
       }
     }
   }
   if (P.want_stats) {
-    s_conv = warp_sum(s_conv);
-    s_img = warp_sum(s_img);
-    s_n = warp_sum(s_n);
+    const double s_conv = warp_sum((double)t_conv);
+    const double s_img = warp_sum((double)t_img);
+    const double s_n = warp_sum((double)t_n);
     if ((tid & 31) == 0) {
       red[tid >> 5][0] = s_conv;
       red[tid >> 5][1] = s_img;
@@ -229,11 +232,16 @@ __global__ void __launch_bounds__(256) k_variance(VarParams P) {
   }
 }
 
-// The per-patch statistics added in a fixed order (strided per thread, then a fixed tree).
-__global__ void __launch_bounds__(256) k_var_stats(const double* part, int n, DevState* st) {
-  __shared__ double red[8][3];
+// The per-patch statistics added in a fixed order (strided per thread, then a fixed tree); one
+// CTA of 1024 threads with four loads in flight per thread keeps this short.
+constexpr int kStatThreads = 1024;
+
+__global__ void __launch_bounds__(kStatThreads) k_var_stats(const double* part, int n,
+                                                             DevState* st) {
+  __shared__ double red[kStatThreads / 32][3];
   double a = 0.0, b = 0.0, c = 0.0;
-  for (int i = threadIdx.x; i < n; i += 256) {
+#pragma unroll 4
+  for (int i = threadIdx.x; i < n; i += kStatThreads) {
     a += part[3 * i];
     b += part[3 * i + 1];
     c += part[3 * i + 2];
@@ -249,7 +257,7 @@ __global__ void __launch_bounds__(256) k_var_stats(const double* part, int n, De
   __syncthreads();
   if (threadIdx.x == 0) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int w = 0; w < 8; ++w) {
+    for (int w = 0; w < kStatThreads / 32; ++w) {
       s0 += red[w][0];
       s1 += red[w][1];
       s2 += red[w][2];
@@ -270,7 +278,8 @@ cudaError_t launch_hw(const VarParams& P, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   dim3 grid((P.g.W + kVarTile - 1) / kVarTile, (P.g.H + kVarTile - 1) / kVarTile);
   k_variance<HW><<<grid, 256, smem, st>>>(P);
-  if (P.want_stats) k_var_stats<<<1, 256, 0, st>>>(P.part, (int)(grid.x * grid.y), P.st);
+  if (P.want_stats)
+    k_var_stats<<<1, kStatThreads, 0, st>>>(P.part, (int)(grid.x * grid.y), P.st);
   return cudaGetLastError();
 }
 
