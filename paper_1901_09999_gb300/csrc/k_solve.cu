@@ -875,9 +875,23 @@ __global__ void __launch_bounds__(256) k_system_delta(SysParams P, int mode, int
     }
     __syncthreads();
     if (mine) {
+      // four independent partial sums keep four Gram loads in flight (fixed order)
       const double* Gr = P.Gt + (int64_t)r0 * Nc * Nc + gij;
-      for (int f = 0; f < nf; ++f)
-        acc = fma(gsh[f * N1 * N1 + pidx], Gr[(int64_t)list[f] * Nc * Nc], acc);
+      const double* gq = gsh + pidx;
+      const int64_t gs = (int64_t)Nc * Nc;
+      const int ps = N1 * N1;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int f = 0;
+      for (; f + 3 < nf; f += 4) {
+        const double g0 = Gr[list[f] * gs], g1 = Gr[list[f + 1] * gs];
+        const double g2 = Gr[list[f + 2] * gs], g3 = Gr[list[f + 3] * gs];
+        a0 = fma(gq[f * ps], g0, a0);
+        a1 = fma(gq[(f + 1) * ps], g1, a1);
+        a2 = fma(gq[(f + 2) * ps], g2, a2);
+        a3 = fma(gq[(f + 3) * ps], g3, a3);
+      }
+      for (; f < nf; ++f) a0 = fma(gq[f * ps], Gr[list[f] * gs], a0);
+      acc += (a0 + a1) + (a2 + a3);
     }
   }
   if (!mine) return;
