@@ -29,6 +29,7 @@ struct ConvParams {
   const double* sk;
   const double* dsol;
   float xscale, yscale;
+  int pgroup;  // horizontal planes held in shared memory at a time
   uint16_t badmask;
 };
 
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(256, 2) k_conv_image(ConvParams P) {
   float* Rs = reinterpret_cast<float*>(smem4);
   float* Hs = Rs + RR * RS;
   const int S = P.b.S, S1 = S + 1;
-  float* Ws = Hs + (P.b.dmax + 1) * RR * TX;
+  float* Ws = Hs + P.pgroup * RR * TX;
   float* alpha = Ws + P.b.NH * P.b.wpad;
   float* beta = alpha + P.b.Nb * S1 * S1;
 
@@ -131,7 +132,9 @@ __global__ void __launch_bounds__(256, 2) k_conv_image(ConvParams P) {
   for (int g = 0; g < P.b.ng; ++g) {
     const int dg = P.b.deg[g];
     const int pb = P.b.plane_base[g];
-    // ---- horizontal passes of every degree of Gaussian g over the staged rows
+    for (int p0 = 0; p0 <= dg; p0 += P.pgroup) {
+    const int p1 = min(dg, p0 + P.pgroup - 1);
+    // ---- horizontal passes of degrees p0..p1 of Gaussian g over the staged rows
     for (int item = tid; item < RR * 8; item += 256) {
       const int row = item >> 3, xg = item & 7;
       float rv[4 * NV4];
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(256, 2) k_conv_image(ConvParams P) {
         rv[4 * j + 2] = t.z;
         rv[4 * j + 3] = t.w;
       }
-      for (int n = 0; n <= dg; ++n) {
+      for (int n = p0; n <= p1; ++n) {
         const float4* wn = reinterpret_cast<const float4*>(Ws + (pb + n) * P.b.wpad);
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
@@ -162,14 +165,15 @@ __global__ void __launch_bounds__(256, 2) k_conv_image(ConvParams P) {
             }
           }
         }
-        *reinterpret_cast<float4*>(Hs + (n * RR + row) * TX + xg * 4) = make_float4(a0, a1, a2, a3);
+        *reinterpret_cast<float4*>(Hs + ((n - p0) * RR + row) * TX + xg * 4) =
+            make_float4(a0, a1, a2, a3);
       }
     }
     __syncthreads();
     // ---- vertical passes: each H value in registers serves 8 outputs and all q
-    for (int p = 0; p <= dg; ++p) {
+    for (int p = p0; p <= p1; ++p) {
       float col[8 + 2 * HW];
-      const float* hp = Hs + (p * RR + wi * 8) * TX + lane;
+      const float* hp = Hs + ((p - p0) * RR + wi * 8) * TX + lane;
 #pragma unroll
       for (int t = 0; t < 8 + 2 * HW; ++t) col[t] = hp[t * TX];
       const int kgp = P.b.kbase[g] + p * (dg + 1) - (p * (p - 1)) / 2;
@@ -195,6 +199,7 @@ __global__ void __launch_bounds__(256, 2) k_conv_image(ConvParams P) {
       }
     }
     __syncthreads();
+    }
   }
 
   float rc[8];
@@ -214,14 +219,24 @@ __global__ void __launch_bounds__(256, 2) k_conv_image(ConvParams P) {
   }
 }
 
+// Shared memory per CTA that leaves room for two resident CTAs per SM (228 KB per SM, 1 KB of
+// it reserved per CTA).
+constexpr size_t kConvSmemTwoCtas = 112 * 1024;
+
 template <int HW>
-cudaError_t launch_hw(const ConvParams& P, cudaStream_t st) {
+cudaError_t launch_hw(ConvParams P, cudaStream_t st) {
   using CS = ConvShape<HW>;
   const int S1 = P.b.S + 1;
-  const size_t smem = sizeof(float) * ((size_t)CS::RR * CS::RS +
-                                       (size_t)(P.b.dmax + 1) * CS::RR * kConvTX +
-                                       (size_t)P.b.NH * P.b.wpad + (size_t)P.b.Nb * S1 * S1 +
-                                       (size_t)S1 * S1);
+  const size_t fixed = sizeof(float) * ((size_t)CS::RR * CS::RS + (size_t)P.b.NH * P.b.wpad +
+                                        (size_t)P.b.Nb * S1 * S1 + (size_t)S1 * S1);
+  const size_t plane = sizeof(float) * (size_t)CS::RR * kConvTX;
+  // as many horizontal planes per group as keep two CTAs per SM (at least one; a Gaussian's
+  // degrees beyond that are processed in further groups)
+  int pg = P.b.dmax + 1;
+  if (fixed + pg * plane > kConvSmemTwoCtas)
+    pg = fixed + plane < kConvSmemTwoCtas ? (int)((kConvSmemTwoCtas - fixed) / plane) : 1;
+  P.pgroup = pg;
+  const size_t smem = fixed + pg * plane;
   cudaError_t e = cudaFuncSetAttribute(k_conv_image<HW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

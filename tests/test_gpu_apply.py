@@ -55,10 +55,13 @@ def test_difference_small_field_given_solution(dev):
 
 @pytest.mark.parametrize("W,H,h,S,deg", [(157, 211, 7, 2, (3, 2, 1)), (64, 65, 3, 1, (2,)),
                                          (300, 97, 12, 3, (4, 2)), (33, 200, 15, 0, (6, 4, 2)),
-                                         (101, 130, 24, 1, (2, 1)), (40, 37, 1, 0, (1,))])
+                                         (101, 130, 24, 1, (2, 1)), (40, 37, 1, 0, (1,)),
+                                         (96, 140, 15, 2, (8, 4)), (70, 90, 24, 1, (6,))])
 def test_ragged_spatially_varying(dev, W, H, h, S, deg):
     """Odd sizes that leave partial tiles in x and y, every spatial order, h from 1 to the
-    largest supported (24)."""
+    largest supported (24).  The last two cases hold more horizontal planes of one Gaussian
+    than the image convolution keeps in shared memory at once (9 planes at h = 15, 7 at
+    h = 24), so their degrees are processed in two groups."""
     f = synth.small_gaussian_field(W + H, size=H, width=W, n_stars=max(5, W * H // 1500),
                                    bad_col_frac=0.02)
     sig = (0.9, 1.8, 3.1)[:len(deg)]
