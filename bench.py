@@ -34,10 +34,9 @@ WORKLOAD = dict(
     workload="full_chip_4846x4868_moffat_S2_49terms_300stamps",
     W=4846, H=4868, basis_sigma=(0.8, 1.6, 3.2), degrees=(6, 4, 2), kernel=31,
     spatial_order=2, stamps=300, grid=(15, 20), seed=2)
-# DRAM bytes (read + write) of one k_conv_image launch on the full-chip workload, from the ncu
-# capture summarised in profiles/k_conv_image_k_variance_full_chip.md; valid for the kernel
-# as captured there.
-CONV_TRAFFIC_FULL_CHIP = 236.08192e6 + 75.049984e6
+# DRAM bytes (read + write) of one k_conv_image launch on the full-chip workload, from an ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as it stands.
+CONV_TRAFFIC_FULL_CHIP = 236.408576e6 + 74.752256e6
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3, "f32x2": 4}
