@@ -47,7 +47,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 template <int HW>
-__global__ void __launch_bounds__(256, 5) k_variance(VarParams P) {
+__global__ void __launch_bounds__(256) k_variance(VarParams P) {
   constexpr int T = kVarTile, W = 2 * HW + 1, VR = T + 2 * HW, VS = VR;
   extern __shared__ float4 smem4[];
   float* Vs = reinterpret_cast<float*>(smem4);          // VR * VS
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256, 5) k_variance(VarParams P) {
         b += red[i][1];
         c += red[i][2];
       }
-      double* pp = P.part + 3 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+      double* pp = P.part + 3 * ((int64_t)(y0 / T) * gridDim.x + x0 / T);
       pp[0] = a;
       pp[1] = b;
       pp[2] = c;
