@@ -7,10 +7,11 @@
 //   beta(x, y)    = b0 - sum_k a_k(x, y) s_k,
 // where a_k(x, y) = sum_s a_{k,s} xt^l yt^m is evaluated per output pixel (Horner in xt, yt).
 //
-// One CTA computes a 32 x 64 output tile.  The masked reference with a halo of h pixels is
-// staged in shared memory once; for each Gaussian the horizontal passes of all its degrees
-// share each register window of the staged rows, and for each (g, p) plane every vertical
-// tap read from shared memory feeds the 8 output rows a thread owns and all degrees q.
+// One CTA computes a 32 (x) by 64 (y) output tile.  The masked reference with a halo of h
+// pixels is staged in shared memory once; for each Gaussian the horizontal passes of a group of
+// its degrees share each register window of the staged rows (the group is as many planes as
+// keep two CTAs per SM: all degrees up to 6 at h = 15), and for each (g, p) plane every
+// vertical tap read from shared memory feeds the 8 output rows a thread owns and all degrees q.
 // Weights live in shared memory and are read as broadcast float4s.
 #include "psfm_internal.h"
 
