@@ -254,10 +254,10 @@ def reference_arm(args):
     val = oracle_rate(res)
     busy = sum(b for r in res for _, b in r)
     print(json.dumps({
-        "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": 0, "steps": args.steps,
+        "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "impl": "reference",
+        "impl": "reference", "device": f"host cores only ({cores}); the GPUs of the launch idle",
         "config": dict(WORKLOAD, sample=f"{ORACLE_CUT}x{ORACLE_CUT} centre cut-out per process "
                                         f"per step, {cores} processes"),
         "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
