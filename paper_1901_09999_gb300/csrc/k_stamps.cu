@@ -138,11 +138,13 @@ __global__ void __launch_bounds__(256) k_median_key_hist(const uint32_t* keys, i
       const int64_t j = 4 * n4 + threadIdx.x;
       if (blockIdx.x == 0 && j < n) kv[0] = keys[j];
     }
+    // keys that share the selected prefix spread over many bins of the next digit, so each
+    // counts with its own shared-memory atomic (no warp-wide grouping)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const uint32_t k = kv[q];
       const bool valid = k != 0u && (pass == 1 ? (k >> 21) == prefix : (k >> 10) == prefix);
-      warp_hist(h, valid, pass == 1 ? (k >> 10) & 2047u : k & 1023u);
+      if (valid) atomicAdd(&h[pass == 1 ? (k >> 10) & 2047u : k & 1023u], 1u);
     }
   }
   __syncthreads();
