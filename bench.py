@@ -45,7 +45,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3, "f32x2": 4}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--chips", type=int, default=4, help="full chips per step (batched)")
