@@ -378,6 +378,54 @@ def solve_spd(M, v):
             raise OracleError("singular normal matrix") from e
 
 
+# Numerical singularity of the normal equations (reading of the paper's "regular matrix
+# methods", Eq. 5-6): a Cholesky pivot d_j within +-PIVOT_SINGULAR of its row's original
+# diagonal M_jj leaves column j a combination of the earlier ones to within the working
+# precision of a solve in ~48-bit arithmetic over a few hundred unknowns, so the system is
+# singular; a pivot below -PIVOT_SINGULAR M_jj is indefiniteness by rounding and goes to LU.
+PIVOT_SINGULAR = 1e-11
+
+
+def _first_bad_pivot(M):
+    """Relative size d_j / M_jj of the first pivot of a plain right-looking Cholesky of M that
+    is not safely positive (within the singular band, negative or not finite); None if every
+    pivot is above the band."""
+    A = np.array(M, dtype=np.float64, copy=True)
+    dg = np.diag(A).copy()
+    n = A.shape[0]
+    for j in range(n):
+        d = A[j, j]
+        if not np.isfinite(d) or d <= PIVOT_SINGULAR * dg[j]:
+            return d / dg[j] if dg[j] != 0 else d
+        l = A[j + 1:, j] / math.sqrt(d)
+        A[j + 1:, j + 1:] -= np.outer(l, l)
+    return None
+
+
+def solve_normal(M, v):
+    """Solve the normal equations M a = v (Eq. 5-6) by Cholesky, falling back to LU with
+    partial pivoting when M is indefinite by rounding; OracleError("singular ...") when a pivot
+    lies within the singular band (PIVOT_SINGULAR) or LU fails."""
+    dg = np.diag(M)
+    try:
+        L = np.linalg.cholesky(M)
+        if np.all(np.diag(L) ** 2 > PIVOT_SINGULAR * dg):
+            z = np.linalg.solve(L, v)
+            return np.linalg.solve(L.T, z)
+    except np.linalg.LinAlgError:
+        pass
+    p = _first_bad_pivot(M)
+    if p is not None and np.isfinite(p) and abs(p) <= PIVOT_SINGULAR:
+        raise OracleError("singular normal matrix")
+    try:
+        a = np.linalg.solve(M, v)
+    except np.linalg.LinAlgError as e:
+        raise OracleError("singular normal matrix") from e
+    if not np.all(np.isfinite(a)):
+        raise OracleError("singular normal matrix")
+    return a
+
+
 def design_rows(st: StampData, n_s: int):
     """Rows of the concatenated design vector (Eq. 4) for the kernel terms of one stamp:
     A[p, k * N_s + s] = g_s(stamp centre) C[p, k]; with the dual kernel the terms applied to
@@ -490,11 +538,11 @@ def solve_from_stamps(stamps, basis: Basis, cfg: Config):
     lam = cfg.penalty if cfg.dual else 0.0
     if cfg.norm_mode == "joint":
         M, v = normal_equations(stamps, basis, "joint", lam=lam)
-        a = solve_spd(M, v)
+        a = solve_normal(M, v)
         return float(a[0]), a[1:-1], float(a[-1])
     b0, d0 = solve_normalisation(stamps)
     M, v = normal_equations(stamps, basis, "separate", b0, d0, lam)
-    a = solve_spd(M, v)
+    a = solve_normal(M, v)
     return b0, a, d0
 
 
@@ -1117,7 +1165,9 @@ def stack_full(warps, sources, target_fwhm, bases, cfg: Config, clip_nsigma=5.0,
       rejected pixels excluded.
 
     Returns dict(conv=(I, V, mask, count), unconv=(I, V, mask, count), rejected=[outlier
-    pixels per input], sols=[...], pm=pseudo-matrix of the convolved stack)."""
+    pixels per input], outliers=[outlier map per input], margins=[|I'_i - m| minus the
+    threshold, NaN where input i is not tested], pass1=[(I'_i, V'_i, usable_i)], sols=[...],
+    pm=pseudo-matrix of the convolved stack)."""
     H, W = warps[0]["image"].shape
     T = render_target(W, H, sources, target_fwhm).astype(np.float32)
     zero = np.zeros((H, W), np.float32)
@@ -1137,12 +1187,15 @@ def stack_full(warps, sources, target_fwhm, bases, cfg: Config, clip_nsigma=5.0,
     with warnings.catch_warnings():
         warnings.simplefilter("ignore", RuntimeWarning)  # pixels with no usable input
         med = np.nanmedian(np.where(nuse >= 3, stackO, np.nan), axis=0)
-    rejected, bad_in = [], []
+    rejected, bad_in, outliers, margins = [], [], [], []
     for (O, Vp, ok), w, sol in zip(conv, wts, sols):
         has = ok & (nuse >= 3)
         m = np.where(has, med, 0.0)
-        out = has & (np.abs(O - m) > clip_nsigma * np.sqrt(Vp + cfg.soften_alpha * np.abs(m)))
+        margin = np.abs(O - m) - clip_nsigma * np.sqrt(Vp + cfg.soften_alpha * np.abs(m))
+        out = has & (margin > 0.0)
         rejected.append(int(out.sum()))
+        outliers.append(out)
+        margins.append(np.where(has, margin, np.nan))
         rb = r_bad(sol, cfg.bad_frac)
         pad = np.zeros((H + 2 * rb, W + 2 * rb), bool)
         pad[rb:rb + H, rb:rb + W] = out
@@ -1181,7 +1234,8 @@ def stack_full(warps, sources, target_fwhm, bases, cfg: Config, clip_nsigma=5.0,
 
     Ps = [pseudo_matrix(sol, cfg) for sol in sols]
     return dict(conv=finish(num, den, var, cnt), unconv=finish(unum, uden, uvar, ucnt),
-                rejected=rejected, sols=sols, pm=combine_pseudo(Ps, wts), weights=wts)
+                rejected=rejected, outliers=outliers, margins=margins, pass1=conv, sols=sols,
+                pm=combine_pseudo(Ps, wts), weights=wts)
 
 
 # ----------------------------------------------------------------------------------------

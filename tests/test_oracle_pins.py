@@ -180,6 +180,39 @@ def _tiny_problem(seed):
     return fld, basis, cfg, pts
 
 
+def test_normal_solve_singular_band():
+    """The normal-equation solve against closed forms: for M = [[1, 1 - e], [1 - e, 1]] the
+    second Cholesky pivot is 1 - (1 - e)^2 ~ 2e.  Above the singular band the solution is the
+    exact inverse applied to v; inside it (and for an exact duplicate) the system is singular;
+    an indefinite matrix beyond the band is solved by LU as the plain inverse."""
+    v = np.array([1.0, 2.0])
+    for e in (1e-3, 1e-8):
+        M = np.array([[1.0, 1.0 - e], [1.0 - e, 1.0]])
+        det = 1.0 - (1.0 - e) ** 2
+        exact = np.array([v[0] - (1 - e) * v[1], v[1] - (1 - e) * v[0]]) / det
+        assert np.allclose(O.solve_normal(M, v), exact, rtol=1e-6)
+    for e in (1e-13, 0.0):
+        M = np.array([[1.0, 1.0 - e], [1.0 - e, 1.0]])
+        with pytest.raises(O.OracleError, match="singular"):
+            O.solve_normal(M, v)
+    M = np.array([[1.0, 2.0], [2.0, 1.0]])   # eigenvalues 3 and -1
+    assert np.allclose(O.solve_normal(M, v), np.array([1.0, 0.0]), atol=1e-15)
+    assert O._first_bad_pivot(np.array([[4.0, 2.0], [2.0, 3.0]])) is None
+
+
+def test_duplicate_gaussian_basis_is_singular():
+    """A basis that lists the same Gaussian twice has duplicate design columns: the normal
+    equations are singular and the solve reports it."""
+    f = synth.small_gaussian_field(1, size=192, n_stars=60)
+    basis = O.Basis((1.5, 1.5), (1, 1), 6, 0)
+    cfg = O.Config(grid_nx=3, grid_ny=3, badmask=synth.BADMASK, max_iter=1)
+    with pytest.raises(O.OracleError, match="singular"):
+        O.solve_kernel(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, basis, cfg)
+    ok = O.Basis((1.5, 2.5), (1, 1), 6, 0)
+    sol = O.solve_kernel(f.ref, f.sci, f.var_ref, f.var_sci, f.mask_ref, f.mask_sci, ok, cfg)
+    assert np.all(np.isfinite(sol.a))
+
+
 def test_joint_solve_equals_svd_least_squares():
     """Gram + Cholesky equals an SVD least-squares solve of the stacked weighted design."""
     fld, basis, cfg, pts = _tiny_problem(11)
@@ -448,21 +481,99 @@ def test_spatially_varying_kernel_maps_the_local_psfs():
 
 # ---------------------------------------------------------------- stacking (Sec. 5.1)
 
-def test_render_target_flux_and_stack_of_equal_inputs():
+def test_render_target_flux():
     T = O.render_target(80, 80, [(40.2, 39.7, 1000.0)], 7.5)
     assert abs(T.sum() - 1000.0) < 1e-6 * 1000
-    sol = _fixed_solution(64, 64)
-    # weighted average of two equal convolved inputs = one convolved input; variance halves
-    rng = np.random.default_rng(2)
-    img = rng.normal(100, 5, (64, 64)).astype(np.float32)
-    V = np.full((64, 64), 25.0, np.float32)
-    m = np.zeros((64, 64), np.uint16)
-    O1 = O.convolve_image(img, m, sol, 0xFF)
-    V1 = O.variance_image(V, m, sol, 0xFF)
-    w = 1.0 / V1.mean()
-    num = 2 * w * O1
-    assert np.allclose(num / (2 * w), O1)
-    assert np.allclose((2 * w * w * V1) / (2 * w) ** 2, V1 / 2)
+
+
+def _coadd_inputs():
+    """Two stack inputs that the matching leaves unchanged (kernel = delta exactly): each
+    warp is the target itself, plus, far from every source and stamp footprint, a smooth
+    pattern below the detection threshold that differs between the warps.  The warps carry
+    constant, different variances and different masked blocks, so the pixels are covered by
+    two inputs, by one, or by none."""
+    W = H = 96
+    src = [(20.3, 14.6, 4e4), (31.7, 29.2, 6e4), (19.4, 47.8, 5e4), (33.1, 63.3, 3e4),
+           (21.8, 80.1, 7e4)]
+    fwhm = 7.5
+    T = O.render_target(W, H, src, fwhm).astype(np.float32)
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    sig2 = (4.0, 9.0)
+    warps = []
+    for i, s2 in enumerate(sig2):
+        pat = np.where(xx >= 72, (1.5 if i == 0 else -1.2) * math.sqrt(s2) *
+                       np.sin(0.21 * xx + 0.13 * (i + 1) * yy) ** 2, 0.0)
+        img = (T.astype(np.float64) + pat).astype(np.float32)
+        m = np.zeros((H, W), np.uint16)
+        if i == 0:
+            m[10:20, 75:85] = synth.MASK_BAD
+            m[40:44, 70:96] = synth.MASK_BAD
+        else:
+            m[15:30, 80:90] = synth.MASK_BAD
+            m[40:44, 70:96] = synth.MASK_BAD
+        warps.append(dict(image=img, var=np.full((H, W), s2, np.float32), mask=m, fwhm=5.0))
+    basis = O.Basis((1.0, 2.0), (2, 1), 5, 0)
+    cfg = O.Config(grid_nx=2, grid_ny=3, badmask=synth.BADMASK)
+    return warps, src, fwhm, basis, cfg, sig2
+
+
+def test_stack_coadd_is_the_minimum_variance_combination():
+    """Sec. 5.1-5.2: the coadd of inputs with constant noise sigma_i^2 that match the target
+    exactly is the minimum-variance combination sum(I_i / sigma_i^2) / sum(1 / sigma_i^2) over
+    the inputs that cover a pixel, with variance 1 / sum(1 / sigma_i^2).  Weights equal to the
+    mean variance (instead of its inverse) or plain averaging fail both."""
+    warps, src, fwhm, basis, cfg, sig2 = _coadd_inputs()
+    img, var, msk, cnt, P, sols = O.stack(warps, src, fwhm, [basis] * 2, cfg)
+    for sol in sols:   # the matching kernel is the delta
+        assert abs(sol.b0 - 1.0) < 1e-9 and np.max(np.abs(sol.a)) < 1e-9
+        assert O.r_bad(sol) == 0
+    use = [(w["mask"].astype(np.int64) & synth.BADMASK) == 0 for w in warps]
+    inv = [np.where(u, 1.0 / s2, 0.0) for u, s2 in zip(use, sig2)]
+    num = sum(iv * w["image"].astype(np.float64) for iv, w in zip(inv, warps))
+    den = sum(inv)
+    n = sum(u.astype(np.int32) for u in use)
+    assert np.array_equal(cnt, n)
+    assert (n == 2).any() and (n == 1).any() and (n == 0).any()
+    assert np.array_equal(msk, np.where(n == 0, 1, 0).astype(np.uint16))
+    cov = n > 0
+    exp_img = num[cov] / den[cov]
+    assert np.max(np.abs(img[cov] - exp_img)) <= 1e-8 * np.max(np.abs(exp_img))
+    assert np.allclose(var[cov], 1.0 / den[cov], rtol=1e-10, atol=0)
+    # the perturbed pixels covered twice are where the weighting shows
+    two = (n == 2) & (np.abs(warps[0]["image"] - warps[1]["image"]) > 0.5)
+    assert two.sum() > 100
+    assert np.all(img[~cov] == 0) and np.all(var[~cov] == 0)
+    assert np.allclose(P, O.embed_centre(np.ones((1, 1)), P.shape[0]), atol=1e-9)
+
+
+def test_combined_pseudo_matrix_of_a_weighted_sum():
+    """Sec. 4.4 add rule for a weighted coadd S = sum w_i X_i of independent noise images,
+    X_i = K_i (x) white noise of variance s_i^2: the covariance of S at lag D is
+    sum w_i^2 s_i^2 (K_i * K_i)(D) (library correlation), so its pseudo-matrix is the
+    average of the inputs' pseudo-matrices with weights w_i^2 mean(V_i), V_i = s_i^2 sum K_i^2
+    being the inputs' variance maps."""
+    u = np.arange(-6, 7, dtype=np.float64)
+    U, V = np.meshgrid(u, u)
+    K1 = np.exp(-(U * U + V * V) / (2 * 1.3 ** 2))
+    K2 = np.exp(-((U - 0.7) ** 2 / (2 * 2.1 ** 2) + V * V / (2 * 1.1 ** 2)))
+    K2 /= K2.sum() / 1.7
+    s2 = (3.0, 11.0)
+    Vm = [s2[0] * np.sum(K1 * K1), s2[1] * np.sum(K2 * K2)]
+    wts = [0.7, 0.2]   # any coadd weights (inverse-variance ones make w_i^2 mean(V_i) = w_i)
+    cov = sum(w * w * s * signal.correlate2d(K, K, mode="full")
+              for w, s, K in zip(wts, s2, (K1, K2)))
+    c = (cov.shape[0] - 1) // 2
+    expected = cov / cov[c, c]
+    Ps = []
+    for K in (K1, K2):
+        P = O.pseudo_conv(K, np.ones((1, 1)))
+        Ps.append(P / P[(P.shape[0] - 1) // 2, (P.shape[0] - 1) // 2])
+    got = O.combine_pseudo(Ps, [w * w * v for w, v in zip(wts, Vm)])
+    assert got.shape == expected.shape
+    assert np.allclose(got, expected, rtol=0, atol=1e-14)
+    # a plain average of the pseudo-matrices, weights w_i or weights mean(V_i) would differ
+    for bad in ([1.0, 1.0], wts, Vm):
+        assert np.max(np.abs(O.combine_pseudo(Ps, bad) - expected)) > 1e-3
 
 
 def test_per_pixel_forms_match_whole_image_forms():
