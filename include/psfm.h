@@ -313,7 +313,8 @@ psfm_status psfm_resample_cov(const double* cov_in, int32_t cov_in_w, double sca
  *   Outliers: at a pixel where at least 3 convolved inputs are usable (no badmask or CONV.BAD
  *   bit), input i is an outlier when |I'_i - m| > clip_nsigma * sqrt(V'_i + soften_alpha |m|),
  *   m the median of the usable convolved values there; n_rejected[i] (host, may be NULL)
- *   counts them.
+ *   counts them; outliers (device [H][pitch] uint32, may be NULL) receives, per pixel, bit i
+ *   set where input i is an outlier.
  *   Rejection: input pixels within the CONV.BAD radius r_bad of input i's kernel (Chebyshev
  *   distance) of one of its outliers get reject_bit (a bit outside badmask, conv_bad and
  *   conv_poor) and count as masked from then on.
@@ -334,9 +335,9 @@ psfm_status psfm_stack_full(int32_t n, const float* const* imgs, const float* co
                             const psfm_config* cfg, double clip_nsigma, uint16_t reject_bit,
                             float* out, float* out_var, uint16_t* out_mask, int32_t* out_count,
                             float* uout, float* uout_var, uint16_t* uout_mask,
-                            int32_t* uout_count, int32_t* n_rejected, double* cov_out,
-                            int32_t cov_out_w, psfm_solution* sols, void* workspace,
-                            size_t ws_bytes, psfm_stream stream);
+                            int32_t* uout_count, int32_t* n_rejected, uint32_t* outliers,
+                            double* cov_out, int32_t cov_out_w, psfm_solution* sols,
+                            void* workspace, size_t ws_bytes, psfm_stream stream);
 
 /* PSF model of one stack input for the envelope PSF: a flux-normalised mixture
  * (1 - moffat_frac) Gaussian + moffat_frac Moffat(beta), both components with the same FWHM
@@ -402,8 +403,8 @@ void psfm_batch_destroy(psfm_batch* b);
 
 /* psfm_convolve without a workspace (no counterpart in the paper: this is an integration
  * aid).  For callers that cannot allocate device memory or hand over a workspace -- for
- * example a plugin running inside another framework's CUDA graph capture, where allocation
- * is forbidden, or a host whose device memory pool is owned by the application.  Computes
+ * example a plugin loaded into a pipeline whose device memory pool is owned by the host
+ * application, or a real-time scheduler that bans allocation after start-up.  Computes
  * the convolved (or difference) image, variance and mask exactly as psfm_convolve does with
  * cov_ref = cov_img = NULL and cov_out = NULL; it allocates nothing and calls no allocating
  * routine.  Its scratch is a fixed 6.1 MiB device array inside the library, present on every
@@ -411,6 +412,8 @@ void psfm_batch_destroy(psfm_batch* b);
  *   Limits: width and height at most 4096 (PSFM_ERR_WORKSPACE otherwise).
  *   The first call on a device looks up the array's device address with that device
  *   current; make that first call before any stream capture.
+ *   Each call uploads its coefficients and tables from host memory (cudaMemcpyAsync on
+ *   `stream`).
  *   All calls share the array: calls that may overlap on the GPU (other streams, unordered
  *   host threads) race and give undefined results.  Calls on one stream are ordered.
  *   Asynchronous on `stream`; errors as for psfm_convolve. */
@@ -434,6 +437,16 @@ psfm_status psfm_convolve_noalloc(const float* ref, const float* var_ref,
  * others return PSFM_ERR_UNSUPPORTED.  The tensor-core modes need PSFM_GRAM_WORKSPACE bytes of
  * 256-byte-aligned device workspace (a status word) and synchronise `stream` to report a
  * device-side PSFM_ERR_TIMEOUT; the FP64 mode is asynchronous. */
+/* Poll limit of the tensor-core Gram's pipeline waits (no counterpart in the paper: a test
+ * hook for the failure path).  Each wait for a shared-memory buffer's earlier MMAs gives up
+ * after `polls` polls: the kernel then records PSFM_ERR_TIMEOUT, waits for the MMAs it has
+ * issued (always with the default limit) and frees its tensor memory, so the context stays
+ * usable and psfm_gram / the TF32 and BF16X3 solves return PSFM_ERR_TIMEOUT.  Applies to the
+ * current device from the next launch; PSFM_WAIT_LIMIT_DEFAULT restores normal operation.
+ * Errors: CUDA. */
+#define PSFM_WAIT_LIMIT_DEFAULT (1u << 24)
+psfm_status psfm_set_pipeline_wait_limit(uint32_t polls);
+
 #define PSFM_GRAM_WORKSPACE 256
 psfm_status psfm_gram(int32_t n_blocks, int32_t n_cols, int32_t n_pix, const float* cols,
                       const float* weights, int32_t precision, double* gram, void* workspace,
@@ -451,6 +464,15 @@ int32_t psfm_profile_count(void);
 int32_t psfm_profile_entry(int32_t i, char* name, int32_t name_cap, double* ms,
                            long long* launches, long long* calls);
 long long psfm_launch_count(void);
+
+/* FP32 FMA throughput probe (no counterpart in the paper: it measures the FP32 peak that the
+ * image and variance kernels are compared with).  Launches n_blocks blocks of 256 threads, each
+ * thread running 8 independent FMA chains for iters x 8 steps, and writes one float per thread
+ * to out (device, n_blocks * 256 floats).  *flops (host, may be NULL) receives the launch's
+ * floating-point operations (2 per FMA); time the launch with CUDA events on `stream`.
+ * Errors: BAD_ARG, CUDA. */
+psfm_status psfm_fma_probe(int32_t n_blocks, int32_t iters, float* out, double* flops,
+                           psfm_stream stream);
 
 #ifdef __cplusplus
 }

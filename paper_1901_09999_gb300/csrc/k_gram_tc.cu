@@ -23,7 +23,12 @@ namespace {
 constexpr int kTcThreads = 128;
 constexpr int kTcM = 128;   // rows of A (TMEM lanes)
 constexpr int kTcKC = 32;   // pixels per staged chunk
-constexpr uint32_t kTcSpinLimit = 1u << 24;
+constexpr uint32_t kTcSpinLimit = PSFM_WAIT_LIMIT_DEFAULT;
+
+// Poll limit of the pipeline waits (a buffer's previous MMAs done before it is refilled).  The
+// final drain wait always uses kTcSpinLimit, so that every MMA issued has completed before the
+// tensor memory is freed, whatever this is set to.
+__device__ uint32_t g_pipe_wait_limit = kTcSpinLimit;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -46,10 +51,12 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// Bounded wait for the phase with the given parity; false if it ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait (at most `limit` polls) for the phase with the given parity; false if it ran
+// out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint32_t limit = kTcSpinLimit) {
   const uint32_t a = smem_u32(bar);
-  for (uint32_t it = 0; it < kTcSpinLimit; ++it) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -259,10 +266,11 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(Src src, int n_tile) {
   const uint32_t sbo = (kTcKC * ESZ / 16) * 128;
   const int kstep = MODE == 0 ? 8 : 16;  // K of one MMA
   const int nchunk = (npix + kTcKC - 1) / kTcKC;
+  const uint32_t pipe_limit = g_pipe_wait_limit;
   for (int ch = 0; ch < nchunk; ++ch) {
     const int s = ch & 1;
     // the MMAs that read this buffer two chunks ago must be done before it is rewritten
-    if (ch >= 2 && !mbar_wait(&bars[s], ((ch - 2) >> 1) & 1) && tid == 0) s_ok = 0;
+    if (ch >= 2 && !mbar_wait(&bars[s], ((ch - 2) >> 1) & 1, pipe_limit) && tid == 0) s_ok = 0;
     __syncthreads();
     if (!s_ok) break;
     const int base = ch * kTcKC;
@@ -445,4 +453,10 @@ extern "C" psfm_status psfm_gram(int32_t n_blocks, int32_t n_cols, int32_t n_pix
       cudaStreamSynchronize(s) != cudaSuccess)
     return PSFM_ERR_CUDA;
   return h;
+}
+
+extern "C" psfm_status psfm_set_pipeline_wait_limit(uint32_t polls) {
+  return cudaMemcpyToSymbol(psfm::g_pipe_wait_limit, &polls, sizeof(polls)) == cudaSuccess
+             ? PSFM_OK
+             : PSFM_ERR_CUDA;
 }

@@ -1018,6 +1018,25 @@ __device__ __forceinline__ df df_rsqrt_pivot(df d) {
   return df{s, __fsub_rn(corr, __fsub_rn(s, r0))};
 }
 
+// Numerical singularity (reading of "regular matrix methods", Eq. 5-6): a pivot whose size
+// relative to its row's original diagonal, |d_j| / (M_jj + penalty_j), is at most
+// kPivotSingular leaves column j a linear combination of the earlier columns to within the
+// working precision of the factorisation (double-float, ~2^-48 per operation, a few 1e-13 over
+// a few hundred columns), so the normal equations are singular (PSFM_ERR_SINGULAR).  A pivot
+// below -kPivotSingular times its diagonal means the matrix is indefinite by rounding: the LU
+// fallback takes it.  Full-rank systems have relative pivots of at least 1 / cond of the
+// unit-diagonal matrix (1e-8 for the full-chip basis).
+constexpr float kPivotSingular = 1e-11f;
+
+// Loads the original diagonal M_jj + penalty_j of rows r0 .. r0 + 31 (1 past n) into dg.
+__device__ __forceinline__ void load_ref_diag(const double* M, const double* pdiag, int n,
+                                              int r0, float* dg) {
+  if (threadIdx.x < kNB) {
+    const int r = r0 + threadIdx.x;
+    dg[threadIdx.x] = r < n ? (float)(M[(int64_t)r * n + r] + pdiag[r]) : 1.f;
+  }
+}
+
 // Cholesky factor and inverse of the 32 x 32 block T (lower triangle; rows and columns past
 // the block's size padded with the identity).  Factor: one barrier per column; thread = (row
 // i, column group g) updating columns g and g + 16; column j is scaled on the fly by the pivot
@@ -1025,9 +1044,12 @@ __device__ __forceinline__ df df_rsqrt_pivot(df d) {
 // sequential chain per column is one update plus one reciprocal square root.  Inverse: from
 // the diagonal 1 / L_ii up by doubling, [A 0; B C]^-1 = [A^-1 0; -C^-1 B A^-1 C^-1], two
 // products per level, five levels.  Lo receives L, Xf inv(L) (zeros above the diagonal), W is
-// scratch.  Returns false (uniformly) when a pivot is not positive and finite.
-__device__ bool tile_factor_inverse(float2 (*T)[kTileLd], float2 (*Lo)[kTileLd],
-                                    float2 (*W)[kTileLd], float2 (*Xf)[kTileLd], float2* rp) {
+// scratch.  dg holds the rows' original diagonals.  Returns (uniformly) 0, or 1 when a pivot is
+// negative beyond the singularity band or not finite (indefinite: LU fallback), or 2 when a
+// pivot lies within the band (singular).
+__device__ int tile_factor_inverse(float2 (*T)[kTileLd], float2 (*Lo)[kTileLd],
+                                   float2 (*W)[kTileLd], float2 (*Xf)[kTileLd], float2* rp,
+                                   const float* dg) {
   const int tid = threadIdx.x, i = tid >> 4, g = tid & 15;
   for (int q = tid; q < kNB * kNB; q += kCholThreads) {
     const int r = q >> 5, c = q & 31;
@@ -1037,8 +1059,10 @@ __device__ bool tile_factor_inverse(float2 (*T)[kTileLd], float2 (*Lo)[kTileLd],
   if (tid == 0) rp[0] = f2(df_rsqrt_pivot(dfv(T[0][0])));
   __syncthreads();
   for (int j = 0; j < kNB; ++j) {
-    const df d = dfv(T[j][j]);
-    if (!(d.hi > 0.f) || !isfinite(d.hi)) return false;  // the same d for every thread
+    const df d = dfv(T[j][j]);  // the same d for every thread
+    if (!isfinite(d.hi)) return 1;
+    if (fabsf(d.hi) <= kPivotSingular * dg[j]) return 2;
+    if (!(d.hi > 0.f)) return 1;
     const df r = dfv(rp[j]);
     if (i >= j) {
       const df lij = i == j ? df_mul(d, r) : df_mul(dfv(T[i][j]), r);
@@ -1082,16 +1106,19 @@ __device__ bool tile_factor_inverse(float2 (*T)[kTileLd], float2 (*Lo)[kTileLd],
     }
     __syncthreads();
   }
-  return true;
+  return 0;
 }
 
 // The first diagonal block.
 __global__ void __launch_bounds__(kCholThreads) k_chol_first(int n, const float* Lh,
                                                              const float* Ll, float* Fh, float* Fl,
-                                                             float2* Linv_all, DevState* st) {
+                                                             float2* Linv_all, const double* M,
+                                                             const double* pdiag, DevState* st) {
   __shared__ float2 S[4][kNB][kTileLd];
   __shared__ float2 rp[kNB];
+  __shared__ float dg[kNB];
   if (st->error || st->done || st->chol_fail) return;
+  load_ref_diag(M, pdiag, n, 0, dg);
   const int m = min(kNB, n);
   for (int q = threadIdx.x; q < kNB * kNB; q += kCholThreads) {
     const int r = q >> 5, c = q & 31;
@@ -1101,8 +1128,12 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_first(int n, const float*
     S[0][r][c] = v;
   }
   __syncthreads();
-  if (!tile_factor_inverse(S[0], S[1], S[2], S[3], rp)) {
-    if (threadIdx.x == 0) st->chol_fail = 1;
+  const int f = tile_factor_inverse(S[0], S[1], S[2], S[3], rp, dg);
+  if (f) {
+    if (threadIdx.x == 0) {
+      if (f == 2) raise_error(st, PSFM_ERR_SINGULAR);
+      else st->chol_fail = 1;
+    }
     return;
   }
   for (int q = threadIdx.x; q < kNB * kNB; q += kCholThreads) {
@@ -1121,9 +1152,11 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_first(int n, const float*
 // tiles also store their 16 panel rows into F.
 __global__ void __launch_bounds__(kCholThreads) k_chol_panel(int n, int kb, float* Lh, float* Ll,
                                                              float* Fh, float* Fl,
-                                                             float2* Linv_all, DevState* st) {
+                                                             float2* Linv_all, const double* M,
+                                                             const double* pdiag, DevState* st) {
   __shared__ float2 S[5][kNB][kTileLd];
   __shared__ float2 rp[kNB];
+  __shared__ float dg[kNB];
   if (st->error || st->done || st->chol_fail) return;
   const int tid = threadIdx.x;
   const int k0 = kb * kNB, base = k0 + kNB;
@@ -1132,6 +1165,7 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_panel(int n, int kb, floa
   for (int q = tid; q < kNB * kNB; q += kCholThreads) Li[q >> 5][q & 31] = Linv[q];
   if (blockIdx.x == 0) {
     const int mb = min(kNB, n - base);
+    load_ref_diag(M, pdiag, n, base, dg);
     float2(*Ar)[kTileLd] = S[4];
     float2(*Pn)[kTileLd] = S[1];
     float2(*T)[kTileLd] = S[2];
@@ -1177,8 +1211,12 @@ __global__ void __launch_bounds__(kCholThreads) k_chol_panel(int n, int kb, floa
     }
     __syncthreads();
     // Li and Ar are free from here: Xf and W reuse them
-    if (!tile_factor_inverse(T, S[3], S[4], S[0], rp)) {
-      if (tid == 0) st->chol_fail = 1;
+    const int f = tile_factor_inverse(T, S[3], S[4], S[0], rp, dg);
+    if (f) {
+      if (tid == 0) {
+        if (f == 2) raise_error(st, PSFM_ERR_SINGULAR);
+        else st->chol_fail = 1;
+      }
       return;
     }
     float2* Lnext = Linv_all + (int64_t)(kb + 1) * kNB * kNB;
@@ -1888,11 +1926,12 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
     k_rhs<<<(N * 32 + 255) / 256, 256, 0, s>>>(sy);
     prof_end("system", s, p.cfg.dual ? 4 : 3);
     prof_begin("cholesky", s);
-    k_chol_first<<<1, kCholThreads, 0, s>>>(N, b.Lh, b.Ll, b.Fh, b.Fl, b.rinv, st);
+    k_chol_first<<<1, kCholThreads, 0, s>>>(N, b.Lh, b.Ll, b.Fh, b.Fl, b.rinv, b.M, b.pdiag,
+                                            st);
     for (int kb = 0; kb + 1 < npanel; ++kb) {
       const int nt = (N - (kb + 1) * kNB + 15) / 16;
       k_chol_panel<<<1 + nt * (nt + 1) / 2, kCholThreads, 0, s>>>(N, kb, b.Lh, b.Ll, b.Fh, b.Fl,
-                                                                   b.rinv, st);
+                                                                   b.rinv, b.M, b.pdiag, st);
     }
     k_chol_solve<<<1, kSolveThreads, sm_solve, s>>>(N, b.Fh, b.Fl, b.rinv, b.v, nullptr, b.x,
                                                     st, 0);

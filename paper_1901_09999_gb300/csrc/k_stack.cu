@@ -2,7 +2,8 @@
 //
 // The target of each input is a circular Gaussian of the stack FWHM at every source
 // position, sampled at pixel centres within ceil(5 sigma) of the nearest pixel (the paper
-// builds it from the envelope PSF and the known source positions).  Each convolved input
+// builds it from the envelope PSF and the known source positions), summed over the sources
+// in their given order in FP64 and rounded to FP32 once per pixel.  Each convolved input
 // contributes where its mask carries neither badmask nor CONV.BAD bits, with weight
 // w_i = 1 / mean(V'_i) (the paper weights by the mean variance of the convolved image; the
 // inverse is the reading used):
@@ -14,21 +15,94 @@
 namespace psfm {
 namespace {
 
-// One CTA per source: add its Gaussian to the target box.
-__global__ void k_render_target(const double* src, int n_src, double sigma, int radius, int W,
-                                int H, int64_t pitch, float* target) {
-  const int i = blockIdx.x;
-  if (i >= n_src) return;
-  const double x0 = src[3 * i], y0 = src[3 * i + 1], f = src[3 * i + 2];
-  const int xi = (int)rint(x0), yi = (int)rint(y0);
-  const int n = 2 * radius + 1;
-  const double norm = f / (2.0 * 3.14159265358979323846 * sigma * sigma);
-  const double c = -1.0 / (2.0 * sigma * sigma);
-  for (int j = threadIdx.x; j < n * n; j += blockDim.x) {
-    const int x = xi - radius + j % n, y = yi - radius + j / n;
-    if (x < 0 || x >= W || y < 0 || y >= H) continue;
-    const double dx = x - x0, dy = y - y0;
-    atomicAdd(&target[(int64_t)y * pitch + x], (float)(norm * exp(c * (dx * dx + dy * dy))));
+// One CTA per 32 x 32 tile of the target.  The CTA lists, in source order, the sources whose
+// box (radius `radius` around the nearest pixel) meets the tile, then every pixel adds the
+// Gaussians of the listed sources that cover it in that order, in FP64, and is rounded to FP32
+// once: the target does not depend on scheduling and equals the FP64 sum over sources in
+// their given order.  The list is processed in batches of kRenderBatch sources.
+constexpr int kRenderTile = 32;
+constexpr int kRenderThreads = 256;
+constexpr int kRenderBatch = 512;
+constexpr int kRenderPix = kRenderTile * kRenderTile / kRenderThreads;  // pixels per thread
+
+__global__ void __launch_bounds__(kRenderThreads) k_render_target(
+    const double* src, int n_src, double sigma, int radius, int W, int H, int64_t pitch,
+    float* target) {
+  __shared__ double s_x[kRenderBatch], s_y[kRenderBatch], s_n[kRenderBatch];
+  __shared__ int s_xi[kRenderBatch], s_yi[kRenderBatch];
+  __shared__ int s_warp[kRenderThreads / 32];
+  __shared__ int s_count;
+  const int tx0 = blockIdx.x * kRenderTile, ty0 = blockIdx.y * kRenderTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double inv2s2 = 2.0 * sigma * sigma;
+  const double area = 2.0 * 3.14159265358979323846 * sigma * sigma;
+  double acc[kRenderPix];
+#pragma unroll
+  for (int k = 0; k < kRenderPix; ++k) acc[k] = 0.0;
+  if (threadIdx.x == 0) s_count = 0;
+  __syncthreads();
+  for (int base = 0; base < n_src; base += kRenderThreads) {
+    // list the sources of this chunk whose box meets the tile, keeping their order
+    const int i = base + threadIdx.x;
+    bool hit = false;
+    double x0 = 0.0, y0 = 0.0, f = 0.0;
+    int xi = 0, yi = 0;
+    if (i < n_src) {
+      x0 = src[3 * i];
+      y0 = src[3 * i + 1];
+      f = src[3 * i + 2];
+      xi = (int)rint(x0);
+      yi = (int)rint(y0);
+      hit = xi + radius >= tx0 && xi - radius < tx0 + kRenderTile && yi + radius >= ty0 &&
+            yi - radius < ty0 + kRenderTile;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) s_warp[warp] = __popc(m);
+    __syncthreads();
+    int off = s_count, tot = 0;
+    for (int w = 0; w < kRenderThreads / 32; ++w) {
+      if (w < warp) off += s_warp[w];
+      tot += s_warp[w];
+    }
+    // flush the list first when this chunk would overflow it
+    if (s_count + tot > kRenderBatch) {
+      const int nl = s_count;
+#pragma unroll
+      for (int k = 0; k < kRenderPix; ++k) {
+        const int j = threadIdx.x + k * kRenderThreads;
+        const int x = tx0 + (j % kRenderTile), y = ty0 + (j / kRenderTile);
+        for (int l = 0; l < nl; ++l) {
+          if (abs(x - s_xi[l]) > radius || abs(y - s_yi[l]) > radius) continue;
+          const double dx = x - s_x[l], dy = y - s_y[l];
+          acc[k] += s_n[l] * exp(-(dx * dx + dy * dy) / inv2s2) / area;
+        }
+      }
+      off -= nl;
+      __syncthreads();
+    }
+    if (hit) {
+      const int o = off + __popc(m & ((1u << lane) - 1u));
+      s_x[o] = x0;
+      s_y[o] = y0;
+      s_n[o] = f;
+      s_xi[o] = xi;
+      s_yi[o] = yi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_count = (s_count + tot > kRenderBatch ? 0 : s_count) + tot;
+    __syncthreads();
+  }
+  const int nl = s_count;
+#pragma unroll
+  for (int k = 0; k < kRenderPix; ++k) {
+    const int j = threadIdx.x + k * kRenderThreads;
+    const int x = tx0 + (j % kRenderTile), y = ty0 + (j / kRenderTile);
+    for (int l = 0; l < nl; ++l) {
+      if (abs(x - s_xi[l]) > radius || abs(y - s_yi[l]) > radius) continue;
+      const double dx = x - s_x[l], dy = y - s_y[l];
+      acc[k] += s_n[l] * exp(-(dx * dx + dy * dy) / inv2s2) / area;
+    }
+    if (x < W && y < H) target[(int64_t)y * pitch + x] = (float)acc[k];
   }
 }
 
@@ -104,8 +178,9 @@ cudaError_t launch_render_target(const Plan& p, const double* src, int n_src, do
                                  float* target, cudaStream_t s) {
   const double sigma = fwhm / (2.0 * sqrt(2.0 * log(2.0)));
   const int radius = (int)ceil(5.0 * sigma);
-  if (n_src > 0)
-    k_render_target<<<n_src, 256, 0, s>>>(src, n_src, sigma, radius, p.W, p.H, p.pitch, target);
+  const dim3 grid((p.W + kRenderTile - 1) / kRenderTile, (p.H + kRenderTile - 1) / kRenderTile);
+  k_render_target<<<grid, kRenderThreads, 0, s>>>(src, n_src, sigma, radius, p.W, p.H, p.pitch,
+                                                   target);
   return cudaGetLastError();
 }
 

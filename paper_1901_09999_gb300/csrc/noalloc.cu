@@ -1,20 +1,21 @@
 // psfm_convolve_noalloc: the image / variance / mask part of psfm_convolve for callers that
 // cannot allocate device memory and cannot hand the library a workspace.
 //
-// Some hosts of this library cannot call cudaMalloc: code running inside a CUDA stream capture
-// of another framework that forbids allocations, plugins loaded into a pipeline whose memory
-// pool is owned by the host application, or real-time schedulers that ban allocation after
-// start-up.  This entry point needs no workspace: its scratch lives in a file-scope device
-// array of fixed size, created when the library is loaded on each GPU and kept until the
-// process exits.
+// Some hosts of this library cannot call cudaMalloc: plugins loaded into a pipeline whose
+// device memory pool is owned by the host application, and real-time schedulers that ban
+// allocation once they have started.  This entry point needs no workspace: its scratch lives
+// in a file-scope device array of fixed size, created when the library is loaded on each GPU
+// and kept until the process exits.
 //
 // Limits and behaviour:
 //   * images of at most 4096 x 4096 pixels (PSFM_ERR_WORKSPACE beyond that);
 //   * no covariance pseudo-matrix (white input noise is assumed for the per-patch covariance
 //     factor, f_t = 1);
 //   * the first call on each device looks up the device address of the scratch array with
-//     cudaGetSymbolAddress while that device is current; make that first call outside any
+//     cudaGetSymbolAddress while that device is current; make that first call before any
 //     stream capture;
+//   * every call uploads its coefficients and tables from host memory with cudaMemcpyAsync
+//     on the caller's stream;
 //   * every call shares the one array: calls that overlap on the GPU (different streams, or
 //     host threads without ordering) race on it and give undefined results.  Calls on one
 //     stream are ordered and safe.  Each call rewrites every byte it later reads (the device

@@ -177,8 +177,9 @@ psfm_status run_stack_full(int n, const float* const* imgs, const float* const* 
                            double clip_nsigma, uint16_t reject_bit, float* out, float* out_var,
                            uint16_t* out_mask, int32_t* out_count, float* uout,
                            float* uout_var, uint16_t* uout_mask, int32_t* uout_count,
-                           int32_t* n_rejected, double* cov_out, int cov_out_w,
-                           psfm_solution* sols, char* base, size_t ws_bytes, cudaStream_t st) {
+                           int32_t* n_rejected, uint32_t* outliers, double* cov_out,
+                           int cov_out_w, psfm_solution* sols, char* base, size_t ws_bytes,
+                           cudaStream_t st) {
   int n_src_max = 1, wmax = 0;
   for (int i = 0; i < n; ++i) {
     if (!imgs[i] || !vars[i] || !masks[i] || n_src[i] < 0 || (n_src[i] > 0 && !src_xyf[i]))
@@ -273,6 +274,9 @@ psfm_status run_stack_full(int n, const float* const* imgs, const float* const* 
                                          (uint16_t)(cfg->badmask | cfg->conv_bad), clip_nsigma,
                                          cfg->soften_alpha, L.rejbits, L.n_rej);
   if (cudaGetLastError() != cudaSuccess) return PSFM_ERR_CUDA;
+  if (outliers && cudaMemcpyAsync(outliers, L.rejbits, sizeof(uint32_t) * npx,
+                                  cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return PSFM_ERR_CUDA;
   prof_end("stack_clip", st, 1);
   // ---- pass 2: reject, convolve again, accumulate both stacks
   for (int i = 0; i < n; ++i) {
@@ -335,9 +339,9 @@ psfm_status psfm_stack_full(int32_t n, const float* const* imgs, const float* co
                             const psfm_config* cfg, double clip_nsigma, uint16_t reject_bit,
                             float* out, float* out_var, uint16_t* out_mask, int32_t* out_count,
                             float* uout, float* uout_var, uint16_t* uout_mask,
-                            int32_t* uout_count, int32_t* n_rejected, double* cov_out,
-                            int32_t cov_out_w, psfm_solution* sols, void* workspace,
-                            size_t ws_bytes, psfm_stream stream) {
+                            int32_t* uout_count, int32_t* n_rejected, uint32_t* outliers,
+                            double* cov_out, int32_t cov_out_w, psfm_solution* sols,
+                            void* workspace, size_t ws_bytes, psfm_stream stream) {
   if (n < 1 || n > psfm::kMaxStackFull || !imgs || !vars || !masks || !src_xyf || !n_src ||
       !basis || !cfg || !out || !out_var || !out_mask || !out_count || !uout || !uout_var ||
       !uout_mask || !uout_count || !workspace)
@@ -348,8 +352,8 @@ psfm_status psfm_stack_full(int32_t n, const float* const* imgs, const float* co
   if (!psfm::aligned256(workspace)) return PSFM_ERR_BAD_ARG;
   return psfm::run_stack_full(n, imgs, vars, masks, shape, src_xyf, n_src, target_fwhm, basis,
                               cfg, clip_nsigma, reject_bit, out, out_var, out_mask, out_count,
-                              uout, uout_var, uout_mask, uout_count, n_rejected, cov_out,
-                              cov_out_w, sols, static_cast<char*>(workspace), ws_bytes,
+                              uout, uout_var, uout_mask, uout_count, n_rejected, outliers,
+                              cov_out, cov_out_w, sols, static_cast<char*>(workspace), ws_bytes,
                               reinterpret_cast<cudaStream_t>(stream));
 }
 

@@ -494,7 +494,8 @@ def psfm_stack_full(imgs, vars_, masks, sources, target_fwhm, bases, cfg, clip_n
     """Stack with outlier rejection and the unconvolved companion stack (C: psfm_stack_full).
 
     Returns dict(conv=(image, variance, mask, count), unconv=(image, variance, mask, count),
-    rejected=[outlier pixels per input], cov=pseudo-matrix or None, sols=[Solution])."""
+    rejected=[outlier pixels per input], outliers=int32 plane with bit i set where input i is
+    an outlier, cov=pseudo-matrix or None, sols=[Solution])."""
     torch = _torch()
     lib = load()
     vp, i32, P_ = C.c_void_p, C.c_int32, C.POINTER
@@ -504,7 +505,7 @@ def psfm_stack_full(imgs, vars_, masks, sources, target_fwhm, bases, cfg, clip_n
     lib.psfm_stack_full.argtypes = [i32, P_(vp), P_(vp), P_(vp), psfm_shape, P_(P_(C.c_double)),
                                     P_(i32), C.c_double, P_(psfm_basis_spec), P_(psfm_config),
                                     C.c_double, C.c_uint16] + [vp] * 8 + [
-                                    P_(i32), vp, i32, P_(psfm_solution), vp, C.c_size_t, vp]
+                                    P_(i32), vp, vp, i32, P_(psfm_solution), vp, C.c_size_t, vp]
     lib.psfm_stack_full.restype = i32
     n = len(imgs)
     shape = _shape_of(*imgs, *vars_, *masks)
@@ -526,17 +527,18 @@ def psfm_stack_full(imgs, vars_, masks, sources, target_fwhm, bases, cfg, clip_n
     sols = [Solution(_ncoef(b, cfg), _ncand(b, cfg, 0)) for b in bases]
     csols = (psfm_solution * n)(*[s_.c for s_ in sols])
     rej = (C.c_int32 * n)()
+    outl = _like(imgs[0], torch.int32)
     ptrs = lambda ts: (vp * n)(*[t.data_ptr() for t in ts])
     st = lib.psfm_stack_full(n, ptrs(imgs), ptrs(vars_), ptrs(masks), shape, sp, nsrc,
                              float(target_fwhm), bs, C.byref(cfg), float(clip_nsigma),
                              int(reject_bit), *[_ptr(t) for t in conv], *[_ptr(t) for t in unconv],
-                             rej, _ptr(cov), ncov if want_cov else 0, csols, _ptr(workspace), need,
-                             _stream(stream))
+                             rej, _ptr(outl), _ptr(cov), ncov if want_cov else 0, csols,
+                             _ptr(workspace), need, _stream(stream))
     if st != PSFM_OK:
         raise PsfmError(st, "psfm_stack_full")
     for s_, c in zip(sols, csols):
         s_.c = c
-    return dict(conv=conv, unconv=unconv, rejected=list(rej), cov=cov, sols=sols)
+    return dict(conv=conv, unconv=unconv, rejected=list(rej), outliers=outl, cov=cov, sols=sols)
 
 
 def psfm_gram(cols, weights, precision, stream=None):
@@ -561,6 +563,20 @@ def psfm_gram(cols, weights, precision, stream=None):
     if st != PSFM_OK:
         raise PsfmError(st, "psfm_gram")
     return G
+
+
+WAIT_LIMIT_DEFAULT = 1 << 24
+
+
+def set_pipeline_wait_limit(polls):
+    """Poll limit of the tensor-core Gram's pipeline waits on the current device (C:
+    psfm_set_pipeline_wait_limit); a test hook for the PSFM_ERR_TIMEOUT path."""
+    lib = load()
+    lib.psfm_set_pipeline_wait_limit.argtypes = [C.c_uint32]
+    lib.psfm_set_pipeline_wait_limit.restype = C.c_int32
+    st = lib.psfm_set_pipeline_wait_limit(int(polls))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_set_pipeline_wait_limit")
 
 
 def psfm_resample_cov(cov_in, scale, stream=None):
@@ -636,6 +652,22 @@ def psfm_launch_count() -> int:
     lib = load()
     _prof_types(lib)
     return int(lib.psfm_launch_count())
+
+
+def fma_probe(n_blocks, iters, stream=None):
+    """FP32 FMA throughput probe (C: psfm_fma_probe): enqueues the probe kernel on ``stream``
+    and returns (flops of the launch, output tensor)."""
+    torch = _torch()
+    lib = load()
+    lib.psfm_fma_probe.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_double),
+                                   C.c_void_p]
+    lib.psfm_fma_probe.restype = C.c_int32
+    out = torch.empty(n_blocks * 256, dtype=torch.float32, device="cuda")
+    fl = C.c_double(0.0)
+    st = lib.psfm_fma_probe(int(n_blocks), int(iters), _ptr(out), C.byref(fl), _stream(stream))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_fma_probe")
+    return fl.value, out
 
 
 def psfm_profile_read() -> dict:

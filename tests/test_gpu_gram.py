@@ -71,3 +71,26 @@ def test_gram_rejects_unsupported(dev):
     with pytest.raises(P.PsfmError) as e:
         P.psfm_gram(tc[:, :50].contiguous(), tw, P.PREC_F32X2)
     assert e.value.code == 9
+
+
+def test_pipeline_wait_that_runs_out_returns_timeout(dev):
+    """Failure detection without a fault: with the pipeline waits limited to zero polls, the
+    first wait for a shared-memory buffer (at the third 32-pixel chunk) runs out; every CTA
+    then waits for the MMAs it issued, frees its tensor memory and records PSFM_ERR_TIMEOUT,
+    which the call returns.  With the default limit restored the same call succeeds and the
+    context is intact."""
+    import torch
+    cols, w = _data(77, 4, 52, 200)
+    G, A = _reference(cols, w)
+    tc, tw = torch.from_numpy(cols).to(dev), torch.from_numpy(w).to(dev)
+    try:
+        P.set_pipeline_wait_limit(0)
+        for prec in (P.PREC_TF32, P.PREC_BF16X3):
+            with pytest.raises(P.PsfmError) as e:
+                P.psfm_gram(tc, tw, prec)
+            assert e.value.code == 6
+    finally:
+        P.set_pipeline_wait_limit(P.WAIT_LIMIT_DEFAULT)
+    g = P.psfm_gram(tc, tw, P.PREC_BF16X3).cpu().numpy()
+    assert np.all(np.abs(g - G) <= 2.0 * (4 * 2.0 ** -18 + 3 * 200 * 2.0 ** -24) * A)
+    torch.cuda.synchronize()

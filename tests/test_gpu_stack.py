@@ -12,9 +12,9 @@ from paper_1901_09999_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# The target is rendered with FP32 atomics on the GPU (FP64 then rounded in the oracle), so
-# the fitted kernels see a right-hand side that differs in the last bits.
-KERNEL_RTOL = 1e-5
+# Realised kernels: as for a single solve (the target is rendered in FP64, source by source in
+# the given order, and rounded once on both sides).
+KERNEL_RTOL = 1e-6
 # Stacked image: 1e-3 of the local noise sigma, as for a single convolved image.
 IMG_TOL_SIGMA = 1e-3
 
@@ -131,22 +131,49 @@ def test_stack_full_spike_matches_oracle(dev, prec):
 
 
 def test_stack_full_uneven_warps_agree_with_oracle(dev):
-    """Uneven warps (different PSFs and masks): outlier decisions taken in FP32 on the GPU and
-    FP64 in the oracle may differ at pixels within rounding of the threshold, so the rejected
-    counts agree to 1 % and the stacks agree wherever the coverage counts agree (>= 99 %)."""
+    """Uneven warps (different PSFs and masks).  Outlier decisions are compared bit for bit;
+    a decision may differ only where the oracle's margin |I'_i - m| - n sqrt(V'_i + alpha |m|)
+    lies within what the parity tolerances allow (1e-3 sigma on every convolved value that
+    enters I'_i and the median m, 2e-5 on V'_i): such pixels are counted as fragile.  Coverage
+    may then differ only within r_bad of a fragile pixel, and the stacks agree everywhere else."""
     warps, src = _warps(7, 3, 320, 150)
     b, c, ob, oc = specs((0.7, 1.5, 3.0), (4, 2, 2), 10, 1, badmask=synth.BADMASK, grid_nx=4,
                          grid_ny=4, precision=P.PREC_F32X2)
     tf = 1.15 * max(w["fwhm"] for w in warps)
+    clip = 5.0
     r = P.psfm_stack_full([_put(w["image"], dev) for w in warps],
                           [_put(w["var"], dev) for w in warps],
-                          [_put(w["mask"], dev) for w in warps], [src] * 3, tf, [b] * 3, c)
-    o = O.stack_full(warps, src, tf, [ob] * 3, oc)
-    for g_, e_ in zip(r["rejected"], o["rejected"]):
-        assert abs(g_ - e_) <= max(2, 0.01 * e_)
+                          [_put(w["mask"], dev) for w in warps], [src] * 3, tf, [b] * 3, c,
+                          clip_nsigma=clip)
+    o = O.stack_full(warps, src, tf, [ob] * 3, oc, clip_nsigma=clip)
+    bits = host(r["outliers"]).view(np.uint32)
+    # largest local noise among the usable convolved inputs: bounds the error of the median
+    sig_max = np.zeros(bits.shape)
+    for O1, V1, ok1 in o["pass1"]:
+        sig_max = np.maximum(sig_max, np.where(ok1, np.sqrt(np.maximum(V1, 0.0)), 0.0))
+    fragile_any = np.zeros(bits.shape, bool)
+    n_fragile = 0
+    for i, (out, margin, (O1, V1, ok1)) in enumerate(zip(o["outliers"], o["margins"],
+                                                          o["pass1"])):
+        g = (bits >> i & 1).astype(bool)
+        diff = g != out
+        tol = 2 * IMG_TOL_SIGMA * sig_max + clip * np.sqrt(np.maximum(V1, 0.0)) * 1e-4
+        assert not np.any(diff & ~np.isfinite(margin)), "decision on an untested pixel"
+        assert np.all(np.abs(margin[diff]) <= tol[diff]), np.abs(margin[diff]).max()
+        n_fragile += int(diff.sum())
+        fragile_any |= diff
+        assert abs(r["rejected"][i] - o["rejected"][i]) <= int(diff.sum())
+    print(f"fragile outlier decisions: {n_fragile} of {bits.size * 3} tests")
+    rb = max(O.r_bad(s_) for s_ in o["sols"])
+    near = np.zeros_like(fragile_any)
+    H, W = near.shape
+    for y, x in zip(*np.nonzero(fragile_any)):
+        near[max(0, y - rb):y + rb + 1, max(0, x - rb):x + rb + 1] = True
     for key in ("conv", "unconv"):
         img, var, msk, cnt = [host(t) for t in r[key]]
         oimg, ovar, omsk, ocnt = o[key]
-        same = (cnt == ocnt) & (ocnt > 0)
-        assert same.sum() >= 0.99 * (ocnt > 0).sum()
+        assert np.all((cnt == ocnt) | near), key
+        same = (cnt == ocnt) & (ocnt > 0) & ~near
+        assert same.sum() >= 0.95 * (ocnt > 0).sum()
         assert np.all(np.abs(img[same] - oimg[same]) <= IMG_TOL_SIGMA * np.sqrt(ovar[same]))
+        assert np.allclose(var[same], ovar[same], rtol=VAR_RTOL, atol=0)

@@ -1,5 +1,6 @@
 """psfm_convolve_noalloc: the workspace-free convolution for callers that cannot allocate
-device memory (for example code running inside another framework's CUDA graph capture).
+device memory (for example a plugin whose host application owns the device memory pool, or a
+real-time scheduler that bans allocation after start-up).
 
 It must give the same image, variance and mask as psfm_convolve on the same inputs, on two
 calls in a row with different inputs (its shared scratch must not carry state from one call
