@@ -128,10 +128,10 @@ __device__ __forceinline__ uint16_t bf16_bits(float x) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
-// Column source of the stamp Grams inside the solve: basis columns from the FP32 design
-// block, then R (masked), 1 and I2 read from the images at the stamp pixels, weights
-// 1 / (V1 + V2) (0 at masked or off-image pixels).  After the Gram it forms the transformed
-// Gram and marks the stamp's block as cached.
+// Column source of the stamp Grams inside the solve: zero-sum basis columns psi_k C_k - s_k R
+// from the FP32 design block, then R (masked), 1 and I2 read from the images at the stamp
+// pixels, weights 1 / (V1 + V2) (0 at masked or off-image pixels).  After the Gram it marks
+// the stamp's block as cached.
 struct StampSource {
   StampParams P;
   int r, cx, cy;
@@ -161,30 +161,22 @@ struct StampSource {
   __device__ float value(int c, int pix) const {
     if (pix >= P.P) return 0.f;
     const int Nb = P.b.Nb;
-    if (c < Nb) return reinterpret_cast<const float*>(P.C)[((int64_t)r * Nb + c) * P.P + pix];
     int64_t o;
-    if (!pixel(pix, &o)) return 0.f;
-    if (c == Nb) return (P.m1[o] & P.badmask) ? 0.f : P.i1[o];
+    const bool on = pixel(pix, &o);
+    const float xr = (on && !(P.m1[o] & P.badmask)) ? P.i1[o] : 0.f;
+    if (c < Nb) {  // zero-sum design column psi_k C_k - s_k R, formed per pixel
+      const float cv = reinterpret_cast<const float*>(P.C)[((int64_t)r * Nb + c) * P.P + pix];
+      return (float)P.psi[c] * cv - (float)P.sk[c] * xr;
+    }
+    if (!on) return 0.f;
+    if (c == Nb) return xr;
     if (c == Nb + 1) return 1.f;
     return P.i2[o];
   }
-  __device__ double* gram() const { return P.G + (int64_t)r * P.Nc * P.Nc; }
+  // the Gram of the zero-sum columns is the transformed Gram the system is assembled from
+  __device__ double* gram() const { return P.Gt + (int64_t)r * P.Nc * P.Nc; }
   __device__ void fail(int code) const { atomicCAS(&P.st->error, 0, code); }
   __device__ void finish(int tid, int nthreads) const {
-    const int Nc = P.Nc, Nb = P.b.Nb, cR = Nb;
-    const double* Gr = gram();
-    double* Gtr = P.Gt + (int64_t)r * Nc * Nc;
-    for (int q = tid; q < Nc * Nc; q += nthreads) {
-      const int i = q / Nc, j = q - i * Nc;
-      const double ai = i < Nb ? P.psi[i] : 1.0, bi3 = i < Nb ? P.sk[i] : 0.0;
-      const double aj = j < Nb ? P.psi[j] : 1.0, bj3 = j < Nb ? P.sk[j] : 0.0;
-      double e = ai * aj * Gr[i * Nc + j];
-      if (bj3 != 0.0) e -= ai * bj3 * Gr[i * Nc + cR];
-      if (bi3 != 0.0) e -= bi3 * aj * Gr[cR * Nc + j];
-      if (bi3 != 0.0 && bj3 != 0.0) e += bi3 * bj3 * Gr[cR * Nc + cR];
-      Gtr[q] = e;
-    }
-    __syncthreads();
     if (tid == 0) {
       P.have[r] = P.ptr[r];
       P.fresh[r] = 1;

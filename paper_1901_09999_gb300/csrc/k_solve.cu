@@ -344,10 +344,12 @@ __global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
 // stamp r.  Each thread owns a 4 x 4 block of the Gram and one of `nsl` interleaved pixel
 // slices of every chunk (nsl a power of two, the slices of a block in adjacent lanes); its 16
 // double-float sums stay in registers over all chunks, the slices are combined by shuffles,
-// and each block writes its FP64 partial Gram.  The weighted columns w * A are formed once per
+// and each block writes its FP64 partial Gram.  The basis columns are staged as the zero-sum
+// design columns psi_k C_k - s_k X (X the image the term convolves) per pixel, so the
+// cancellation of the delta term happens once per pixel in double-float (as in the definition
+// of Eq. 4) and not between large Gram entries; the weighted columns w * A are formed once per
 // chunk in shared memory.  The last block of a stamp to finish (counted with an atomic) adds
-// the partials in split order, so the result does not depend on which block finishes last,
-// and forms the transformed Gram.
+// the partials in split order, so the result does not depend on which block finishes last.
 constexpr int kGramChunk = 64;
 // row stride of the staged columns: one float of padding puts the rows that the threads of a
 // warp read (different columns, same pixel) in different shared-memory banks
@@ -406,6 +408,23 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_stamp_gram_df(StampParams P
   }
   const float2* Cr = reinterpret_cast<const float2*>(P.C) + (int64_t)r * Nb * P.P;
   double* Gp = P.Gpart + ((int64_t)r * kGramSplit + split) * Nc * Nc;
+  // psi_k and s_k of every design column as double-floats, and the chunk's pixel values of the
+  // images the zero-sum delta terms use (masked R; I2 for the dual kernel's columns)
+  float* psh = wl + nch * kGramChunk;
+  float* psl = psh + Nb;
+  float* skh = psl + Nb;
+  float* skl = skh + Nb;
+  float* xr = skl + Nb;
+  float* xi = xr + kGramChunk;
+  const int nbk = P.b.Nb;
+  for (int c = tid; c < Nb; c += kGramThreads) {
+    const int k = c < nbk ? c : c - nbk;
+    const df a = df_split(P.psi[k]), b = df_split(P.sk[k]);
+    psh[c] = a.hi;
+    psl[c] = a.lo;
+    skh[c] = b.hi;
+    skl[c] = b.lo;
+  }
   const int nass = npair * nsl, rounds = (nass + kGramThreads - 1) / kGramThreads;
   for (int rd = 0; rd < rounds; ++rd) {
     const int pp = rd * kGramThreads + tid;
@@ -425,22 +444,35 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_stamp_gram_df(StampParams P
       const float* wht = wh + t * kGramChunk;
       const float* wlt = wl + t * kGramChunk;
       __syncthreads();
+      if (tid < kGramChunk) {
+        const int pix = base + tid;
+        float vr = 0.f, vi = 0.f;
+        if (pix < P.P) {
+          const int py = pix / P.sw, px = pix - py * P.sw;
+          const int gx = cx - P.s + px, gy = cy - P.s + py;
+          if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
+            const int64_t o = (int64_t)gy * P.g.pitch + gx;
+            vr = (P.m1[o] & P.badmask) ? 0.f : P.i1[o];
+            vi = P.i2[o];
+          }
+        }
+        xr[tid] = vr;
+        xi[tid] = vi;
+      }
+      __syncthreads();
       for (int i = tid; i < ncr * kGramChunk; i += kGramThreads) {
         const int c = i / kGramChunk, j = i - c * kGramChunk, pix = base + j;
         df v = {0.f, 0.f};
         if (pix < P.P) {
           if (c < Nb) {
             const float2 cv = Cr[(int64_t)c * P.P + pix];
-            v = df{cv.x, cv.y};
-          } else if (c < Nc) {
-            const int py = pix / P.sw, px = pix - py * P.sw;
-            const int gx = cx - P.s + px, gy = cy - P.s + py;
-            if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
-              const int64_t o = (int64_t)gy * P.g.pitch + gx;
-              if (c == Nb) v.hi = (P.m1[o] & P.badmask) ? 0.f : P.i1[o];
-              else if (c == Nb + 1) v.hi = 1.f;
-              else v.hi = P.i2[o];
+            v = df_mul(df{psh[c], psl[c]}, df{cv.x, cv.y});
+            if (skh[c] != 0.f) {
+              const float x = c < nbk ? xr[j] : xi[j];
+              v = df_add(v, df_neg(df_mul(df{skh[c], skl[c]}, df{x, 0.f})));
             }
+          } else if (c < Nc) {
+            v.hi = c == Nb ? xr[j] : (c == Nb + 1 ? 1.f : xi[j]);
           }
         }
         const df b = df_mul(df{wht[j], wlt[j]}, v);
@@ -488,29 +520,13 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_stamp_gram_df(StampParams P
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  double* Gr = P.G + (int64_t)r * Nc * Nc;
+  // the Gram of the zero-sum columns is the transformed Gram the system is assembled from
+  double* Gr = P.Gt + (int64_t)r * Nc * Nc;
   const double* Gp0 = P.Gpart + (int64_t)r * kGramSplit * Nc * Nc;
   for (int q = tid; q < Nc * Nc; q += kGramThreads) {
     double v = 0.0;
     for (int k = 0; k < nsplit; ++k) v += __ldcg(Gp0 + (int64_t)k * Nc * Nc + q);
     Gr[q] = v;
-  }
-  __syncthreads();
-  // transformed Gram: design column i of basis term k becomes psi_k C_i - s_k X, X the image
-  // the term convolves (R for the first N_b columns, I2 for the dual kernel's)
-  double* Gtr = P.Gt + (int64_t)r * Nc * Nc;
-  const int nbk = P.b.Nb;
-  for (int q = tid; q < Nc * Nc; q += kGramThreads) {
-    const int i = q / Nc, j = q - i * Nc;
-    const int ki = i < nbk ? i : i - nbk, kj = j < nbk ? j : j - nbk;
-    const double ai = i < Nb ? P.psi[ki] : 1.0, bi3 = i < Nb ? P.sk[ki] : 0.0;
-    const double aj = j < Nb ? P.psi[kj] : 1.0, bj3 = j < Nb ? P.sk[kj] : 0.0;
-    const int ci = i < nbk ? Nb : Nb + 2, cj = j < nbk ? Nb : Nb + 2;
-    double e = ai * aj * Gr[i * Nc + j];
-    if (bj3 != 0.0) e -= ai * bj3 * Gr[i * Nc + cj];
-    if (bi3 != 0.0) e -= bi3 * aj * Gr[ci * Nc + j];
-    if (bi3 != 0.0 && bj3 != 0.0) e += bi3 * bj3 * Gr[ci * Nc + cj];
-    Gtr[q] = e;
   }
   __syncthreads();
   if (tid == 0) {
@@ -520,8 +536,9 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_stamp_gram_df(StampParams P
   }
 }
 
-// grid (nreg): weighted Gram of the augmented design block of one stamp; products in T,
-// sums over 32-pixel chunks in T, chunk sums accumulated in FP64.
+// grid (nreg): weighted Gram of the augmented design block of one stamp (zero-sum basis
+// columns psi_k C_k - s_k R formed per pixel, then R, 1, I2); products in T, sums over 32-pixel
+// chunks in T, chunk sums accumulated in FP64.
 template <typename T>
 __global__ void __launch_bounds__(256) k_stamp_gram(StampParams P) {
   extern __shared__ double shd[];
@@ -547,11 +564,13 @@ __global__ void __launch_bounds__(256) k_stamp_gram(StampParams P) {
         const int gx = cx - P.s + px, gy = cy - P.s + py;
         const bool on = gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H;
         const int64_t o = (int64_t)gy * P.g.pitch + gx;
+        const T xr = (on && !(P.m1[o] & P.badmask)) ? (T)P.i1[o] : (T)0;
         if (c < Nb) {
-          v = Cr[(int64_t)c * P.P + pix];
+          // zero-sum design column psi_k C_k - s_k R, formed per pixel
+          v = (T)P.psi[c] * Cr[(int64_t)c * P.P + pix];
+          if (P.sk[c] != 0.0) v -= (T)P.sk[c] * xr;
         } else if (on) {
-          const bool ok1 = !(P.m1[o] & P.badmask);
-          if (c == Nb) v = ok1 ? (T)P.i1[o] : (T)0;
+          if (c == Nb) v = xr;
           else if (c == Nb + 1) v = 1;
           else v = (T)P.i2[o];
         }
@@ -606,7 +625,8 @@ __global__ void __launch_bounds__(256) k_stamp_gram(StampParams P) {
     }
   }
   __syncthreads();
-  double* Gr = P.G + (int64_t)r * Nc * Nc;
+  // the Gram of the zero-sum columns is the transformed Gram the system is assembled from
+  double* Gr = P.Gt + (int64_t)r * Nc * Nc;
   for (int pr = tid; pr < npair; pr += 256) {
     int bi = 0, rem = pr;
     while (rem >= nblk - bi) {
@@ -622,21 +642,6 @@ __global__ void __launch_bounds__(256) k_stamp_gram(StampParams P) {
           Gr[j * Nc + i] = acc[pr * 16 + e * 4 + f];
         }
       }
-  }
-  __syncthreads();
-  // transformed Gram: basis column k becomes psi_k C_k - s_k R (the zero-sum term B_k of
-  // Sec. 2 convolved with R); the R, 1 and I2 columns are unchanged
-  double* Gtr = P.Gt + (int64_t)r * Nc * Nc;
-  const int cR = Nb;
-  for (int q = tid; q < Nc * Nc; q += 256) {
-    const int i = q / Nc, j = q - i * Nc;
-    const double ai = i < Nb ? P.psi[i] : 1.0, bi = i < Nb ? P.sk[i] : 0.0;
-    const double aj = j < Nb ? P.psi[j] : 1.0, bj = j < Nb ? P.sk[j] : 0.0;
-    double e = ai * aj * Gr[i * Nc + j];
-    if (bj != 0.0) e -= ai * bj * Gr[i * Nc + cR];
-    if (bi != 0.0) e -= bi * aj * Gr[cR * Nc + j];
-    if (bi != 0.0 && bj != 0.0) e += bi * bj * Gr[cR * Nc + cR];
-    Gtr[q] = e;
   }
   __syncthreads();
   if (tid == 0) {
@@ -1754,7 +1759,6 @@ void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b) {
   b.ptr = ws.take<int32_t>(p.nreg);
   b.have = ws.take<int32_t>(p.nreg);
   b.C = ws.take<double>((size_t)p.nreg * p.Nd * p.P);
-  b.G = ws.take<double>((size_t)p.nreg * p.Nc * p.Nc);
   b.Gt = ws.take<double>((size_t)p.nreg * p.Nc * p.Nc);
   b.Gpart = ws.take<double>((size_t)p.nreg * kGramSplit * p.Nc * p.Nc);
   b.gram_count = ws.take<int32_t>(p.nreg);
@@ -1817,7 +1821,6 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   sp.have = b.have;
   sp.fresh = b.fresh;
   sp.C = b.C;
-  sp.G = b.G;
   sp.Gt = b.Gt;
   sp.Gpart = b.Gpart;
   sp.gram_count = b.gram_count;
@@ -1869,7 +1872,8 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
     sm_design = sizeof(float) * ((size_t)p.foot * p.foot + 2 * (size_t)p.foot * p.sw +
                                  2 * (size_t)(p.dmax + 1) * p.w);
     const int maxch = ((p.P + kGramChunk - 1) / kGramChunk + kGramSplit - 1) / kGramSplit;
-    sm_gram = sizeof(float) * (4 * nblk * 4 * kGramLd + 2 * maxch * kGramChunk);
+    sm_gram = sizeof(float) * (4 * nblk * 4 * kGramLd + 2 * maxch * kGramChunk + 4 * p.Nd +
+                               2 * kGramChunk);
   }
   if (sm_design > 200 * 1024 || sm_gram > 200 * 1024) return PSFM_ERR_UNSUPPORTED;
   // TF32 / BF16X3: FP32 design blocks, the Gram on the tensor cores (k_gram_tc.cu)

@@ -75,9 +75,42 @@ void prof_end(const char* name, cudaStream_t s, int n_launches) {
   t_begin = nullptr;
 }
 
+// FP32 FMA throughput probe: every thread runs kProbeChains independent FMA chains, unrolled
+// so that the loop costs two instructions per 8 * kProbeChains FMAs.  The chains' sum is
+// written out so that nothing is eliminated.
+constexpr int kProbeChains = 8;
+constexpr int kProbeUnroll = 8;
+
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, float* out) {
+  float a[kProbeChains];
+#pragma unroll
+  for (int j = 0; j < kProbeChains; ++j) a[j] = 1e-3f * (threadIdx.x + j);
+  const float b = 0.99999f, c = 1e-6f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < kProbeUnroll; ++u) {
+#pragma unroll
+      for (int j = 0; j < kProbeChains; ++j) a[j] = fmaf(a[j], b, c);
+    }
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int j = 0; j < kProbeChains; ++j) t += a[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
 }  // namespace psfm
 
 extern "C" {
+
+psfm_status psfm_fma_probe(int32_t n_blocks, int32_t iters, float* out, double* flops,
+                           psfm_stream stream) {
+  if (n_blocks < 1 || iters < 1 || !out) return PSFM_ERR_BAD_ARG;
+  psfm::k_fma_probe<<<n_blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(iters, out);
+  if (flops)
+    *flops = 2.0 * n_blocks * 256.0 * psfm::kProbeChains * psfm::kProbeUnroll * (double)iters;
+  return cudaGetLastError() == cudaSuccess ? PSFM_OK : PSFM_ERR_CUDA;
+}
 
 void psfm_profile_enable(int32_t on) {
   std::lock_guard<std::mutex> lk(psfm::g_mu);

@@ -27,8 +27,8 @@ struct SolveBuffers {
   int32_t* have;       // [nreg] rank whose design block is cached, -1 none
   // per-region stamp data
   void* C;       // [nreg][Nb][P] basis-convolved masked reference at the stamp pixels (float or double)
-  double* G;     // [nreg][Nc][Nc] weighted Gram of (basis columns, R, 1, I2)
-  double* Gt;    // [nreg][Nc][Nc] the same with basis columns psi_k C_k - s_k R
+  double* Gt;    // [nreg][Nc][Nc] weighted Gram of (zero-sum basis columns psi_k C_k - s_k X,
+                 // R, 1, I2)
   double* Gpart;        // [nreg][kGramSplit][Nc][Nc] partial Grams over pixel chunks
   int32_t* gram_count;  // [nreg] partial Grams finished for the stamp being built
   double* foot;  // [nreg][4] footprint sums F1, F2, n, unused

@@ -49,8 +49,7 @@ struct StampParams {
   int32_t* have;
   int32_t* fresh;  // [nreg] Gram recomputed in this iteration (added to M by k_system_delta)
   void* C;  // [nreg][Nb][P] of T (float or double, by precision mode)
-  double* G;
-  double* Gt;
+  double* Gt;      // [nreg][Nc][Nc] Gram of the zero-sum augmented design block
   double* Gpart;        // [nreg][kGramSplit][Nc][Nc] partial Grams (double-float mode)
   int32_t* gram_count;  // [nreg] partials finished, reset by the block that combines them
   double* footsum;

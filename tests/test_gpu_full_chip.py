@@ -18,7 +18,7 @@ import os
 import numpy as np
 import pytest
 
-from gpu_common import IMG_TOL_SIGMA, VAR_RTOL, device, host, kernel_rel_err, \
+from gpu_common import IMG_TOL_SIGMA, VAR_RTOL, coeff_rel_err, device, host, kernel_rel_err, \
     oracle_solution_from_gpu
 from oracle import psfm_oracle as O
 from paper_1901_09999_gb300 import psfm as P
@@ -28,6 +28,7 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "full_chip_seed2_oracle.npz")
 KERNEL_RTOL = 1e-6
+COEFF_RTOL = 1e-6
 B0_RTOL = 1e-9
 N_SAMPLES = 240
 
@@ -132,6 +133,10 @@ def test_full_chip_batch_matches_oracle(dev, chip):
             assert abs(q[k] - oq[k]) <= 1e-6 * max(1.0, abs(oq[k])), k
         assert abs(q["chi2_mean"] - float(used.mean())) <= 1e-4 * float(used.mean())
         assert q["flags"] == oq["flags"]
+        ce = coeff_rel_err(sol.coeff[:g["coeff"].size - 1], g["coeff"][:-1])
+        print(f"[coeff] full chip, copy {i}: normwise coefficient error {ce:.3e}, "
+              f"kernel {ke:.3e}")
+        assert ce <= COEFF_RTOL, ce
     # difference pseudo-matrix = (w1 P_conv + w2 delta) / (w1 + w2) (Sec. 4.4)
     Pc = O.pseudo_matrix(chip["osol"], chip["oc"])
     Pd = batch.cov[0].cpu().numpy()
