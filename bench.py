@@ -40,6 +40,13 @@ CONV_TRAFFIC_FULL_CHIP = 236.01408e6 + 75.43168e6
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3, "f32x2": 4}
+PRECISION_NOTE = {
+    "f32x2": "stamp design+Gram double-float (FP32 pairs), normal equations double-float "
+             "Cholesky + FP64 refinement, FP32 image/variance",
+    "fp64": "stamp design+Gram FP64, double-float Cholesky + FP64 refinement, FP32 image/variance",
+    "fp32": "stamp design+Gram FP32 (plain), FP32 image/variance",
+    "tf32": "FP32 stamp design, Gram on tensor cores (TF32), FP32 image/variance",
+    "bf16x3": "FP32 stamp design, Gram on tensor cores (BF16x3), FP32 image/variance"}
 
 
 def parse():
@@ -58,7 +65,10 @@ def parse():
     ap.add_argument("--precision", default="f32x2", choices=list(PRECISION))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the unbatched and plain FP32 comparison arms")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the exposure and stacking sub-results")
     return ap.parse_args()
 
 
@@ -121,7 +131,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}",
                                           "--format=csv,noheader,nounits", "-i", str(self.index),
-                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
@@ -160,38 +170,61 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-_ORACLE_INPUTS = None
-ORACLE_CUT = 288
+# Samples the FP64 oracle is timed on (a baseline, not a target):
+#  * "small": the 512 x 512 plain-method workload in full (30 stamps, S = 0, 27 terms);
+#  * "chip_block": a block of 4 x 3 subregions of the full chip's real 15 x 20 grid (each
+#    subregion 323 x 243 px, so 12 stamps and about 0.95 Mpix, plus the 30 px footprint margin
+#    on every side), with the full-chip basis (S = 2, 49 terms); its stamps per pixel are those
+#    of the chip, so the chip's rate follows linearly.
+BLOCK_GRID = (4, 3)
+BLOCK_MARGIN = 30   # stamp half width + kernel half width
 
 
-def write_oracle_inputs(path, chip=None):
-    """Save a 288 x 288 cut-out around the centre of a full chip (generated from the workload's
-    seed unless given as the 6 host arrays sci, ref, var_sci, var_ref, mask_sci, mask_ref)."""
+def chip_block(chip, k, W=None, H=None):
+    """Block k (row-major over the 15 / 4 x 20 / 3 blocks of the grid) of a full chip given as
+    the 6 host arrays (sci, ref, var_sci, var_ref, mask_sci, mask_ref)."""
+    H, W = chip[0].shape
+    gx, gy = WORKLOAD["grid"]
+    bx, by = BLOCK_GRID
+    nbx = gx // bx
+    i, j = k % nbx, (k // nbx) % (gy // by)
+    x0, x1 = (i * bx * W) // gx, ((i + 1) * bx * W) // gx
+    y0, y1 = (j * by * H) // gy, ((j + 1) * by * H) // gy
+    xa, xb = max(0, x0 - BLOCK_MARGIN), min(W, x1 + BLOCK_MARGIN)
+    ya, yb = max(0, y0 - BLOCK_MARGIN), min(H, y1 + BLOCK_MARGIN)
+    return tuple(np.ascontiguousarray(a[ya:yb, xa:xb]) for a in chip)
+
+
+def write_oracle_inputs(path, kind, chip=None, k=0):
+    """Save one oracle sample: the small workload (seed 1 + k), or block k of a full chip
+    (generated from the workload's seed unless given as the 6 host arrays)."""
     from paper_1901_09999_gb300 import synth
-    if chip is None:
-        f = synth.full_chip_field(WORKLOAD["seed"])
-        chip = (f.sci, f.ref, f.var_sci, f.var_ref, f.mask_sci, f.mask_ref)
-    sci, ref, var_sci, var_ref, mask_sci, mask_ref = chip
-    n = ORACLE_CUT
-    y0, x0 = (sci.shape[0] - n) // 2, (sci.shape[1] - n) // 2
-    cut = lambda a: np.ascontiguousarray(a[y0:y0 + n, x0:x0 + n])
-    np.savez(path, I1=cut(ref), I2=cut(sci), V1=cut(var_ref), V2=cut(var_sci), m1=cut(mask_ref),
-             m2=cut(mask_sci))
+    if kind == "small":
+        f = synth.small_gaussian_field(1 + k)
+        arrs = (f.sci, f.ref, f.var_sci, f.var_ref, f.mask_sci, f.mask_ref)
+    else:
+        if chip is None:
+            f = synth.full_chip_field(WORKLOAD["seed"])
+            chip = (f.sci, f.ref, f.var_sci, f.var_ref, f.mask_sci, f.mask_ref)
+        arrs = chip_block(chip, k)
+    np.savez(path, kind=kind, I2=arrs[0], I1=arrs[1], V2=arrs[2], V1=arrs[3], m2=arrs[4],
+             m1=arrs[5])
 
 
 def oracle_sample(path):
-    """Time the FP64 oracle (solve + convolve + variance + mask + covariance) on the cut-out
-    with the full-chip basis (S = 2, 49 terms) and a 2 x 2 stamp grid."""
-    global _ORACLE_INPUTS
+    """Time the FP64 oracle's whole path (extraction, solve with the rejection loop, convolve,
+    variance, mask, covariance pseudo-matrix) on one saved sample; returns (Mpix, seconds)."""
     from oracle import psfm_oracle as O
     from paper_1901_09999_gb300 import synth
-    if _ORACLE_INPUTS is None:
-        z = np.load(path)
-        _ORACLE_INPUTS = tuple(z[k] for k in ("I1", "I2", "V1", "V2", "m1", "m2"))
-    I1, I2, V1, V2, m1, m2 = _ORACLE_INPUTS
-    n = I1.shape[0]
-    ob = O.Basis(WORKLOAD["basis_sigma"], WORKLOAD["degrees"], 15, 2)
-    oc = O.Config(grid_nx=2, grid_ny=2, badmask=synth.BADMASK)
+    z = np.load(path)
+    kind = str(z["kind"])
+    I1, I2, V1, V2, m1, m2 = (z[k] for k in ("I1", "I2", "V1", "V2", "m1", "m2"))
+    if kind == "small":
+        ob = O.Basis((0.7, 1.5, 3.0), (4, 2, 2), 10, 0)
+        oc = O.Config(badmask=synth.BADMASK)
+    else:
+        ob = O.Basis(WORKLOAD["basis_sigma"], WORKLOAD["degrees"], 15, 2)
+        oc = O.Config(grid_nx=BLOCK_GRID[0], grid_ny=BLOCK_GRID[1], badmask=synth.BADMASK)
     t = time.perf_counter()
     sol = O.solve_kernel(I1, I2, V1, V2, m1, m2, ob, oc)
     O.convolve_image(I1, m1, sol, oc.badmask, I2)
@@ -199,19 +232,22 @@ def oracle_sample(path):
     O.mask_image(m1, sol, oc, m2)
     O.pseudo_matrix(sol, oc)
     dt = time.perf_counter() - t
-    return n * n / 1e6, dt
+    return I1.size / 1e6, dt
 
 
-def run_oracle_parallel(reps, cores, path):
-    """Run the oracle sample ``reps`` times in each of ``cores`` concurrent single-threaded
-    processes; returns (per-process [(Mpix, s)] lists, wall seconds)."""
+def run_oracle_parallel(reps, paths):
+    """Run the oracle sample ``reps`` times in one single-threaded process per path, all
+    concurrently; returns (per-process [(Mpix, s)] lists, wall seconds)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "r=[bench.oracle_sample(%r) for _ in range(%d)]; print(json.dumps(r))"
-            % (ROOT, path, reps))
     t = time.perf_counter()
-    procs = [subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
-                              stderr=subprocess.PIPE, text=True, cwd=ROOT) for _ in range(cores)]
+    procs = []
+    for path in paths:
+        code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+                "r=[bench.oracle_sample(%r) for _ in range(%d)]; print(json.dumps(r))"
+                % (ROOT, path, reps))
+        procs.append(subprocess.Popen([sys.executable, "-c", code], env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                                      cwd=ROOT))
     res = []
     for pr in procs:
         out, err = pr.communicate(timeout=1800)
@@ -233,38 +269,82 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(reps, path, cores):
-    res, wall = run_oracle_parallel(reps, cores, path)
-    busy = sum(b for r in res for _, b in r)
-    single, _ = run_oracle_parallel(2, 1, path)
-    return {"value": oracle_rate(res), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
-            "single_thread": oracle_rate(single),
-            "sample": f"{reps} x {ORACLE_CUT}x{ORACLE_CUT} centre cut-out of the first full chip per "
-                      f"process, {cores} concurrent single-threaded processes (S=2, 49 terms, 2x2 "
-                      f"stamp grid), solve+convolve+variance+mask+covariance, FP64 numpy; "
-                      f"{busy:.1f} CPU-s in {wall:.1f} s wall"}
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                return ln.split(":", 1)[1].strip()
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_paths(d, kind, n, chip=None):
+    paths = []
+    for k in range(n):
+        p = os.path.join(d, f"oracle_{kind}_{k}.npz")
+        write_oracle_inputs(p, kind, chip, k)
+        paths.append(p)
+    return paths
+
+
+def cpu_baseline(cores, chip=None):
+    """The oracle on the host cores: the small workload in full and a block of the full chip,
+    each single-threaded (one process) and on every core (one single-threaded process per core,
+    each on its own sample).  The headline value is the full-chip block on every core."""
+    rows = []
+    with tempfile.TemporaryDirectory() as d:
+        for kind, what in (("small", "512x512 plain-method workload in full (30 stamps, S=0, "
+                                     "27 terms)"),
+                           ("chip_block", "4x3-subregion block of the 4846x4868 chip's real "
+                                          "15x20 grid (12 stamps, ~1.0 Mpix with the 30 px "
+                                          "margin, S=2, 49 terms), scaled linearly to the "
+                                          "chip")):
+            paths = oracle_paths(d, kind, cores, chip)
+            single, w1 = run_oracle_parallel(1, paths[:1])
+            allc, wn = run_oracle_parallel(1, paths)
+            busy = sum(b for r in allc for _, b in r)
+            rows.append({"sample": kind, "what": what, "mpix_per_sample": single[0][0][0],
+                         "single_thread": oracle_rate(single), "all_cores": oracle_rate(allc),
+                         "processes": len(paths), "cpu_s": round(busy, 1),
+                         "wall_s": round(w1 + wn, 1)})
+    head = rows[1]
+    return {"value": head["all_cores"], "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "single_thread": head["single_thread"], "cpu_model": cpu_model(), "nproc": cores,
+            "sample": f"FP64 numpy oracle, whole path (extraction, solve with rejection, convolve, "
+                      f"variance, mask, pseudo-matrix); value = {head['what']}, one "
+                      f"single-threaded process per core ({cores}), each on its own block",
+            "rows": rows}
 
 
 def reference_arm(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores, on blocks of the
+    full-chip workload (each step: one 4 x 3-subregion block of the real 15 x 20 grid in each of
+    one single-threaded process per core)."""
     cores = host_cores()
     with tempfile.TemporaryDirectory() as d:
-        path = os.path.join(d, "oracle_cut.npz")
-        write_oracle_inputs(path)
+        paths = oracle_paths(d, "chip_block", cores)
         for _ in range(args.warmup):
-            run_oracle_parallel(1, cores, path)
-        res, wall = run_oracle_parallel(args.steps, cores, path)
+            run_oracle_parallel(1, paths)
+        res, wall = run_oracle_parallel(args.steps, paths)
     val = oracle_rate(res)
     busy = sum(b for r in res for _, b in r)
+    mpix = res[0][0][0]
+    sample = (f"{args.steps} step(s); per step one 4x3-subregion block (~{mpix:.2f} Mpix with "
+              f"margin, 12 stamps) of the full chip's 15x20 grid in each of {cores} "
+              f"single-threaded processes; {busy:.1f} CPU-s")
     print(json.dumps({
         "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference", "device": f"host cores only ({cores}); the GPUs of the launch idle",
-        "config": dict(WORKLOAD, sample=f"{ORACLE_CUT}x{ORACLE_CUT} centre cut-out per process "
-                                        f"per step, {cores} processes"),
+        "config": dict(WORKLOAD, sample=sample),
         "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} x {ORACLE_CUT}x{ORACLE_CUT} cut-outs in each of "
-                                   f"{cores} single-threaded processes, {busy:.1f} CPU-s"},
+                         "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -291,15 +371,12 @@ STACK = dict(workload="stack_16_warps_6000x6000_target_fwhm7.5_S1", warps=16, si
              sources=6000, target_fwhm=7.5, spatial_order=1, grid=(12, 12), seed=5)
 
 
-def run_stack(args, world, local):
+def stack_result(dev, args, steps, warmup, stream):
     """Config 5: PSF-homogenised stack of 16 warps of one 6000 x 6000 skycell (psfm_stack: each
     warp matched to a Gaussian target of FWHM 7.5 px, convolved with its variance, mask and
-    pseudo-matrix, then the inverse-variance weighted coadd).  Mpix/s counts input pixels."""
+    pseudo-matrix, then the inverse-variance weighted coadd).  Mpix/s counts input pixels.
+    Returns a result dict (value, ms_per_step, config, launches, stage times)."""
     import torch
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    from paper_1901_09999_gb300 import build
-    build.build()
     from paper_1901_09999_gb300 import psfm as P
     from paper_1901_09999_gb300 import synth
     n, size = STACK["warps"], STACK["size"]
@@ -312,7 +389,6 @@ def run_stack(args, world, local):
     imgs = [w["image"] for w in warps]
     vars_ = [w["var"] for w in warps]
     masks = [w["mask"] for w in warps]
-    stream = torch.cuda.Stream()
     shape = P.psfm_shape(size, size, size)
     ws = torch.empty(P.psfm_workspace_size(P.OP_STACK, shape, b, cfg, len(src)), dtype=torch.uint8,
                      device=dev)
@@ -322,18 +398,16 @@ def run_stack(args, world, local):
                             workspace=ws, stream=stream)
 
     with torch.cuda.stream(stream):
-        for _ in range(max(3, args.warmup)):
+        for _ in range(warmup):
             out = step()
         torch.cuda.synchronize()
         l0 = P.psfm_launch_count()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
-            torch.cuda.synchronize()
-            e0.record(stream)
-            for _ in range(args.steps):
-                out = step()
-            e1.record(stream)
-            torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            out = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         launches = P.psfm_launch_count() - l0
         P.psfm_profile_enable(True)
@@ -341,27 +415,90 @@ def run_stack(args, world, local):
         torch.cuda.synchronize()
         prof = P.psfm_profile_read()
         P.psfm_profile_enable(False)
-    mpix_in = n * size * size / 1e6
-    f_img, _ = flops_per_pixel(b)
-    conv_ms, conv_n, _ = prof.get("conv_image", (float("nan"), 1, 1))
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
-    achieved = size * size * f_img / (conv_ms / conv_n / 1e3) / 1e12
     cnt = out[3].cpu().numpy()
+    conv_ms, conv_n, _ = prof.get("conv_image", (float("nan"), 1, 1))
+    f_img, _ = flops_per_pixel(b)
+    res = {"value": n * size * size / 1e6 * steps / (ms / 1e3), "unit": "Mpix/s",
+           "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
+           "config": dict(STACK, h=h, basis_sigma=list(sig), degrees=[6, 4, 2],
+                          precision=args.precision, counts="input pixels",
+                          output_mpix=size * size / 1e6, coverage_mean=float(cnt.mean()),
+                          l2="inputs larger than L2"),
+           "gpu_launches": launches, "conv_image_ms": conv_ms / conv_n,
+           "conv_image_tflops": size * size * f_img / (conv_ms / conv_n / 1e3) / 1e12,
+           "stages_ms": {k: v[0] for k, v in prof.items()}}
+    del warps, imgs, vars_, masks, ws, out
+    return res
+
+
+def exposure_result(dev, args, steps, warmup, stream):
+    """Config 4: one exposure of 60 uneven chips in one batch (graph replay); returns a result
+    dict (value, ms_per_step, config, launches)."""
+    import torch
+    from paper_1901_09999_gb300 import psfm as P
+    chips, bases, cfg = exposure_chips(dev, precision=args.precision)
+    mpix = sum(c["img"].numel() for c in chips) / 1e6
+    batch = P.Batch(chips, bases, cfg, n_streams=args.streams, want_cov=True)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            batch.run(stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            batch.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sols = batch.solutions(stream)
+    res = {"value": mpix * steps / (ms / 1e3), "unit": "Mpix/s", "ms_per_step": ms / steps,
+           "steps": steps, "warmup": warmup,
+           "config": {"workload": "exposure_60_uneven_chips_S1-3_49-70terms", "chips": len(chips),
+                      "mpix": mpix, "precision": args.precision,
+                      "batching": f"{len(chips)} chips on {args.streams} streams, CUDA graph "
+                                  "replay"},
+           "gpu_launches": batch.kernel_count() * steps,
+           "stamps_used_min": min(s_.n_used for s_ in sols)}
+    batch.close()
+    del chips, batch
+    return res
+
+
+def run_stack(args, world, local):
+    """--stack: the stacking workload as the bench line."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1901_09999_gb300 import build
+    build.build()
+    stream = torch.cuda.Stream()
+    with ClockSampler(local) as clk:
+        r = stack_result(dev, args, args.steps, max(3, args.warmup), stream)
     print(json.dumps({
-        "metric": METRIC, "value": mpix_in * args.steps / (ms / 1e3), "unit": "Mpix/s",
-        "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(STACK, h=h, basis_sigma=list(sig), degrees=[6, 4, 2],
-                       precision=args.precision, counts="input pixels",
-                       output_mpix=size * size / 1e6,
-                       coverage_mean=float(cnt.mean()), l2="inputs larger than L2"),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_conv_image",
-                     "kernel_ms": conv_ms / conv_n},
-        "gpu_launches": launches, "clocks": clk.summary(),
-        "stages_ms": {k: v[0] for k, v in prof.items()}}))
+        "metric": METRIC, "value": r["value"], "unit": "Mpix/s", "n_gpus": world,
+        "steps": args.steps, "warmup": r["warmup"], "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": r["config"], "gpu_launches": r["gpu_launches"],
+        "clocks": clk.summary(), "stages_ms": r["stages_ms"]}))
     return 0
+
+
+def fp32_peak_probe(dev, stream, sms):
+    """Measured FP32 FMA throughput (TFLOP/s) of the library's probe kernel: 8 blocks of 256
+    threads per SM, 8 independent chains per thread; best of 3 launches after one warm-up."""
+    import torch
+    from paper_1901_09999_gb300 import psfm as P
+    best = 0.0
+    with torch.cuda.stream(stream):
+        P.fma_probe(sms * 8, 4000, stream)
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fl, _ = P.fma_probe(sms * 8, 40000, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = max(best, fl / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
 
 
 def max_over_ranks(ms, world, device=None):
@@ -480,6 +617,10 @@ def main():
 
     # roofline of the dominant kernel, timed with the library's CUDA events on its stream in a
     # separate (non-graph, unshared) subtraction of chip 0 right after the timed region
+    clocks = clk.summary()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else 2070.0
     c0, b0 = chips[0], bases[0]
     P.psfm_profile_enable(True)
     with torch.cuda.stream(stream):
@@ -493,50 +634,77 @@ def main():
     npx0 = c0["img"].numel()
     conv_ms, conv_n, _ = prof.get("conv_image", (float("nan"), 1, 1))
     var_ms, var_n, _ = prof.get("variance", (float("nan"), 1, 1))
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    peak = sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    probe = fp32_peak_probe(dev, stream, sms)
     achieved = npx0 * f_img / (conv_ms / conv_n / 1e3) / 1e12
+    step_flops = sum(c["img"].numel() * sum(flops_per_pixel(b)) for c, b in zip(chips, bases))
+    step_tflops = step_flops / (ms / args.steps / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": (CONV_TRAFFIC_FULL_CHIP if (not args.small and not args.exposure)
                             else None),
                 "kernel": "k_conv_image", "kernel_ms": conv_ms / conv_n,
                 "algorithmic_flop_per_px": f_img,
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived; an "
-                             "FMA-chain probe measured 74.7 TFLOP/s)",
+                "peak_note": f"FP32 FMA: {sms} SMs (device properties) x 128 lanes x 2 flop x "
+                             f"{sm_mhz:.0f} MHz (median SM clock sampled in the timed region)",
+                "peak_probe": probe, "frac_of_probe": achieved / probe,
                 "variance_kernel": {"achieved": npx0 * f_var / (var_ms / var_n / 1e3) / 1e12,
-                                    "ms": var_ms / var_n}}
+                                    "ms": var_ms / var_n},
+                "step": {"flop_per_px": f_img + f_var, "achieved": step_tflops,
+                         "frac": step_tflops / peak,
+                         "what": "image + variance algorithmic flops of every chip of a step / "
+                                 "ms_per_step (the solve side counted as overhead)"}}
     stages = {k: v[0] / v[2] for k, v in prof.items()}
 
-    # the plain FP32 GPU path on the same chips: one unbatched psfm_subtract per chip with FP32
-    # stamp design and Gram, no streams or graph
-    plain = None
+    # comparison arms on the same chips: (1) batching: one unbatched psfm_subtract per chip at
+    # the same precision; (2) precision: the same batch with FP32 stamp design and Gram (the
+    # plain FP32 path; its normal equations are not numerically positive definite, so it takes
+    # the FP64 LU fallback, and it misses the parity tolerances)
+    comparisons = None
     if not args.no_plain and not args.single:
-        _, cfg32 = chip_specs("fp32", args.small)
-        outs32 = [dict(out=P._like(c["img"]), out_var=P._like(c["img"]),
-                       out_mask=P._like(c["mask_img"])) for c in chips]
-        ws32 = torch.empty(max(P.psfm_workspace_size(
+        def time_arm(fn, n):
+            with torch.cuda.stream(stream):
+                fn()
+                torch.cuda.synchronize()
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                for _ in range(n):
+                    fn()
+                a1.record(stream)
+                torch.cuda.synchronize()
+            return a0.elapsed_time(a1) / n
+
+        outs1 = [dict(out=P._like(c["img"]), out_var=P._like(c["img"]),
+                      out_mask=P._like(c["mask_img"])) for c in chips]
+        ws1 = torch.empty(max(P.psfm_workspace_size(
             P.OP_SUBTRACT, P.psfm_shape(c["img"].shape[1], c["img"].shape[0], c["img"].stride(0)),
-            b, cfg32) for c, b in zip(chips, bases)), dtype=torch.uint8, device=dev)
+            b, cfg) for c, b in zip(chips, bases)), dtype=torch.uint8, device=dev)
 
-        def plain_pass():
-            for c, b, o in zip(chips, bases, outs32):
+        def unbatched():
+            for c, b, o in zip(chips, bases, outs1):
                 P.psfm_subtract(c["img"], c["ref"], c["var_img"], c["var_ref"], c["mask_img"],
-                                c["mask_ref"], b, cfg32, workspace=ws32, stream=stream, **o)
+                                c["mask_ref"], b, cfg, workspace=ws1, stream=stream, **o)
 
-        with torch.cuda.stream(stream):
-            plain_pass()
-            torch.cuda.synchronize()
-            n3 = max(1, min(3, args.steps))
-            e0.record(stream)
-            for _ in range(n3):
-                plain_pass()
-            e1.record(stream)
-            torch.cuda.synchronize()
-        pms = e0.elapsed_time(e1) / n3
-        plain = {"value": px_per_step / 1e6 / (pms / 1e3), "unit": "Mpix/s", "ms_per_step": pms,
-                 "what": "same chips, one unbatched psfm_subtract each, FP32 stamp design+Gram",
-                 "batched_speedup": value / (px_per_step / 1e6 / (pms / 1e3))}
-        del outs32, ws32
+        n3 = max(1, min(3, args.steps))
+        ums = time_arm(unbatched, n3)
+        del outs1, ws1
+        _, cfg32 = chip_specs("fp32", args.small)
+        batch32 = P.Batch(chips, bases, cfg32, n_streams=args.streams, want_cov=True)
+        pms = time_arm(lambda: batch32.run(stream), n3)
+        batch32.close()
+        del batch32
+        comparisons = {
+            "unbatched_same_precision": {
+                "value": px_per_step / 1e6 / (ums / 1e3), "unit": "Mpix/s", "ms_per_step": ums,
+                "what": f"same chips, one psfm_subtract each ({args.precision}), no streams or "
+                        "graph"},
+            "batched_plain_fp32": {
+                "value": px_per_step / 1e6 / (pms / 1e3), "unit": "Mpix/s", "ms_per_step": pms,
+                "what": "same batch (streams + graph), FP32 stamp design and Gram; fails the "
+                        "parity tolerances (FP32 normal equations; FP64 LU fallback)"},
+            "batched_over_unbatched": ums / (ms / args.steps),
+            "this_precision_over_plain_fp32": pms / (ms / args.steps)}
 
     e2e = None
     if not args.no_e2e and not args.exposure:
@@ -630,6 +798,21 @@ def main():
                "overlap": "copies of one step overlap the compute of the next (two buffer sets)"
                           if batch is not None else "none"}
 
+    # the batching and stacking workloads as sub-results of the same run (their own steps)
+    subs = {}
+    if not args.no_sub and not args.small and not args.exposure and not args.single:
+        if batch is not None:
+            batch.close()
+            batch = None
+        del chips
+        torch.cuda.empty_cache()
+        for name, fn in (("exposure", exposure_result), ("stack", stack_result)):
+            try:
+                subs[name] = fn(dev, args, 3, 2, stream)
+            except Exception as e:  # reported, not fatal for the headline
+                subs[name] = {"error": str(e)[-300:]}
+            torch.cuda.empty_cache()
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -637,29 +820,25 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         try:
-            with tempfile.TemporaryDirectory() as d:
-                path = os.path.join(d, "oracle_cut.npz")
-                write_oracle_inputs(path, oracle_chip)
-                cpu = cpu_baseline(4, path, host_cores())
+            cpu = cpu_baseline(host_cores(), oracle_chip)
         except Exception as e:  # the oracle is a reported baseline only
             cpu = {"error": str(e)[-300:]}
     sol_info = None
     if sols is not None:
-        sol_info = [{"n_used": s.n_used, "n_iter": s.n_iter, "b0": s.b0, "r_bad": s.r_bad}
-                    for s in sols[:4]]
+        sol_info = [{"n_used": s_.n_used, "n_iter": s_.n_iter, "b0": s_.b0, "r_bad": s_.r_bad}
+                    for s_ in sols[:4]]
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload, l2="inputs larger than L2 (472 MB per chip), no flush",
-                       precision=f"stamp design+Gram {args.precision}, normal equations "
-                                 "double-float Cholesky + FP64 refinement, FP32 image/variance",
+                       precision=PRECISION_NOTE[args.precision],
                        batching=("none" if args.single else
-                                 f"{len(chips)} chips on {args.streams} streams, CUDA graph replay"),
+                                 f"{nchips} chips on {args.streams} streams, CUDA graph replay"),
                        parallelism=f"replicas x{world}"),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "plain_fp32": plain,
-        "clocks": clk.summary(), "single_chip_stages_ms": stages, "solutions": sol_info,
+        "comparisons": comparisons, "sub_results": subs or None,
+        "clocks": clocks, "single_chip_stages_ms": stages, "solutions": sol_info,
     }
     print(json.dumps(line))
     if batch is not None:
