@@ -39,14 +39,17 @@ WORKLOAD = dict(
 CONV_TRAFFIC_FULL_CHIP = 236.01408e6 + 75.43168e6
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3, "f32x2": 4}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3, "f32x2": 4, "bf16x6": 5}
 PRECISION_NOTE = {
     "f32x2": "stamp design+Gram double-float (FP32 pairs), normal equations double-float "
              "Cholesky + FP64 refinement, FP32 image/variance",
     "fp64": "stamp design+Gram FP64, double-float Cholesky + FP64 refinement, FP32 image/variance",
     "fp32": "stamp design+Gram FP32 (plain), FP32 image/variance",
     "tf32": "FP32 stamp design, Gram on tensor cores (TF32), FP32 image/variance",
-    "bf16x3": "FP32 stamp design, Gram on tensor cores (BF16x3), FP32 image/variance"}
+    "bf16x3": "FP32 stamp design, Gram on tensor cores (BF16x3), FP32 image/variance",
+    "bf16x6": "stamp design double-float, Gram on tensor cores from six BF16 slices per operand "
+              "with exact per-level integer sums, double-float Cholesky + FP64 refinement, FP32 "
+              "image/variance"}
 
 
 def parse():
@@ -67,6 +70,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the unbatched and plain FP32 comparison arms")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="default image-convolution launch shape (no autotuning)")
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the exposure and stacking sub-results")
     return ap.parse_args()
@@ -390,6 +395,8 @@ def stack_result(dev, args, steps, warmup, stream):
     vars_ = [w["var"] for w in warps]
     masks = [w["mask"] for w in warps]
     shape = P.psfm_shape(size, size, size)
+    if not args.no_tune:
+        autotune([b], [(size, size)], stream)
     ws = torch.empty(P.psfm_workspace_size(P.OP_STACK, shape, b, cfg, len(src)), dtype=torch.uint8,
                      device=dev)
 
@@ -438,6 +445,8 @@ def exposure_result(dev, args, steps, warmup, stream):
     from paper_1901_09999_gb300 import psfm as P
     chips, bases, cfg = exposure_chips(dev, precision=args.precision)
     mpix = sum(c["img"].numel() for c in chips) / 1e6
+    if not args.no_tune:
+        autotune(bases, [(c["img"].shape[1], c["img"].shape[0]) for c in chips], stream)
     batch = P.Batch(chips, bases, cfg, n_streams=args.streams, want_cov=True)
     with torch.cuda.stream(stream):
         for _ in range(warmup):
@@ -481,6 +490,41 @@ def run_stack(args, world, local):
         "data": "synthetic", "config": r["config"], "gpu_launches": r["gpu_launches"],
         "clocks": clk.summary(), "stages_ms": r["stages_ms"]}))
     return 0
+
+
+def autotune(bases, sizes, stream):
+    """Tunes the image convolution's launch shape (tile height, planes per chunk) for every
+    distinct basis class of the workload on a synthetic image of that class's size (the
+    largest chip of the class: larger than L2, as the real inputs are, so that the staging of
+    each tile from HBM is part of what is timed), unless the library's table has it already
+    (loaded from PSFM_TUNE_CACHE when set).  Returns the table entries used and the seconds
+    spent."""
+    from paper_1901_09999_gb300 import psfm as P
+    t0 = time.perf_counter()
+    cache = os.environ.get("PSFM_TUNE_CACHE")
+    if cache and os.path.exists(cache):
+        try:
+            P.tune_load(cache)
+        except Exception:
+            pass
+    have = {(e["half_width"], e["spatial_order"], tuple(e["degree"])) for e in P.tune_entries()}
+    classes = {}
+    for b, (w, h) in zip(bases, sizes):
+        key = (b.half_width, b.spatial_order, tuple(b.degree[:b.n_gauss]))
+        cw, ch = classes.get(key, (0, 0, None))[:2]
+        classes[key] = (max(cw, w), max(ch, h), b)
+    for key, (w, h, b) in classes.items():
+        if key not in have:
+            P.tune_conv(b, w, h, stream)
+    if cache:
+        try:
+            os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+            P.tune_save(cache)
+        except Exception:
+            pass
+    used = [e for e in P.tune_entries()
+            if (e["half_width"], e["spatial_order"], tuple(e["degree"])) in classes]
+    return used, time.perf_counter() - t0
 
 
 def fp32_peak_probe(dev, stream, sms):
@@ -569,6 +613,10 @@ def main():
     del host_chips
     px_per_step = sum(c["img"].numel() for c in chips)
     stream = torch.cuda.Stream()
+    tuning, tuning_s = (None, 0.0)
+    if not args.no_tune:
+        tuning, tuning_s = autotune(bases, [(c["img"].shape[1], c["img"].shape[0]) for c in chips],
+                                    stream)
 
     if args.single:
         c0 = chips[0]
@@ -838,6 +886,9 @@ def main():
                        parallelism=f"replicas x{world}"),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "comparisons": comparisons, "sub_results": subs or None,
+        "tuning": {"entries": tuning, "seconds": tuning_s,
+                   "what": "image-convolution launch shape per basis class, chosen by the "
+                           "library's autotuner (psfm_tune_conv) before the timed region"},
         "clocks": clocks, "single_chip_stages_ms": stages, "solutions": sol_info,
     }
     print(json.dumps(line))

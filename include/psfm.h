@@ -99,6 +99,9 @@ typedef struct {
 #define PSFM_PREC_BF16X3 3   /* FP32 design; Gram on the tensor cores from a BF16 hi/lo split,
                                 3 products (hi*hi + hi*lo + lo*hi), FP32 sums */
 #define PSFM_PREC_F32X2 4    /* design and Gram in double-float (FP32 pairs, ~48 bits) */
+#define PSFM_PREC_BF16X6 5   /* double-float design; Gram on the tensor cores from seven BF16
+                                slices per operand, exact per-level sums (>= 48 bits; at most
+                                64 augmented columns) */
 
 /* Options; psfm_config_default() fills the defaults noted in brackets. */
 typedef struct {
@@ -432,6 +435,9 @@ psfm_status psfm_convolve_noalloc(const float* ref, const float* var_ref,
  * gram: device [n_blocks][n_cols][n_cols] double, written symmetric.  precision:
  *   PSFM_PREC_FP64   FP64 products and sums (the reference; workspace unused, may be NULL);
  *   PSFM_PREC_TF32   tensor cores, TF32 products, FP32 accumulation, n_cols <= 128;
+ *   PSFM_PREC_BF16X6 tensor cores, seven BF16 slices per operand (each column scaled by a
+ *                    power of two), 28 slice products, levels 0..3 summed exactly as integers
+ *                    over 256-pixel groups, n_cols <= 64 (at least 48 bits, like double-float);
  *   PSFM_PREC_BF16X3 tensor cores, BF16 hi/lo split, three products, FP32 accumulation,
  *                    n_cols <= 128;
  * others return PSFM_ERR_UNSUPPORTED.  The tensor-core modes need PSFM_GRAM_WORKSPACE bytes of
@@ -464,6 +470,37 @@ int32_t psfm_profile_count(void);
 int32_t psfm_profile_entry(int32_t i, char* name, int32_t name_cap, double* ms,
                            long long* launches, long long* calls);
 long long psfm_launch_count(void);
+
+/* Autotuner of the image convolution's launch shape (no counterpart in the paper).  The
+ * library keeps a table, per basis class (half width, spatial order, Gaussian count and degrees),
+ * of the tile height the image convolution is launched with in psfm_convolve, psfm_subtract,
+ * the batches and the stacks: 64 output rows (two CTAs of 8 warps per SM) or 128 (one CTA of
+ * 16 warps); classes not in the table use 64.  Entries apply to launches enqueued (or
+ * captured) after they are set.
+ * psfm_tune_conv times both heights for `basis` on a synthetic width x height image (three
+ * launches each, median, CUDA events on `stream`, which it synchronises; give the size of the
+ * images the shape will serve: whether a tile's inputs come from L2 or from HBM changes which
+ * shape is fastest), stores the faster in the table and, if `out` is not NULL, returns it
+ * (ms = its median time).  Its workspace (psfm_tune_conv_workspace_size bytes, 256-byte
+ * aligned device memory) holds the image, the output and the tables.  psfm_tune_get /
+ * psfm_tune_set / psfm_tune_count / psfm_tune_clear read and write the table (for example to
+ * persist it between processes).  The table is shared by every thread of the process.
+ * Errors: BAD_ARG, WORKSPACE, UNSUPPORTED, CUDA. */
+typedef struct {
+  int32_t half_width, spatial_order, n_gauss;
+  int32_t degree[PSFM_MAX_GAUSS];
+  int32_t tile_rows;    /* 64 or 128 */
+  int32_t plane_chunk;  /* horizontal planes per shared-memory chunk: 4 (0 reads as 4) */
+  float ms;             /* measured median time of the tuning image, or 0 */
+} psfm_tune_entry;
+size_t psfm_tune_conv_workspace_size(int32_t width, int32_t height, const psfm_basis_spec* basis);
+psfm_status psfm_tune_conv(int32_t width, int32_t height, const psfm_basis_spec* basis,
+                           void* workspace, size_t ws_bytes, psfm_stream stream,
+                           psfm_tune_entry* out);
+int32_t psfm_tune_count(void);
+psfm_status psfm_tune_get(int32_t i, psfm_tune_entry* out);
+psfm_status psfm_tune_set(const psfm_tune_entry* e);
+void psfm_tune_clear(void);
 
 /* FP32 FMA throughput probe (no counterpart in the paper: it measures the FP32 peak that the
  * image and variance kernels are compared with).  Launches n_blocks blocks of 256 threads, each

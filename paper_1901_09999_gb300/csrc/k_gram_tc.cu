@@ -345,6 +345,399 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(Src src, int n_tile) {
   src.finish(tid, kTcThreads);
 }
 
+// ---- Tensor-core Gram with error-free split products (precision mode BF16X6) ----
+//
+// Each augmented column c of the stamp (the zero-sum design columns in double-float, R, 1,
+// I2) and each weighted column w * c is scaled by a power of two so that its largest value is
+// below 1/4 and written as seven signed base-256 digits, x = sum_k d_k 2^(-8(k+1)),
+// |d_k| <= 129, each digit times its weight held exactly by a BF16 slice: 56 bits below the
+// column's largest value, enough for the 48 bits of a double-float value a hundred times
+// smaller.  The product of slices i and j is exact in the tensor cores and has the weight
+// 2^(-8(i+j+2)) of its level L = i + j.  Levels 0..3 are accumulated in their own tensor-memory
+// tiles over groups of 256 pixels, where every partial sum is an integer below 2^24 units of the
+// level and so exact in FP32; after each group they are read back and added, as integers, into
+// a 64-bit accumulator per Gram entry.  Levels 4..6 (weights 2^-48 .. 2^-64) share one FP32 tile
+// over the whole stamp.  The Gram entry is the integer sum plus the small levels, times the two
+// column scales: it carries the bits of its double-float inputs while the products run on the
+// tensor cores.  One CTA per stamp, four threads per Gram column (each thread reads 32 columns
+// of one accumulator lane back); at most 64 columns (one N = 64 tile).
+constexpr int kOzSlices = 7;
+constexpr int kOzExact = 4;  // levels summed exactly per group
+constexpr int kOzGroup = 8;  // 32-pixel sub-chunks per exact group (256 pixels)
+
+// seven balanced base-256 digits of the double-float h + l (|h + l| < 1/4), as BF16 bits of
+// d_k 2^(-8(k+1))
+__device__ __forceinline__ void oz_digits(float h, float l, uint16_t out[kOzSlices]) {
+#pragma unroll
+  for (int k = 0; k < kOzSlices; ++k) {
+    const float sc = __int_as_float((127 + 8 * (k + 1)) << 23);   // 2^(8(k+1))
+    const float isc = __int_as_float((127 - 8 * (k + 1)) << 23);  // 2^(-8(k+1))
+    const float d = rintf(h * sc);
+    const float dv = d * isc;  // exact: |d| <= 129
+    out[k] = bf16_bits(dv);
+    const float r = h - dv;  // exact (d is the nearest integer to h * sc)
+    // renormalise (r, l) with the error-free sum
+    const float s2 = r + l;
+    const float bb = s2 - r;
+    l = (r - (s2 - bb)) + (l - bb);
+    h = s2;
+  }
+}
+
+// Column source of the split Gram inside the solve: double-float design block (zero-sum
+// columns formed per pixel), R, 1, I2; weights 1 / (V1 + V2) as double-floats.  prepare()
+// stages the stamp's per-pixel weights and image values and the per-column psi_k and s_k in
+// shared memory once, so that the two passes over the stamp read only the design block.
+struct OzStampSource {
+  StampParams P;
+  int r, cx, cy;
+  float *wh, *wl, *xr, *xi, *ph, *pl, *sh, *sl;  // shared memory, set by prepare()
+  __device__ bool open(int blk) {
+    r = blk;
+    if (P.st->error || P.st->done) return false;
+    if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return false;
+    return P.have[r] != P.ptr[r];
+  }
+  __device__ int ncols() const { return P.Nc; }
+  __device__ int npix() const { return P.P; }
+  __host__ __device__ static size_t prep_floats(int npix, int nd) {
+    return 4 * (size_t)npix + 4 * (size_t)nd;
+  }
+  __device__ void bind(float* sm) {
+    const int n = P.P, nd = P.Nd;
+    wh = sm;
+    wl = wh + n;
+    xr = wl + n;
+    xi = xr + n;
+    ph = xi + n;
+    pl = ph + nd;
+    sh = pl + nd;
+    sl = sh + nd;
+  }
+  __device__ void prepare(int tid, int nthr) {
+    for (int pix = tid; pix < P.P; pix += nthr) {
+      const int py = pix / P.sw, px = pix - py * P.sw;
+      const int gx = cx - P.s + px, gy = cy - P.s + py;
+      float a = 0.f, b = 0.f, h = 0.f, l = 0.f;
+      if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
+        const int64_t o = (int64_t)gy * P.g.pitch + gx;
+        a = (P.m1[o] & P.badmask) ? 0.f : P.i1[o];
+        b = P.i2[o];
+        if (!((P.m1[o] | P.m2[o]) & P.badmask)) {
+          const double wd = 1.0 / ((double)P.v1[o] + (double)P.v2[o]);
+          if (!isfinite(P.i1[o]) || !isfinite(b) || !isfinite(wd))
+            raise_error(P.st, PSFM_ERR_NONFINITE);
+          h = (float)wd;
+          l = (float)(wd - (double)h);
+        }
+      }
+      xr[pix] = a;
+      xi[pix] = b;
+      wh[pix] = h;
+      wl[pix] = l;
+    }
+    const int nbk = P.b.Nb;
+    for (int c = tid; c < P.Nd; c += nthr) {
+      const int k = c < nbk ? c : c - nbk;
+      const double psd = P.psi[k], skd = P.sk[k];
+      ph[c] = (float)psd;
+      pl[c] = (float)(psd - (double)ph[c]);
+      sh[c] = (float)skd;
+      sl[c] = (float)(skd - (double)sh[c]);
+    }
+  }
+  __device__ void weight(int pix, float* h, float* l) const {
+    *h = pix < P.P ? wh[pix] : 0.f;
+    *l = pix < P.P ? wl[pix] : 0.f;
+  }
+  __device__ void value(int c, int pix, float* vh, float* vl) const {
+    *vh = 0.f;
+    *vl = 0.f;
+    if (pix >= P.P || c >= P.Nc) return;
+    const int Nd = P.Nd, nbk = P.b.Nb;
+    if (c < Nd) {
+      const float2 cv = reinterpret_cast<const float2*>(P.C)[((int64_t)r * Nd + c) * P.P + pix];
+      // psi C - s X in double-float, X = masked R (or I2 for the dual kernel's terms)
+      const float pa = ph[c], pb = pl[c];
+      float h = __fmul_rn(pa, cv.x);
+      float e = __fmaf_rn(pa, cv.x, -h);
+      e = __fmaf_rn(pa, cv.y, e);
+      e = __fmaf_rn(pb, cv.x, e);
+      const float sa = sh[c];
+      if (sa != 0.f) {
+        const float x = c < nbk ? xr[pix] : xi[pix], sb = sl[c];
+        const float q = __fmul_rn(sa, x);
+        const float qe = __fmaf_rn(sb, x, __fmaf_rn(sa, x, -q));
+        const float s2 = __fsub_rn(h, q);
+        const float bb = __fsub_rn(s2, h);
+        const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s2, bb)), __fsub_rn(-q, bb));
+        h = s2;
+        e = __fadd_rn(e, __fsub_rn(err, qe));
+      }
+      const float s2 = __fadd_rn(h, e);
+      *vh = s2;
+      *vl = __fsub_rn(e, __fsub_rn(s2, h));
+      return;
+    }
+    if (c == Nd) *vh = xr[pix];
+    else if (c == Nd + 1) *vh = 1.f;
+    else *vh = xi[pix];
+  }
+  __device__ double* gram() const { return P.Gt + (int64_t)r * P.Nc * P.Nc; }
+  __device__ void fail(int code) const { atomicCAS(&P.st->error, 0, code); }
+  __device__ void finish(int tid) const {
+    if (tid == 0) {
+      P.have[r] = P.ptr[r];
+      P.fresh[r] = 1;
+    }
+  }
+};
+
+// Column source of psfm_gram in the split mode: caller FP32 columns and weights (exact).
+struct OzPlainSource {
+  const float* cols;
+  const float* w;
+  double* G;
+  int32_t* status;
+  int n_cols, n_pix, r;
+  __device__ bool open(int blk) {
+    r = blk;
+    return true;
+  }
+  __device__ int ncols() const { return n_cols; }
+  __device__ int npix() const { return n_pix; }
+  __host__ __device__ static size_t prep_floats(int, int) { return 0; }
+  __device__ void bind(float*) {}
+  __device__ void prepare(int, int) {}
+  __device__ void weight(int pix, float* wh, float* wl) const {
+    *wh = pix < n_pix ? w[(int64_t)r * n_pix + pix] : 0.f;
+    *wl = 0.f;
+  }
+  __device__ void value(int c, int pix, float* vh, float* vl) const {
+    *vh = (pix < n_pix && c < n_cols) ? cols[((int64_t)r * n_cols + c) * n_pix + pix] : 0.f;
+    *vl = 0.f;
+  }
+  __device__ double* gram() const { return G + (int64_t)r * n_cols * n_cols; }
+  __device__ void fail(int code) const { atomicCAS(status, 0, code); }
+  __device__ void finish(int) const {}
+};
+
+// (h, l) * (a, b) in double-float
+__device__ __forceinline__ void oz_mul(float h, float l, float a, float b, float* rh, float* rl) {
+  const float p = __fmul_rn(h, a);
+  float e = __fmaf_rn(h, a, -p);
+  e = __fmaf_rn(h, b, e);
+  e = __fmaf_rn(l, a, e);
+  const float s2 = __fadd_rn(p, e);
+  *rh = s2;
+  *rl = __fsub_rn(e, __fsub_rn(s2, p));
+}
+
+// Power-of-two scale putting max |x| below 1/4 (2^-e with e = ilogb(max) + 3), as the exponent.
+__device__ __forceinline__ int oz_exponent(float m) {
+  if (!(m > 0.f) || !isfinite(m)) return 0;
+  return ilogbf(m) + 3;
+}
+
+template <class Src>
+__global__ void __launch_bounds__(512, 1) k_gram_oz(Src src, int n_tile) {
+  constexpr int ESZ = 2;
+  extern __shared__ __align__(1024) unsigned char tc_sh[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ unsigned int s_maxa[kTcM], s_maxb[kTcM];
+  __shared__ int s_ea[kTcM], s_eb[kTcM];
+  __shared__ float s_wh[kTcKC], s_wl[kTcKC];
+  __shared__ int s_ok, s_last, s_open;
+  const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) s_open = src.open(blockIdx.x) ? 1 : 0;
+  __syncthreads();
+  if (!s_open) return;
+  if (tid != 0) src.open(blockIdx.x);
+  const int Nc = src.ncols(), npix = src.npix();
+  const uint32_t a_bytes = kTcM * kTcKC * ESZ, b_bytes = (uint32_t)n_tile * kTcKC * ESZ;
+  const uint32_t stage_bytes = kOzSlices * (a_bytes + b_bytes);
+  auto a_plane = [&](int s, int k) { return tc_sh + s * stage_bytes + k * a_bytes; };
+  auto b_plane = [&](int s, int k) {
+    return tc_sh + s * stage_bytes + kOzSlices * a_bytes + k * b_bytes;
+  };
+  // ---- column scales: the largest |value| and |weight * value| of every column (FP32 estimates)
+  for (int c = tid; c < kTcM; c += nthr) {
+    s_maxa[c] = 0u;
+    s_maxb[c] = 0u;
+  }
+  for (uint32_t i = tid; i < 2 * stage_bytes / 4; i += nthr)
+    reinterpret_cast<uint32_t*>(tc_sh)[i] = 0u;  // rows >= Nc stay zero throughout
+  src.bind(reinterpret_cast<float*>(tc_sh + 2 * stage_bytes));
+  src.prepare(tid, nthr);
+  __syncthreads();
+  for (int i = tid; i < Nc * npix; i += nthr) {
+    const int c = i / npix, pix = i - c * npix;
+    float vh, vl, wh, wl;
+    src.value(c, pix, &vh, &vl);
+    src.weight(pix, &wh, &wl);
+    const float a = fabsf(vh), b = fabsf(vh * wh);
+    if (a > 0.f) atomicMax(&s_maxa[c], __float_as_uint(a));
+    if (b > 0.f) atomicMax(&s_maxb[c], __float_as_uint(b));
+  }
+  __syncthreads();
+  for (int c = tid; c < kTcM; c += nthr) {
+    s_ea[c] = oz_exponent(__uint_as_float(s_maxa[c]));
+    s_eb[c] = oz_exponent(__uint_as_float(s_maxb[c]));
+  }
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_ok = 1;
+    s_last = -1;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  // tensor-memory columns: exact level L at L n_tile, the small levels at 4 n_tile
+  const uint32_t rest_col = (uint32_t)(kOzExact * n_tile);
+  const uint32_t idesc = instr_desc(1u, n_tile, kTcM);
+  const uint32_t sbo = (kTcKC * ESZ / 16) * 128;
+  const int nsub = (npix + kTcKC - 1) / kTcKC;
+  // Gram readback: thread = (lane quadrant, 32-column slice)
+  const int quad = warp & 3, cslice = warp >> 2;
+  const int row = quad * 32 + lane, col0 = cslice * 32;
+  long long acc[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) acc[j] = 0;
+  for (int ch = 0; ch < nsub; ++ch) {
+    const int s = ch & 1;
+    const int grp = ch / kOzGroup, q = ch - grp * kOzGroup;
+    if (ch >= 2 && !mbar_wait(&bars[s], ((ch - 2) >> 1) & 1) && tid == 0) s_ok = 0;
+    __syncthreads();
+    if (!s_ok) break;
+    const int base = ch * kTcKC;
+    if (tid < kTcKC) src.weight(base + tid, &s_wh[tid], &s_wl[tid]);
+    __syncthreads();
+    for (int i = tid; i < Nc * kTcKC; i += nthr) {
+      const int c = i / kTcKC, j = i - c * kTcKC;
+      float vh, vl, bh, bl;
+      src.value(c, base + j, &vh, &vl);
+      oz_mul(vh, vl, s_wh[j], s_wl[j], &bh, &bl);
+      const float sa = __int_as_float((127 - s_ea[c]) << 23);
+      const float sb = __int_as_float((127 - s_eb[c]) << 23);
+      uint16_t da[kOzSlices], db[kOzSlices];
+      oz_digits(vh * sa, vl * sa, da);
+      oz_digits(bh * sb, bl * sb, db);
+      const uint32_t off = tile_off<ESZ>(c, j);
+#pragma unroll
+      for (int k = 0; k < kOzSlices; ++k) {
+        *reinterpret_cast<uint16_t*>(a_plane(s, k) + off) = da[k];
+        *reinterpret_cast<uint16_t*>(b_plane(s, k) + off) = db[k];
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      for (int k0 = 0; k0 < kTcKC; k0 += 16) {
+        const uint32_t koff = (uint32_t)(k0 / 8) * 128;
+#pragma unroll
+        for (int i = 0; i < kOzSlices; ++i) {
+          const uint64_t ad = smem_desc(smem_u32(a_plane(s, i)) + koff, 128, sbo);
+#pragma unroll
+          for (int j = 0; i + j < kOzSlices; ++j) {
+            const uint64_t bd = smem_desc(smem_u32(b_plane(s, j)) + koff, 128, sbo);
+            const int L = i + j;
+            uint32_t dst, accf;
+            if (L < kOzExact) {
+              dst = tmem + (uint32_t)(L * n_tile);
+              accf = (q == 0 && k0 == 0 && i == 0) ? 0u : 1u;
+            } else {
+              dst = tmem + rest_col;
+              accf = (ch == 0 && k0 == 0 && i == 0 && j == kOzExact) ? 0u : 1u;
+            }
+            tc_mma<1>(dst, ad, bd, idesc, accf);
+          }
+        }
+      }
+      tc_commit(&bars[s]);
+      s_last = ch;
+    }
+    if (q == kOzGroup - 1 || ch == nsub - 1) {
+      // the group's exact levels: wait for its MMAs, read them back, add them as integers (the
+      // next group's first MMAs overwrite the tiles only after the barrier below)
+      __syncthreads();
+      if (!mbar_wait(&bars[s], (ch >> 1) & 1) && tid == 0) s_ok = 0;
+      __syncthreads();
+      if (!s_ok) break;
+      tc_fence_after();
+      if (row < kTcM) {
+        const uint32_t lanebase = ((uint32_t)(quad * 32)) << 16;
+#pragma unroll
+        for (int L = 0; L < kOzExact; ++L) {
+          const uint32_t cb = (uint32_t)(L * n_tile + col0);
+          float v0[16], v1[16];
+          tc_ld16(tmem + lanebase + cb, v0);
+          tc_ld16(tmem + lanebase + cb + 16, v1);
+          const float up = __int_as_float((127 + 8 * (L + 2)) << 23);  // 2^(8(L+2))
+          const int sh = 8 * (kOzExact - 1 - L);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            acc[j] += (long long)__float2int_rn(v0[j] * up) << sh;
+            acc[j + 16] += (long long)__float2int_rn(v1[j] * up) << sh;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  // drain: every MMA issued is complete before the tensor memory is read or freed
+  const int last = s_last;
+  const bool drained = last < 0 || mbar_wait(&bars[last & 1], (last >> 1) & 1);
+  __syncthreads();
+  if (!drained && tid == 0) s_ok = 0;
+  __syncthreads();
+  tc_fence_after();
+  const bool ok = s_ok != 0 && last == nsub - 1;
+  if (ok) {
+    float rv0[16], rv1[16];
+    const uint32_t lanebase = ((uint32_t)(quad * 32)) << 16;
+    tc_ld16(tmem + lanebase + rest_col + col0, rv0);
+    tc_ld16(tmem + lanebase + rest_col + col0 + 16, rv1);
+    double* Gr = src.gram();
+    if (row < Nc) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int d = col0 + j;
+        if (d <= row && d < Nc) {
+          const double small = (double)(j < 16 ? rv0[j] : rv1[j - 16]);
+          const double g = ldexp((double)acc[j] * 0x1p-40 + small, s_ea[row] + s_eb[d]);
+          Gr[row * Nc + d] = g;
+          Gr[d * Nc + row] = g;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  if (!ok) {
+    if (tid == 0) src.fail(PSFM_ERR_TIMEOUT);
+    return;
+  }
+  __syncthreads();
+  src.finish(tid);
+}
+
 }  // namespace
 
 size_t gram_tc_smem(int mode, int n_tile) {
@@ -369,6 +762,42 @@ cudaError_t launch_gram_tc_src(int mode, const Src& src, int nblk, int n_cols, c
     k_gram_tc<1, Src><<<nblk, kTcThreads, smem, s>>>(src, n_tile);
   }
   return cudaGetLastError();
+}
+
+size_t gram_oz_smem(int n_tile) {
+  return 2 * (size_t)kOzSlices * (kTcM + n_tile) * kTcKC * 2;
+}
+
+template <class Src>
+cudaError_t launch_gram_oz_src(const Src& src, int nblk, int n_cols, int n_pix, int n_d,
+                               cudaStream_t s) {
+  if (n_cols > 64) return cudaErrorInvalidValue;
+  const int n_tile = 64;
+  const size_t smem = gram_oz_smem(n_tile) + sizeof(float) * Src::prep_floats(n_pix, n_d);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_gram_oz<Src>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_gram_oz<Src><<<nblk, 4 * n_tile, smem, s>>>(src, n_tile);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_oz(const StampParams& sp, int nreg, cudaStream_t s) {
+  OzStampSource src;
+  src.P = sp;
+  return launch_gram_oz_src(src, nreg, sp.Nc, sp.P, sp.Nd, s);
+}
+
+cudaError_t launch_gram_oz_plain(const float* cols, const float* w, int n_blocks, int n_cols,
+                                 int n_pix, double* G, int32_t* status, cudaStream_t s) {
+  OzPlainSource src;
+  src.cols = cols;
+  src.w = w;
+  src.G = G;
+  src.status = status;
+  src.n_cols = n_cols;
+  src.n_pix = n_pix;
+  return launch_gram_oz_src(src, n_blocks, n_cols, n_pix, 0, s);
 }
 
 cudaError_t launch_gram_tc(int mode, const StampParams& sp, int nreg, cudaStream_t s) {
@@ -430,16 +859,21 @@ extern "C" psfm_status psfm_gram(int32_t n_blocks, int32_t n_cols, int32_t n_pix
     psfm::k_gram_fp64<<<grid, 256, 0, s>>>(cols, weights, n_cols, n_pix, gram);
     return cudaGetLastError() == cudaSuccess ? PSFM_OK : PSFM_ERR_CUDA;
   }
-  if (precision != PSFM_PREC_TF32 && precision != PSFM_PREC_BF16X3) return PSFM_ERR_UNSUPPORTED;
-  if (n_cols > 128) return PSFM_ERR_UNSUPPORTED;
+  if (precision != PSFM_PREC_TF32 && precision != PSFM_PREC_BF16X3 &&
+      precision != PSFM_PREC_BF16X6)
+    return PSFM_ERR_UNSUPPORTED;
+  if (n_cols > (precision == PSFM_PREC_BF16X6 ? 64 : 128)) return PSFM_ERR_UNSUPPORTED;
   if (!workspace || ws_bytes < PSFM_GRAM_WORKSPACE ||
       (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
     return PSFM_ERR_WORKSPACE;
   int32_t* status = static_cast<int32_t*>(workspace);
   if (cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) return PSFM_ERR_CUDA;
-  if (psfm::launch_gram_tc_plain(precision == PSFM_PREC_TF32 ? 0 : 1, cols, weights, n_blocks,
-                                 n_cols, n_pix, gram, status, s) != cudaSuccess)
-    return PSFM_ERR_CUDA;
+  const cudaError_t e =
+      precision == PSFM_PREC_BF16X6
+          ? psfm::launch_gram_oz_plain(cols, weights, n_blocks, n_cols, n_pix, gram, status, s)
+          : psfm::launch_gram_tc_plain(precision == PSFM_PREC_TF32 ? 0 : 1, cols, weights,
+                                       n_blocks, n_cols, n_pix, gram, status, s);
+  if (e != cudaSuccess) return PSFM_ERR_CUDA;
   int32_t h = 0;
   if (cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)

@@ -28,6 +28,7 @@
 namespace psfm {
 
 cudaError_t launch_gram_tc(int mode, const StampParams& sp, int nreg, cudaStream_t s);
+cudaError_t launch_gram_oz(const StampParams& sp, int nreg, cudaStream_t s);
 
 namespace {
 
@@ -1868,7 +1869,7 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   size_t sm_design = esz * ((size_t)p.foot * p.foot + (size_t)p.foot * p.sw);
   const int nblk = (p.Nc + 3) / 4, npair = nblk * (nblk + 1) / 2;
   size_t sm_gram = sizeof(double) * npair * 16 + esz * (nblk * 4 * 32 + 32);
-  if (prec == PSFM_PREC_F32X2) {
+  if (prec == PSFM_PREC_F32X2 || prec == PSFM_PREC_BF16X6) {
     sm_design = sizeof(float) * ((size_t)p.foot * p.foot + 2 * (size_t)p.foot * p.sw +
                                  2 * (size_t)(p.dmax + 1) * p.w);
     const int maxch = ((p.P + kGramChunk - 1) / kGramChunk + kGramSplit - 1) / kGramSplit;
@@ -1877,13 +1878,15 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   }
   if (sm_design > 200 * 1024 || sm_gram > 200 * 1024) return PSFM_ERR_UNSUPPORTED;
   // TF32 / BF16X3: FP32 design blocks, the Gram on the tensor cores (k_gram_tc.cu)
+  // BF16X6: double-float design blocks, the Gram on the tensor cores from exact split products
   const bool tcm = prec == PSFM_PREC_TF32 || prec == PSFM_PREC_BF16X3;
+  const bool ozm = prec == PSFM_PREC_BF16X6;
+  const bool dfm = prec == PSFM_PREC_F32X2 || ozm;
   auto design = prec == PSFM_PREC_FP64 ? k_stamp_design<double>
-                : prec == PSFM_PREC_F32X2 ? k_stamp_design_df : k_stamp_design<float>;
+                : dfm ? k_stamp_design_df : k_stamp_design<float>;
   auto gram = prec == PSFM_PREC_FP64 ? k_stamp_gram<double>
-              : prec == PSFM_PREC_F32X2 ? k_stamp_gram_df : k_stamp_gram<float>;
-  auto chi2 = prec == PSFM_PREC_FP64 ? k_chi2<double>
-              : prec == PSFM_PREC_F32X2 ? k_chi2<float2> : k_chi2<float>;
+              : dfm ? k_stamp_gram_df : k_stamp_gram<float>;
+  auto chi2 = prec == PSFM_PREC_FP64 ? k_chi2<double> : dfm ? k_chi2<float2> : k_chi2<float>;
   if (cudaFuncSetAttribute(design, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_design) !=
           cudaSuccess ||
       cudaFuncSetAttribute(gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_gram) !=
@@ -1912,13 +1915,14 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
       cudaMemsetAsync(b.gram_count, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess ||
       cudaMemsetAsync(b.pdiag, 0, sizeof(double) * p.Nsys, s) != cudaSuccess)
     return PSFM_ERR_CUDA;
-  const bool dfm = prec == PSFM_PREC_F32X2;
   for (int it = 0; it < p.cfg.max_iter; ++it) {
     prof_begin("stamps", s);
     design<<<dim3(p.nreg, dfm ? p.NH * (p.cfg.dual ? 2 : 1) : p.ng), 256, sm_design, s>>>(sp);
     if (tcm) {
       if (launch_gram_tc(prec == PSFM_PREC_TF32 ? 0 : 1, sp, p.nreg, s) != cudaSuccess)
         return PSFM_ERR_CUDA;
+    } else if (ozm) {
+      if (launch_gram_oz(sp, p.nreg, s) != cudaSuccess) return PSFM_ERR_CUDA;
     } else {
       gram<<<dim3(p.nreg, dfm ? kGramSplit : 1), dfm ? kGramThreads : 256, sm_gram, s>>>(sp);
     }

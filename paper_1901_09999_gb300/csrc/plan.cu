@@ -131,7 +131,7 @@ psfm_status make_plan(Plan& p, psfm_shape shape, const psfm_basis_spec* b, const
   if (c->dual && c->precision != PSFM_PREC_F32X2) return PSFM_ERR_UNSUPPORTED;
   if (c->precision != PSFM_PREC_FP64 && c->precision != PSFM_PREC_FP32 &&
       c->precision != PSFM_PREC_F32X2 && c->precision != PSFM_PREC_TF32 &&
-      c->precision != PSFM_PREC_BF16X3)
+      c->precision != PSFM_PREC_BF16X3 && c->precision != PSFM_PREC_BF16X6)
     return PSFM_ERR_BAD_ARG;
   if (!(c->thresh_nsigma >= 0.0) || !(c->reject_nsigma > 0.0) || !(c->soften_alpha >= 0.0) ||
       !(c->bad_frac >= 0.0 && c->bad_frac <= 1.0))
@@ -155,6 +155,9 @@ psfm_status make_plan(Plan& p, psfm_shape shape, const psfm_basis_spec* b, const
   // the tensor-core Gram holds the augmented block in one 128-lane accumulator tile
   if ((c->precision == PSFM_PREC_TF32 || c->precision == PSFM_PREC_BF16X3) && p.Nc > 128)
     return PSFM_ERR_UNSUPPORTED;
+  // the split-product Gram holds its four exact levels and the small ones in tensor memory for
+  // one N = 64 tile
+  if (c->precision == PSFM_PREC_BF16X6 && p.Nc > 64) return PSFM_ERR_UNSUPPORTED;
   return PSFM_OK;
 }
 

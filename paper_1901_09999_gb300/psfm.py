@@ -24,7 +24,7 @@ STATUS = {0: "OK", 1: "BAD_ARG", 2: "TOO_FEW_STAMPS", 3: "SINGULAR", 4: "NONFINI
           6: "TIMEOUT", 8: "WORKSPACE", 9: "UNSUPPORTED"}
 OP_SOLVE, OP_CONVOLVE, OP_SUBTRACT, OP_STACK = 1, 2, 3, 4
 NORM_SEPARATE, NORM_JOINT = 0, 1
-PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16X3, PREC_F32X2 = 0, 1, 2, 3, 4
+PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16X3, PREC_F32X2, PREC_BF16X6 = 0, 1, 2, 3, 4, 5
 CAND_UNUSED, CAND_USED, CAND_REJECTED = 0, 1, 2
 (QUALITY_FEW_STAMPS, QUALITY_MEAN_DEV, QUALITY_RMS_DEV, QUALITY_MOMENT1, QUALITY_MOMENT2,
  QUALITY_DECONV) = 1, 2, 4, 8, 16, 32
@@ -563,6 +563,111 @@ def psfm_gram(cols, weights, precision, stream=None):
     if st != PSFM_OK:
         raise PsfmError(st, "psfm_gram")
     return G
+
+
+class psfm_tune_entry(C.Structure):
+    _fields_ = [("half_width", C.c_int32), ("spatial_order", C.c_int32), ("n_gauss", C.c_int32),
+                ("degree", C.c_int32 * MAX_GAUSS), ("tile_rows", C.c_int32),
+                ("plane_chunk", C.c_int32), ("ms", C.c_float)]
+
+
+def _tune_types(lib):
+    P_, i32 = C.POINTER, C.c_int32
+    lib.psfm_tune_conv_workspace_size.argtypes = [i32, i32, P_(psfm_basis_spec)]
+    lib.psfm_tune_conv_workspace_size.restype = C.c_size_t
+    lib.psfm_tune_conv.argtypes = [i32, i32, P_(psfm_basis_spec), C.c_void_p, C.c_size_t,
+                                   C.c_void_p, P_(psfm_tune_entry)]
+    lib.psfm_tune_conv.restype = i32
+    lib.psfm_tune_count.argtypes = []
+    lib.psfm_tune_count.restype = i32
+    lib.psfm_tune_get.argtypes = [i32, P_(psfm_tune_entry)]
+    lib.psfm_tune_get.restype = i32
+    lib.psfm_tune_set.argtypes = [P_(psfm_tune_entry)]
+    lib.psfm_tune_set.restype = i32
+    lib.psfm_tune_clear.argtypes = []
+    lib.psfm_tune_clear.restype = None
+
+
+def _entry_dict(e: psfm_tune_entry) -> dict:
+    return {"half_width": e.half_width, "spatial_order": e.spatial_order, "n_gauss": e.n_gauss,
+            "degree": list(e.degree)[:e.n_gauss], "tile_rows": e.tile_rows,
+            "plane_chunk": e.plane_chunk, "ms": float(e.ms)}
+
+
+def tune_conv(basis, width, height, stream=None) -> dict:
+    """Autotune the image convolution's launch shape for the class of ``basis`` on a synthetic
+    width x height image (C: psfm_tune_conv); the choice goes into the library's table and is
+    returned as a dict."""
+    torch = _torch()
+    lib = load()
+    _tune_types(lib)
+    need = int(lib.psfm_tune_conv_workspace_size(int(width), int(height), C.byref(basis)))
+    if need == 0:
+        raise PsfmError(1, "psfm_tune_conv_workspace_size")
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    e = psfm_tune_entry()
+    st = lib.psfm_tune_conv(int(width), int(height), C.byref(basis), _ptr(ws), need,
+                            _stream(stream), C.byref(e))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_tune_conv")
+    return _entry_dict(e)
+
+
+def tune_entries() -> list:
+    """The library's tuning table as a list of dicts (C: psfm_tune_get)."""
+    lib = load()
+    _tune_types(lib)
+    out = []
+    for i in range(lib.psfm_tune_count()):
+        e = psfm_tune_entry()
+        if lib.psfm_tune_get(i, C.byref(e)) == PSFM_OK:
+            out.append(_entry_dict(e))
+    return out
+
+
+def tune_set(entry: dict):
+    """Adds or replaces one tuning-table entry (C: psfm_tune_set)."""
+    lib = load()
+    _tune_types(lib)
+    e = psfm_tune_entry()
+    e.half_width, e.spatial_order = int(entry["half_width"]), int(entry["spatial_order"])
+    deg = list(entry["degree"])
+    e.n_gauss = len(deg)
+    for g, d in enumerate(deg):
+        e.degree[g] = int(d)
+    e.tile_rows, e.plane_chunk = int(entry["tile_rows"]), int(entry["plane_chunk"])
+    e.ms = float(entry.get("ms", 0.0))
+    st = lib.psfm_tune_set(C.byref(e))
+    if st != PSFM_OK:
+        raise PsfmError(st, "psfm_tune_set")
+
+
+def tune_clear():
+    lib = load()
+    _tune_types(lib)
+    lib.psfm_tune_clear()
+
+
+def tune_save(path, device_name=""):
+    """Writes the tuning table to a JSON file (with the device it was measured on)."""
+    import json
+    with open(path, "w") as f:
+        json.dump({"version": 1, "device": device_name, "entries": tune_entries()}, f, indent=1)
+
+
+def tune_load(path, device_name=None) -> int:
+    """Loads tuning entries from a JSON file written by tune_save; entries measured on another
+    device are skipped when ``device_name`` is given.  Returns the number loaded."""
+    import json
+    with open(path) as f:
+        d = json.load(f)
+    if device_name is not None and d.get("device") not in ("", device_name):
+        return 0
+    n = 0
+    for e in d.get("entries", []):
+        tune_set(e)
+        n += 1
+    return n
 
 
 WAIT_LIMIT_DEFAULT = 1 << 24

@@ -77,3 +77,32 @@ def test_envelope_argument_errors_are_caught_on_the_host(lib):
                  ((4.0, 4.0, 0.0, 3.0), 65), ((40.0, 40.0, 0.0, 3.0), 0)):
         arr = (P.psfm_psf_model * 1)(P.psfm_psf_model(*m))
         assert lib.psfm_envelope_fwhm(1, arr, r, C.byref(out), fake_ws, 256, None) == 1
+
+
+def test_tuning_table_host_side(lib):
+    """The convolution tuning table: entries are set, replaced per basis class, read back,
+    persisted through JSON and cleared, all on the host; illegal shapes are rejected."""
+    import os
+    import tempfile
+    P.tune_clear()
+    e = {"half_width": 15, "spatial_order": 2, "degree": [6, 4, 2], "tile_rows": 64,
+         "plane_chunk": 4, "ms": 1.5}
+    P.tune_set(e)
+    P.tune_set(dict(e, half_width=10, tile_rows=128))
+    P.tune_set(dict(e, tile_rows=128, plane_chunk=0))   # replaces the first class
+    got = sorted(P.tune_entries(), key=lambda x: x["half_width"])
+    assert [(x["half_width"], x["tile_rows"], x["plane_chunk"]) for x in got] == \
+        [(10, 128, 4), (15, 128, 0)]
+    with pytest.raises(P.PsfmError):
+        P.tune_set(dict(e, tile_rows=32))
+    with pytest.raises(P.PsfmError):
+        P.tune_set(dict(e, plane_chunk=3))
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "tune.json")
+        P.tune_save(path, "dev")
+        P.tune_clear()
+        assert P.tune_entries() == []
+        assert P.tune_load(path, "other") == 0
+        assert P.tune_load(path, "dev") == 2
+    assert sorted(x["half_width"] for x in P.tune_entries()) == [10, 15]
+    P.tune_clear()

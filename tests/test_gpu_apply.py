@@ -119,3 +119,50 @@ def test_identity_kernel(dev):
     assert np.allclose(host(V_)[ok], f.var_ref[ok], rtol=1e-6)
     cc = cov.cpu().numpy()
     assert cc[cc.shape[0] // 2, cc.shape[0] // 2] == 1.0 and abs(cc.sum() - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("ty", [64, 128])
+@pytest.mark.parametrize("W,H,h,S,deg", [(157, 211, 7, 2, (3, 2, 1)), (96, 300, 15, 2, (8, 4)),
+                                         (70, 90, 24, 1, (6,)), (45, 260, 1, 3, (2,))])
+def test_every_launch_shape_matches_oracle(dev, ty, W, H, h, S, deg):
+    """Both tile heights the autotuner may choose (64 and 128 output rows), forced through the
+    tuning table, give the same image as the oracle on ragged sizes."""
+    f = synth.small_gaussian_field(W * H, size=H, width=W, n_stars=max(5, W * H // 1500),
+                                   bad_col_frac=0.02)
+    sig = (0.9, 1.8, 3.1)[:len(deg)]
+    b, c, ob, oc = specs(sig, deg, h, S, badmask=synth.BADMASK, cov_grid=3)
+    osol = _random_solution(ob, W, H, seed=H)
+    rb = O.r_bad(osol, oc.bad_frac)
+    t = upload(f, dev, pad=5)
+    P.tune_clear()
+    P.tune_set({"half_width": h, "spatial_order": S, "degree": list(deg), "tile_rows": ty,
+                "plane_chunk": 4})
+    try:
+        D, V, M, cov = P.psfm_convolve(t["ref"], t["var_ref"], t["mask_ref"], b, c,
+                                       gpu_solution_from_oracle(osol, rb), img=t["sci"],
+                                       var_img=t["var_sci"], mask_img=t["mask_sci"])
+    finally:
+        P.tune_clear()
+    _compare(f, osol, oc, D, V, M, cov)
+
+
+def test_autotuner_picks_a_legal_shape(dev):
+    """psfm_tune_conv times the legal shapes of a basis class and stores the fastest; the
+    convolution then runs with it and still matches the oracle."""
+    W, H = 400, 300
+    f = synth.small_gaussian_field(3, size=H, width=W, n_stars=100)
+    b, c, ob, oc = specs((0.8, 1.6, 3.2), (6, 4, 2), 15, 2, badmask=synth.BADMASK)
+    P.tune_clear()
+    e = P.tune_conv(b, W, H)
+    assert e["tile_rows"] in (64, 128) and e["plane_chunk"] == 4 and e["ms"] > 0
+    assert P.tune_entries() == [e]
+    osol = _random_solution(ob, W, H, seed=5)
+    rb = O.r_bad(osol, oc.bad_frac)
+    t = upload(f, dev)
+    try:
+        D, V, M, cov = P.psfm_convolve(t["ref"], t["var_ref"], t["mask_ref"], b, c,
+                                       gpu_solution_from_oracle(osol, rb), img=t["sci"],
+                                       var_img=t["var_sci"], mask_img=t["mask_sci"])
+    finally:
+        P.tune_clear()
+    _compare(f, osol, oc, D, V, M, cov)

@@ -179,8 +179,9 @@ def test_precision_study_full_chip(dev, chip):
     pts9 = [(x, y) for x in (0, W // 2, W - 1) for y in (0, H // 2, H - 1)]
     a_or = chip["osol"].a.ravel()
     rows = []
-    for name, prec in (("f32x2", P.PREC_F32X2), ("fp64", P.PREC_FP64), ("fp32", P.PREC_FP32),
-                       ("bf16x3", P.PREC_BF16X3), ("tf32", P.PREC_TF32)):
+    for name, prec in (("f32x2", P.PREC_F32X2), ("bf16x6", P.PREC_BF16X6),
+                       ("fp64", P.PREC_FP64), ("fp32", P.PREC_FP32), ("bf16x3", P.PREC_BF16X3),
+                       ("tf32", P.PREC_TF32)):
         b, c = _specs(g, prec)
         try:
             D, V, M, cov, sol = P.psfm_subtract(t["img"], t["ref"], t["var_img"], t["var_ref"],
@@ -197,8 +198,9 @@ def test_precision_study_full_chip(dev, chip):
         ratio = float(np.median(tr[:, 0] / tr[:, 2]))
         zrms = float(np.sqrt(np.mean(((tr[:, 0] - tr[:, 2]) / tr[:, 1]) ** 2)))
         rows.append((name, same, sol.n_used, ke, ce, de, ve, me, len(tr), ratio, zrms))
-        if prec in (P.PREC_F32X2, P.PREC_FP64):
+        if prec in (P.PREC_F32X2, P.PREC_FP64, P.PREC_BF16X6):
             assert same and ke <= KERNEL_RTOL and de <= IMG_TOL_SIGMA and ve <= VAR_RTOL
+            assert coeff_rel_err(sol.coeff[:a_or.size], a_or) <= COEFF_RTOL
         assert np.isfinite(ke) and np.isfinite(de)
     print("\nmode    stamps=oracle n_used kernel_L2  coeff_inf  D/sigma   V_rel    mask "
           "n_tr flux_ratio z_rms")

@@ -61,6 +61,25 @@ def test_gram_modes_within_rounding_bounds(dev, nc, npix):
     assert med[P.PREC_BF16X3] < 0.05 * med[P.PREC_TF32]
 
 
+@pytest.mark.parametrize("nc,npix", [(52, 961), (60, 441), (64, 70), (7, 33), (40, 600),
+                                     (64, 257)])
+def test_split_product_gram_is_exact_to_double_float(dev, nc, npix):
+    """BF16X6: seven BF16 slices per operand, products exact on the tensor cores, levels 0..3
+    summed exactly as integers over 256-pixel groups.  For FP32 columns and weights the
+    weighted column is an exact 48-bit product, so the Gram agrees with the FP64 one to a few
+    units of 2^-48 of its terms (against 2^-9 for TF32)."""
+    import torch
+    cols, w = _data(nc * 7 + npix, 3, nc, npix)
+    G, A = _reference(cols, w)
+    tc, tw = torch.from_numpy(cols).to(dev), torch.from_numpy(w).to(dev)
+    g = P.psfm_gram(tc, tw, P.PREC_BF16X6).cpu().numpy()
+    err = np.abs(g - G)
+    rel = float(np.max(err / np.where(A > 0, A, 1.0)))
+    print(f"nc={nc} npix={npix}: BF16X6 max |err| / sum|terms| {rel:.2e}")
+    assert rel <= 2.0 ** -40
+    assert np.array_equal(g, np.swapaxes(g, 1, 2))
+
+
 def test_gram_rejects_unsupported(dev):
     import torch
     cols, w = _data(5, 1, 130, 40)

@@ -19,8 +19,9 @@ KERNEL_RTOL = 1e-6
 B0_RTOL = 1e-9
 # Kernel coefficients (normwise relative): the tolerance the method is held to.
 COEFF_RTOL = 1e-6
-# The accurate solve modes: FP64, and double-float (FP32 pairs) on the FP32 pipes.
-PRECISIONS = [P.PREC_FP64, P.PREC_F32X2]
+# The accurate solve modes: FP64; double-float (FP32 pairs) on the FP32 pipes; double-float
+# design with the Gram on the tensor cores from exact BF16 split products.
+PRECISIONS = [P.PREC_FP64, P.PREC_F32X2, P.PREC_BF16X6]
 
 
 @pytest.fixture(scope="module")
