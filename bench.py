@@ -742,6 +742,13 @@ def main():
         pms = time_arm(lambda: batch32.run(stream), n3)
         batch32.close()
         del batch32
+        tms = None
+        if args.precision != "bf16x6":
+            _, cfgtc = chip_specs("bf16x6", args.small)
+            batchtc = P.Batch(chips, bases, cfgtc, n_streams=args.streams, want_cov=True)
+            tms = time_arm(lambda: batchtc.run(stream), n3)
+            batchtc.close()
+            del batchtc
         comparisons = {
             "unbatched_same_precision": {
                 "value": px_per_step / 1e6 / (ums / 1e3), "unit": "Mpix/s", "ms_per_step": ums,
@@ -753,6 +760,11 @@ def main():
                         "parity tolerances (FP32 normal equations; FP64 LU fallback)"},
             "batched_over_unbatched": ums / (ms / args.steps),
             "this_precision_over_plain_fp32": pms / (ms / args.steps)}
+        if tms is not None:
+            comparisons["batched_bf16x6_tensor_core_gram"] = {
+                "value": px_per_step / 1e6 / (tms / 1e3), "unit": "Mpix/s", "ms_per_step": tms,
+                "what": "same batch, stamp Gram on the tensor cores from exact BF16 split "
+                        "products (meets the parity tolerances)"}
 
     e2e = None
     if not args.no_e2e and not args.exposure:
@@ -770,7 +782,10 @@ def main():
                        for t in (b.diff[i], b.diff_var[i], b.diff_mask[i])]
                       for i in range(len(chips))] for _, b in sets]
             bo = sum(t.numel() * t.element_size() for hs in h_out[0] for t in hs)
-            copy = torch.cuda.Stream()
+            # host-to-device and device-to-host copies on streams of their own, so that the two
+            # directions of the link run at the same time
+            up = torch.cuda.Stream()
+            down = torch.cuda.Stream()
             ev_up = [torch.cuda.Event(), torch.cuda.Event()]
             ev_comp = [torch.cuda.Event(), torch.cuda.Event()]
             ev_down = [torch.cuda.Event(), torch.cuda.Event()]
@@ -779,31 +794,34 @@ def main():
                 for c, hs in zip(sets[si][0], h_in):
                     for k, hh in zip(keys, hs):
                         c[k].copy_(hh, non_blocking=True)
-                ev_up[si].record(copy)
+                ev_up[si].record(up)
 
             def download(si):
                 b = sets[si][1]
                 for i, hs in enumerate(h_out[si]):
                     for hh, d in zip(hs, (b.diff[i], b.diff_var[i], b.diff_mask[i])):
                         hh.copy_(d, non_blocking=True)
-                ev_down[si].record(copy)
+                ev_down[si].record(down)
 
             def e2e_run(n, start_event=None):
-                with torch.cuda.stream(copy):
+                with torch.cuda.stream(up):
                     if start_event is not None:
-                        copy.wait_event(start_event)
+                        up.wait_event(start_event)
                     upload(0)
                 for k in range(n):
                     si = k % 2
                     stream.wait_event(ev_up[si])
+                    if k >= 2:  # this set's outputs of two steps ago have been read back
+                        stream.wait_event(ev_down[si])
                     sets[si][1].run(stream)
                     ev_comp[si].record(stream)
-                    with torch.cuda.stream(copy):
-                        if k + 1 < n:
-                            if k >= 1:
-                                copy.wait_event(ev_comp[1 - si])
+                    if k + 1 < n:
+                        with torch.cuda.stream(up):
+                            if k >= 1:  # the other set's inputs are free once its step is done
+                                up.wait_event(ev_comp[1 - si])
                             upload(1 - si)
-                        copy.wait_event(ev_comp[si])
+                    with torch.cuda.stream(down):
+                        down.wait_event(ev_comp[si])
                         download(si)
                 stream.wait_event(ev_down[(n - 1) % 2])
 
@@ -843,7 +861,8 @@ def main():
             e2e_ms = e0.elapsed_time(e1)
         e2e = {"value": px_per_step * n2 / 1e6 / (e2e_ms / 1e3), "unit": "Mpix/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
-               "overlap": "copies of one step overlap the compute of the next (two buffer sets)"
+               "overlap": "copies of one step overlap the compute of the next (two buffer sets; "
+                          "uploads and read-backs on separate streams)"
                           if batch is not None else "none"}
 
     # the batching and stacking workloads as sub-results of the same run (their own steps)

@@ -73,12 +73,28 @@ cudaError_t launch_conv_image(const Plan& p, const DevTables& t, const double* d
   return dispatch(p.h, P, st);
 }
 
+// Synthetic tuning images: a sky-like reference with a hashed texture, about 2 % of the pixels
+// masked, and a science image for the difference mode.
+__global__ void k_tune_fill(int W, int H, int64_t pitch, float* ref, float* img, uint16_t* mask) {
+  const int64_t n = (int64_t)H * pitch;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t v = (uint32_t)i * 2654435761u;
+    v ^= v >> 15;
+    v *= 2246822519u;
+    v ^= v >> 13;
+    ref[i] = 500.f + (float)(v & 1023);
+    img[i] = 510.f + (float)((v >> 10) & 1023);
+    mask[i] = (v >> 24) < 5 ? (uint16_t)1 : (uint16_t)0;
+  }
+}
+
 }  // namespace psfm
 
 namespace {
 
 struct TuneLayout {
-  size_t ref = 0, mask = 0, out = 0, dsol = 0, tab = 0, total = 0;
+  size_t ref = 0, img = 0, mask = 0, out = 0, dsol = 0, tab = 0, total = 0;
 };
 
 TuneLayout tune_layout(const psfm::Plan& p, size_t blob) {
@@ -86,7 +102,8 @@ TuneLayout tune_layout(const psfm::Plan& p, size_t blob) {
   TuneLayout L;
   const size_t npx = (size_t)p.H * p.pitch;
   L.ref = 0;
-  L.mask = al(L.ref + sizeof(float) * npx);
+  L.img = al(L.ref + sizeof(float) * npx);
+  L.mask = al(L.img + sizeof(float) * npx);
   L.out = al(L.mask + sizeof(uint16_t) * npx);
   L.dsol = al(L.out + sizeof(float) * npx);
   L.tab = al(L.dsol + sizeof(double) * (2 + p.ncoef));
@@ -129,15 +146,17 @@ psfm_status psfm_tune_conv(int32_t width, int32_t height, const psfm_basis_spec*
   if (ws_bytes < L.total) return PSFM_ERR_WORKSPACE;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* base = static_cast<char*>(workspace);
-  // a smooth synthetic reference (the kernel's time does not depend on the values), no mask,
-  // and a solution with every coefficient non-zero
+  // synthetic reference and science images with a few masked pixels (difference mode, as in
+  // a subtraction) and a solution with every coefficient non-zero
   std::vector<double> sol(2 + p.ncoef);
   sol[0] = 1.0;
   sol[1] = 0.5;
   for (int i = 0; i < p.ncoef; ++i) sol[2 + i] = 0.01 * ((i * 7919) % 13 - 6);
   const size_t npx = (size_t)p.H * p.pitch;
-  if (cudaMemsetAsync(base + L.ref, 0, sizeof(float) * npx, st) != cudaSuccess ||
-      cudaMemsetAsync(base + L.mask, 0, sizeof(uint16_t) * npx, st) != cudaSuccess ||
+  k_tune_fill<<<1024, 256, 0, st>>>(p.W, p.H, p.pitch, reinterpret_cast<float*>(base + L.ref),
+                                    reinterpret_cast<float*>(base + L.img),
+                                    reinterpret_cast<uint16_t*>(base + L.mask));
+  if (cudaGetLastError() != cudaSuccess ||
       cudaMemcpyAsync(base + L.dsol, sol.data(), sizeof(double) * sol.size(),
                       cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(base + L.tab, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) !=
@@ -147,7 +166,8 @@ psfm_status psfm_tune_conv(int32_t width, int32_t height, const psfm_basis_spec*
   const DevTables t = bind_tables(base + L.tab, offs);
   conv::ConvParams P = conv_params(p, t, reinterpret_cast<const double*>(base + L.dsol),
                                    reinterpret_cast<const float*>(base + L.ref),
-                                   reinterpret_cast<const uint16_t*>(base + L.mask), nullptr,
+                                   reinterpret_cast<const uint16_t*>(base + L.mask),
+                                   reinterpret_cast<const float*>(base + L.img),
                                    reinterpret_cast<float*>(base + L.out));
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return PSFM_ERR_CUDA;

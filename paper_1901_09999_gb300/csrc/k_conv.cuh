@@ -41,6 +41,7 @@ struct ConvParams {
   const double* dsol;
   float xscale, yscale;
   int ty;      // tile rows: 8 per warp of the CTA (64 or 128)
+  int nslots;  // horizontal planes held in shared memory at once (4..8)
   uint16_t badmask;
 };
 
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(4 * TY, TY == 64 ? 2 : 1) k_conv_image(ConvPar
   float* Rs = reinterpret_cast<float*>(smem4);
   float* Hs = Rs + RR * RS;
   constexpr int S = SS, S1 = SS + 1;
-  float* Wf = Hs + kMaxChunk * RR * TX;
+  float* Wf = Hs + P.nslots * RR * TX;
   float* alpha = Wf + P.b.ng * FG;
   float* beta = alpha + P.b.Nb * S1 * S1;
 
@@ -276,55 +277,72 @@ __global__ void __launch_bounds__(4 * TY, TY == 64 ? 2 : 1) k_conv_image(ConvPar
 #pragma unroll
   for (int i = 0; i < 8; ++i) out[i] = 0.f;
 
+  // One pass over the staged rows and one over the columns per group of planes: all planes of
+  // a Gaussian when they fit the plane slots (even degrees first, then odd), otherwise the
+  // planes of one parity four at a time.
   for (int g = 0; g < P.b.ng; ++g) {
     const int dg = P.b.deg[g];
     const float* wfg = Wf + g * FG;
-    for (int par = 0; par < 2; ++par) {
-      const int np = par == 0 ? dg / 2 + 1 : (dg + 1) / 2;  // planes of this parity
-      for (int c0 = 0; c0 < np; c0 += kMaxChunk) {
-        const int nc = min(kMaxChunk, np - c0);
-        const int n0 = par + 2 * c0;  // degree of the chunk's first plane
-        // ---- horizontal passes of the chunk's planes over the staged rows
-        for (int item = tid; item < RR * 8; item += NT) {
-          const int row = item >> 3, xg = item & 7;
-          float rv[4 * NV4];
-          const float4* src = reinterpret_cast<const float4*>(Rs + row * RS + xg * 4);
-#pragma unroll
-          for (int j = 0; j < NV4; ++j) {
-            const float4 t = src[j];
-            rv[4 * j] = t.x;
-            rv[4 * j + 1] = t.y;
-            rv[4 * j + 2] = t.z;
-            rv[4 * j + 3] = t.w;
-          }
-          float* hs = Hs + row * TX + xg * 4;
-          // chunks start at degree 0 or 8 (even) or 1 (odd): slot 0, 4 or 8, an aligned float4
-          if (par == 0) hfold_n<HW, 0>(nc, rv, wfg + fold_slot(n0), hs, RR * TX);
-          else hfold_n<HW, 1>(nc, rv, wfg + fold_slot(n0), hs, RR * TX);
-        }
-        __syncthreads();
-        // ---- vertical passes: each H value in registers serves 8 outputs and all q
-        for (int c = 0; c < nc; ++c) {
-          const int p = n0 + 2 * c;
-          float col[8 + 2 * HW];
-          const float* hp = Hs + (c * RR + wi * 8) * TX + lane;
-#pragma unroll
-          for (int t = 0; t < 8 + 2 * HW; ++t) col[t] = hp[t * TX];
-          const int kgp = P.b.kbase[g] + p * (dg + 1) - (p * (p - 1)) / 2;  // term (g, p, 0)
-          const int nq = dg - p + 1;
-          for (int q0 = 0; q0 < nq; q0 += 2 * MAXNE) {  // even q
-            const int ne = min(MAXNE, (nq - q0 + 1) / 2);
-            vfold_n<HW, SS, 0>(ne, col, wfg + fold_slot(q0), alpha + (kgp + q0) * S1 * S1, xt,
-                               yt, out);
-          }
-          for (int q0 = 1; q0 < nq; q0 += 2 * MAXNE) {  // odd q
-            const int ne = min(MAXNE, (nq - q0 + 1) / 2);
-            vfold_n<HW, SS, 1>(ne, col, wfg + fold_slot(q0), alpha + (kgp + q0) * S1 * S1, xt,
-                               yt, out);
-          }
-        }
-        __syncthreads();
+    const int ne_g = dg / 2 + 1, no_g = (dg + 1) / 2;  // planes of even / odd degree
+    const bool whole = ne_g + no_g <= P.nslots && ne_g <= kMaxChunk && no_g <= kMaxChunk;
+    for (int grp = 0; grp < (whole ? 1 : 2 * ((ne_g + kMaxChunk - 1) / kMaxChunk)); ++grp) {
+      // planes of this group: ce of even degree from e0, co of odd degree from o0
+      int ce, co, e0, o0;
+      if (whole) {
+        ce = ne_g;
+        co = no_g;
+        e0 = 0;
+        o0 = 1;
+      } else {
+        const int par = grp & 1, c0 = (grp >> 1) * kMaxChunk;
+        const int np = par == 0 ? ne_g : no_g;
+        const int nc = c0 < np ? min(kMaxChunk, np - c0) : 0;
+        ce = par == 0 ? nc : 0;
+        co = par == 1 ? nc : 0;
+        e0 = 2 * c0;
+        o0 = 1 + 2 * c0;
       }
+      if (ce + co == 0) continue;  // uniform over the CTA
+      // ---- horizontal passes of the group's planes over the staged rows; chunks start at
+      // degree 0 or 8 (even) or 1 (odd): slot 0, 4 or 8, an aligned float4
+      for (int item = tid; item < RR * 8; item += NT) {
+        const int row = item >> 3, xg = item & 7;
+        float rv[4 * NV4];
+        const float4* src = reinterpret_cast<const float4*>(Rs + row * RS + xg * 4);
+#pragma unroll
+        for (int j = 0; j < NV4; ++j) {
+          const float4 t = src[j];
+          rv[4 * j] = t.x;
+          rv[4 * j + 1] = t.y;
+          rv[4 * j + 2] = t.z;
+          rv[4 * j + 3] = t.w;
+        }
+        float* hs = Hs + row * TX + xg * 4;
+        if (ce) hfold_n<HW, 0>(ce, rv, wfg + fold_slot(e0), hs, RR * TX);
+        if (co) hfold_n<HW, 1>(co, rv, wfg + fold_slot(o0), hs + ce * RR * TX, RR * TX);
+      }
+      __syncthreads();
+      // ---- vertical passes: each H value in registers serves 8 outputs and all q
+      for (int c = 0; c < ce + co; ++c) {
+        const int p = c < ce ? e0 + 2 * c : o0 + 2 * (c - ce);
+        float col[8 + 2 * HW];
+        const float* hp = Hs + (c * RR + wi * 8) * TX + lane;
+#pragma unroll
+        for (int t = 0; t < 8 + 2 * HW; ++t) col[t] = hp[t * TX];
+        const int kgp = P.b.kbase[g] + p * (dg + 1) - (p * (p - 1)) / 2;  // term (g, p, 0)
+        const int nq = dg - p + 1;
+        for (int q0 = 0; q0 < nq; q0 += 2 * MAXNE) {  // even q
+          const int ne = min(MAXNE, (nq - q0 + 1) / 2);
+          vfold_n<HW, SS, 0>(ne, col, wfg + fold_slot(q0), alpha + (kgp + q0) * S1 * S1, xt, yt,
+                             out);
+        }
+        for (int q0 = 1; q0 < nq; q0 += 2 * MAXNE) {  // odd q
+          const int ne = min(MAXNE, (nq - q0 + 1) / 2);
+          vfold_n<HW, SS, 1>(ne, col, wfg + fold_slot(q0), alpha + (kgp + q0) * S1 * S1, xt, yt,
+                             out);
+        }
+      }
+      __syncthreads();
     }
   }
 
@@ -350,14 +368,13 @@ __global__ void __launch_bounds__(4 * TY, TY == 64 ? 2 : 1) k_conv_image(ConvPar
 constexpr size_t kConvSmemTwoCtas = 112 * 1024;
 constexpr size_t kConvSmemMax = 227 * 1024;
 
-// Shared memory of a CTA with tile height ty (four horizontal planes per chunk).
+// Shared memory of a CTA with tile height ty and ns plane slots.
 template <int HW>
-size_t conv_smem(const ConvParams& P, int ty) {
+size_t conv_smem(const ConvParams& P, int ty, int ns) {
   using CS = ConvShape<HW>;
   const int S1 = P.b.S + 1, RR = ty + 2 * HW;
   return sizeof(float) * ((size_t)RR * CS::RS + (size_t)P.b.ng * (HW + 1) * kFoldLd +
-                          (size_t)P.b.Nb * S1 * S1 + (size_t)S1 * S1 +
-                          (size_t)kMaxChunk * RR * kConvTX);
+                          (size_t)P.b.Nb * S1 * S1 + (size_t)S1 * S1 + (size_t)ns * RR * kConvTX);
 }
 
 template <int HW, int TY>
@@ -381,14 +398,22 @@ cudaError_t launch_ty(const ConvParams& P, size_t smem, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Launch with P.ty = 64 or 128 output rows per CTA.
+// Launch with P.ty = 64 or 128 output rows per CTA and as many plane slots (up to all planes
+// of the widest Gaussian, at least four) as keep the CTAs of that height resident together.
 template <int HW>
-cudaError_t launch_hw(const ConvParams& P, cudaStream_t st) {
-  const size_t smem = conv_smem<HW>(P, P.ty);
-  if (smem > (P.ty == 64 ? kConvSmemTwoCtas : kConvSmemMax)) return cudaErrorInvalidValue;
+cudaError_t launch_hw(ConvParams P, cudaStream_t st) {
+  if (P.ty != 64 && P.ty != 128) return cudaErrorInvalidValue;
+  const size_t budget = P.ty == 64 ? kConvSmemTwoCtas : kConvSmemMax;
+  int want = kMaxChunk;
+  for (int g = 0; g < P.b.ng; ++g) want = max(want, P.b.deg[g] + 1);
+  want = min(want, 2 * kMaxChunk);
+  int ns = want;
+  while (ns > kMaxChunk && conv_smem<HW>(P, P.ty, ns) > budget) --ns;
+  P.nslots = ns;
+  const size_t smem = conv_smem<HW>(P, P.ty, ns);
+  if (smem > budget) return cudaErrorInvalidValue;
   if (P.ty == 64) return launch_ty<HW, 64>(P, smem, st);
-  if (P.ty == 128) return launch_ty<HW, 128>(P, smem, st);
-  return cudaErrorInvalidValue;
+  return launch_ty<HW, 128>(P, smem, st);
 }
 
 // Launches the convolution for half widths in [lo, hi] (one translation unit per range, so that

@@ -359,8 +359,9 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(Src src, int n_tile) {
 // a 64-bit accumulator per Gram entry.  Levels 4..6 (weights 2^-48 .. 2^-64) share one FP32 tile
 // over the whole stamp.  The Gram entry is the integer sum plus the small levels, times the two
 // column scales: it carries the bits of its double-float inputs while the products run on the
-// tensor cores.  One CTA per stamp, four threads per Gram column (each thread reads 32 columns
-// of one accumulator lane back); at most 64 columns (one N = 64 tile).
+// tensor cores.  One CTA of 16 warps per stamp (the staging is latency bound: it waits on the
+// design values), of which eight read the accumulators back (a thread: 32 columns of one
+// accumulator lane); at most 64 columns (one N = 64 tile).
 constexpr int kOzSlices = 7;
 constexpr int kOzExact = 4;  // levels summed exactly per group
 constexpr int kOzGroup = 8;  // 32-pixel sub-chunks per exact group (256 pixels)
@@ -450,13 +451,17 @@ struct OzStampSource {
     *h = pix < P.P ? wh[pix] : 0.f;
     *l = pix < P.P ? wl[pix] : 0.f;
   }
-  __device__ void value(int c, int pix, float* vh, float* vl) const {
+  // the design value of column c at pixel pix (the global load, issued ahead of its use)
+  __device__ float2 fetch(int c, int pix) const {
+    if (pix >= P.P || c >= P.Nd) return make_float2(0.f, 0.f);
+    return reinterpret_cast<const float2*>(P.C)[((int64_t)r * P.Nd + c) * P.P + pix];
+  }
+  __device__ void make(int c, int pix, float2 cv, float* vh, float* vl) const {
     *vh = 0.f;
     *vl = 0.f;
     if (pix >= P.P || c >= P.Nc) return;
     const int Nd = P.Nd, nbk = P.b.Nb;
     if (c < Nd) {
-      const float2 cv = reinterpret_cast<const float2*>(P.C)[((int64_t)r * Nd + c) * P.P + pix];
       // psi C - s X in double-float, X = masked R (or I2 for the dual kernel's terms)
       const float pa = ph[c], pb = pl[c];
       float h = __fmul_rn(pa, cv.x);
@@ -513,8 +518,12 @@ struct OzPlainSource {
     *wh = pix < n_pix ? w[(int64_t)r * n_pix + pix] : 0.f;
     *wl = 0.f;
   }
-  __device__ void value(int c, int pix, float* vh, float* vl) const {
-    *vh = (pix < n_pix && c < n_cols) ? cols[((int64_t)r * n_cols + c) * n_pix + pix] : 0.f;
+  __device__ float2 fetch(int c, int pix) const {
+    return make_float2(
+        (pix < n_pix && c < n_cols) ? cols[((int64_t)r * n_cols + c) * n_pix + pix] : 0.f, 0.f);
+  }
+  __device__ void make(int, int, float2 cv, float* vh, float* vl) const {
+    *vh = cv.x;
     *vl = 0.f;
   }
   __device__ double* gram() const { return G + (int64_t)r * n_cols * n_cols; }
@@ -571,14 +580,26 @@ __global__ void __launch_bounds__(512, 1) k_gram_oz(Src src, int n_tile) {
   src.bind(reinterpret_cast<float*>(tc_sh + 2 * stage_bytes));
   src.prepare(tid, nthr);
   __syncthreads();
-  for (int i = tid; i < Nc * npix; i += nthr) {
-    const int c = i / npix, pix = i - c * npix;
-    float vh, vl, wh, wl;
-    src.value(c, pix, &vh, &vl);
-    src.weight(pix, &wh, &wl);
-    const float a = fabsf(vh), b = fabsf(vh * wh);
-    if (a > 0.f) atomicMax(&s_maxa[c], __float_as_uint(a));
-    if (b > 0.f) atomicMax(&s_maxb[c], __float_as_uint(b));
+  // four elements per thread at a time, their loads issued together
+  for (int i0 = tid; i0 < Nc * npix; i0 += 4 * nthr) {
+    float2 cv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * nthr;
+      cv[u] = i < Nc * npix ? src.fetch(i / npix, i % npix) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * nthr;
+      if (i >= Nc * npix) break;
+      const int c = i / npix, pix = i - c * npix;
+      float vh, vl, wh, wl;
+      src.make(c, pix, cv[u], &vh, &vl);
+      src.weight(pix, &wh, &wl);
+      const float a = fabsf(vh), b = fabsf(vh * wh);
+      if (a > 0.f) atomicMax(&s_maxa[c], __float_as_uint(a));
+      if (b > 0.f) atomicMax(&s_maxb[c], __float_as_uint(b));
+    }
   }
   __syncthreads();
   for (int c = tid; c < kTcM; c += nthr) {
@@ -623,21 +644,32 @@ __global__ void __launch_bounds__(512, 1) k_gram_oz(Src src, int n_tile) {
     const int base = ch * kTcKC;
     if (tid < kTcKC) src.weight(base + tid, &s_wh[tid], &s_wl[tid]);
     __syncthreads();
-    for (int i = tid; i < Nc * kTcKC; i += nthr) {
-      const int c = i / kTcKC, j = i - c * kTcKC;
-      float vh, vl, bh, bl;
-      src.value(c, base + j, &vh, &vl);
-      oz_mul(vh, vl, s_wh[j], s_wl[j], &bh, &bl);
-      const float sa = __int_as_float((127 - s_ea[c]) << 23);
-      const float sb = __int_as_float((127 - s_eb[c]) << 23);
-      uint16_t da[kOzSlices], db[kOzSlices];
-      oz_digits(vh * sa, vl * sa, da);
-      oz_digits(bh * sb, bl * sb, db);
-      const uint32_t off = tile_off<ESZ>(c, j);
+    for (int i0 = tid; i0 < Nc * kTcKC; i0 += 2 * nthr) {
+      float2 cv[2];
 #pragma unroll
-      for (int k = 0; k < kOzSlices; ++k) {
-        *reinterpret_cast<uint16_t*>(a_plane(s, k) + off) = da[k];
-        *reinterpret_cast<uint16_t*>(b_plane(s, k) + off) = db[k];
+      for (int u = 0; u < 2; ++u) {
+        const int i = i0 + u * nthr;
+        cv[u] = i < Nc * kTcKC ? src.fetch(i / kTcKC, base + i % kTcKC) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int i = i0 + u * nthr;
+        if (i >= Nc * kTcKC) break;
+        const int c = i / kTcKC, j = i - c * kTcKC;
+        float vh, vl, bh, bl;
+        src.make(c, base + j, cv[u], &vh, &vl);
+        oz_mul(vh, vl, s_wh[j], s_wl[j], &bh, &bl);
+        const float sa = __int_as_float((127 - s_ea[c]) << 23);
+        const float sb = __int_as_float((127 - s_eb[c]) << 23);
+        uint16_t da[kOzSlices], db[kOzSlices];
+        oz_digits(vh * sa, vl * sa, da);
+        oz_digits(bh * sb, bl * sb, db);
+        const uint32_t off = tile_off<ESZ>(c, j);
+#pragma unroll
+        for (int k = 0; k < kOzSlices; ++k) {
+          *reinterpret_cast<uint16_t*>(a_plane(s, k) + off) = da[k];
+          *reinterpret_cast<uint16_t*>(b_plane(s, k) + off) = db[k];
+        }
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -676,7 +708,7 @@ __global__ void __launch_bounds__(512, 1) k_gram_oz(Src src, int n_tile) {
       __syncthreads();
       if (!s_ok) break;
       tc_fence_after();
-      if (row < kTcM) {
+      if (col0 < n_tile) {
         const uint32_t lanebase = ((uint32_t)(quad * 32)) << 16;
 #pragma unroll
         for (int L = 0; L < kOzExact; ++L) {
@@ -706,7 +738,7 @@ __global__ void __launch_bounds__(512, 1) k_gram_oz(Src src, int n_tile) {
   __syncthreads();
   tc_fence_after();
   const bool ok = s_ok != 0 && last == nsub - 1;
-  if (ok) {
+  if (ok && col0 < n_tile) {
     float rv0[16], rv1[16];
     const uint32_t lanebase = ((uint32_t)(quad * 32)) << 16;
     tc_ld16(tmem + lanebase + rest_col + col0, rv0);
@@ -778,7 +810,7 @@ cudaError_t launch_gram_oz_src(const Src& src, int nblk, int n_cols, int n_pix, 
   cudaError_t e = cudaFuncSetAttribute(k_gram_oz<Src>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gram_oz<Src><<<nblk, 4 * n_tile, smem, s>>>(src, n_tile);
+  k_gram_oz<Src><<<nblk, 512, smem, s>>>(src, n_tile);
   return cudaGetLastError();
 }
 
