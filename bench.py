@@ -36,7 +36,7 @@ WORKLOAD = dict(
     spatial_order=2, stamps=300, grid=(15, 20), seed=2)
 # DRAM bytes (read + write) of one k_conv_image launch on the full-chip workload, from an ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as it stands.
-CONV_TRAFFIC_FULL_CHIP = 236.01408e6 + 75.43168e6
+CONV_TRAFFIC_FULL_CHIP = 236.24064e6 + 75.099904e6
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3, "f32x2": 4, "bf16x6": 5}
