@@ -21,6 +21,7 @@
 #include <cstring>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "psfm_internal.h"
 #include "solve.h"
 #include "stamp.h"
@@ -29,6 +30,9 @@ namespace psfm {
 
 cudaError_t launch_gram_tc(int mode, const StampParams& sp, int nreg, cudaStream_t s);
 cudaError_t launch_gram_oz(const StampParams& sp, int nreg, cudaStream_t s);
+size_t design_df_smem(int foot, int sw, int h, int dmax);
+cudaError_t launch_design_df(int h, dim3 grid, size_t smem, const StampParams& sp,
+                             cudaStream_t s);
 
 namespace {
 
@@ -121,225 +125,6 @@ __global__ void __launch_bounds__(256) k_stamp_design(StampParams P) {
   }
 }
 
-// ---- Double-float ("FP32 pair") arithmetic: a value is hi + lo with |lo| <= ulp(hi) / 2.
-// Products use the exact FMA residual, sums the error-free TwoSum, so each operation keeps
-// about 48 significant bits while running on the FP32 pipes (FP64 on this GPU runs at 1/64
-// of the FP32 rate).  Intrinsics keep the compiler from re-associating the compensations.
-struct df {
-  float hi, lo;
-};
-
-__device__ __forceinline__ df df_split(double v) {
-  df r;
-  r.hi = (float)v;
-  r.lo = (float)(v - (double)r.hi);
-  return r;
-}
-
-// acc += p + e where p is an FP32 value and e a small correction
-__device__ __forceinline__ void df_acc(df& acc, float p, float e) {
-  const float s = __fadd_rn(acc.hi, p);
-  const float bb = __fsub_rn(s, acc.hi);
-  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  acc.hi = s;
-  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
-}
-
-// acc += a * b for an FP32 a (exact) and a double-float b
-__device__ __forceinline__ void df_fma_f(df& acc, float a, df b) {
-  const float p = __fmul_rn(b.hi, a);
-  float e = __fmaf_rn(b.hi, a, -p);
-  e = __fmaf_rn(b.lo, a, e);
-  df_acc(acc, p, e);
-}
-
-// acc += a * b for double-floats a and b (the lo * lo term is below the precision kept)
-__device__ __forceinline__ void df_fma(df& acc, df a, df b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  df_acc(acc, p, e);
-}
-
-__device__ __forceinline__ df df_mul(df a, df b) {
-  df r;
-  r.hi = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -r.hi);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  const float s = __fadd_rn(r.hi, e);
-  r.lo = __fsub_rn(e, __fsub_rn(s, r.hi));
-  r.hi = s;
-  return r;
-}
-
-__device__ __forceinline__ df df_norm(df a) {
-  df r;
-  r.hi = __fadd_rn(a.hi, a.lo);
-  r.lo = __fsub_rn(a.lo, __fsub_rn(r.hi, a.hi));
-  return r;
-}
-
-__device__ __forceinline__ double df_to_d(df a) { return (double)a.hi + (double)a.lo; }
-
-__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
-
-__device__ __forceinline__ df df_add(df a, df b) {
-  df t = a;
-  df_acc(t, b.hi, b.lo);
-  return df_norm(t);
-}
-
-// grid (nreg, N_H): the basis-convolved footprint of the terms of one horizontal plane (g, p),
-// that is B_{g,p,q} (x) R for q = 0..d_g - p, in double-float.  The reference pixels are exact
-// FP32; the 1-D factors are split into FP32 pairs.  One block per plane spreads a stamp over
-// N_H blocks, so a handful of replaced stamps still fill many SMs.
-__global__ void __launch_bounds__(256) k_stamp_design_df(StampParams P) {
-  extern __shared__ __align__(16) unsigned char sh_raw[];
-  // blockIdx.y = set * N_H + plane: set 0 convolves the masked reference, set 1 (dual kernel,
-  // Eq. 2) the science image with its own mask, into design columns N_b..2 N_b - 1
-  const int r = blockIdx.x, set = blockIdx.y / P.b.NH, pl = blockIdx.y - set * P.b.NH;
-  const int tid = threadIdx.x;
-  if (block_skip(P.st)) return;
-  int cx, cy;
-  if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return;
-  if (P.have[r] == P.ptr[r]) return;
-  int g = 0;
-  while (g + 1 < P.b.ng && pl >= P.b.plane_base[g + 1]) ++g;
-  const int h = P.b.h, W = P.b.w, foot = P.foot, sw = P.sw;
-  const int dg = P.b.deg[g], pb = P.b.plane_base[g], p = pl - pb;
-  float* F = reinterpret_cast<float*>(sh_raw);   // foot x foot
-  float* Hh = F + foot * foot;                    // foot x sw
-  float* Hl = Hh + foot * sw;
-  float* wh = Hl + foot * sw;                     // (dg+1) x W
-  float* wl = wh + (dg + 1) * W;
-  for (int i = tid; i < (dg + 1) * W; i += 256) {
-    const int n = i / W, t = i - n * W;
-    const df v = df_split(P.f1d64[(pb + n) * W + t]);
-    wh[i] = v.hi;
-    wl[i] = v.lo;
-  }
-  const int x0 = cx - P.s - h, y0 = cy - P.s - h;
-  double f1 = 0.0, f2 = 0.0, nf = 0.0;
-  for (int i = tid; i < foot * foot; i += 256) {
-    const int rr = i / foot, cc = i - rr * foot;
-    const int gx = x0 + cc, gy = y0 + rr;
-    float v = 0.f;
-    if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
-      const int64_t o = (int64_t)gy * P.g.pitch + gx;
-      const uint16_t a = P.m1[o] & P.badmask, b = P.m2[o] & P.badmask;
-      if (set == 0) {
-        if (!a) v = P.i1[o];
-      } else if (!b) {
-        v = P.i2[o];
-      }
-      if (set == 0 && pl == 0 && !a && !b) {
-        f1 += v;
-        f2 += P.i2[o];
-        nf += 1.0;
-      }
-    }
-    F[i] = v;
-  }
-  if (set == 0 && pl == 0) {
-    __shared__ double red[3][8];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      f1 += __shfl_xor_sync(0xffffffffu, f1, o);
-      f2 += __shfl_xor_sync(0xffffffffu, f2, o);
-      nf += __shfl_xor_sync(0xffffffffu, nf, o);
-    }
-    if ((tid & 31) == 0) {
-      red[0][tid >> 5] = f1;
-      red[1][tid >> 5] = f2;
-      red[2][tid >> 5] = nf;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double a = 0, b = 0, c = 0;
-      for (int i = 0; i < 8; ++i) {
-        a += red[0][i];
-        b += red[1][i];
-        c += red[2][i];
-      }
-      P.footsum[4 * r] = a;
-      P.footsum[4 * r + 1] = b;
-      P.footsum[4 * r + 2] = c;
-    }
-  }
-  __syncthreads();
-  // horizontal pass: each thread takes 4 neighbouring outputs of one footprint row and slides
-  // a 4-value register window along the taps (one shared-memory load per tap instead of four);
-  // each output still sums its taps in order t = 0..W-1
-  {
-    const float* ph = wh + p * W;
-    const float* pw = wl + p * W;
-    const int ncg = (sw + 3) / 4;
-    for (int it = tid; it < foot * ncg; it += 256) {
-      const int rr = it / ncg, px0 = (it - rr * ncg) * 4;
-      const float* row = F + rr * foot;
-      float x0 = row[min(px0 + 2 * h, foot - 1)], x1 = row[min(px0 + 1 + 2 * h, foot - 1)];
-      float x2 = row[min(px0 + 2 + 2 * h, foot - 1)], x3 = row[min(px0 + 3 + 2 * h, foot - 1)];
-      df a0 = {0.f, 0.f}, a1 = a0, a2 = a0, a3 = a0;
-      for (int t = 0; t < W; ++t) {
-        const df w = {ph[t], pw[t]};
-        df_fma_f(a0, x0, w);
-        df_fma_f(a1, x1, w);
-        df_fma_f(a2, x2, w);
-        df_fma_f(a3, x3, w);
-        x3 = x2;
-        x2 = x1;
-        x1 = x0;
-        if (t + 1 < W) x0 = row[px0 + 2 * h - t - 1];
-      }
-      const df o[4] = {df_norm(a0), df_norm(a1), df_norm(a2), df_norm(a3)};
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (px0 + j < sw) {
-          Hh[rr * sw + px0 + j] = o[j].hi;
-          Hl[rr * sw + px0 + j] = o[j].lo;
-        }
-    }
-  }
-  __syncthreads();
-  // vertical passes: each thread takes 4 neighbouring rows of one column, with the same
-  // sliding window over the horizontal-pass rows
-  const int kgp = P.b.kbase[g] + p * (dg + 1) - (p * (p - 1)) / 2;
-  const int nrg = (sw + 3) / 4;
-  for (int q = 0; q <= dg - p; ++q) {
-    const float* qh = wh + q * W;
-    const float* ql = wl + q * W;
-    float2* out = reinterpret_cast<float2*>(P.C) +
-                  ((int64_t)r * P.Nd + set * P.b.Nb + kgp + q) * P.P;
-    for (int it = tid; it < sw * nrg; it += 256) {
-      const int rg = it / sw, px = it - rg * sw, py0 = rg * 4;
-      auto ld = [&](int row) {
-        const int o = min(row, foot - 1) * sw + px;
-        return df{Hh[o], Hl[o]};
-      };
-      df y0 = ld(py0 + 2 * h), y1 = ld(py0 + 1 + 2 * h), y2 = ld(py0 + 2 + 2 * h);
-      df y3 = ld(py0 + 3 + 2 * h);
-      df a0 = {0.f, 0.f}, a1 = a0, a2 = a0, a3 = a0;
-      for (int t = 0; t < W; ++t) {
-        const df w = {qh[t], ql[t]};
-        df_fma(a0, y0, w);
-        df_fma(a1, y1, w);
-        df_fma(a2, y2, w);
-        df_fma(a3, y3, w);
-        y3 = y2;
-        y2 = y1;
-        y1 = y0;
-        if (t + 1 < W) y0 = ld(py0 + 2 * h - t - 1);
-      }
-      const df o[4] = {df_norm(a0), df_norm(a1), df_norm(a2), df_norm(a3)};
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (py0 + j < sw) out[(py0 + j) * sw + px] = make_float2(o[j].hi, o[j].lo);
-    }
-  }
-}
-
 // grid (nreg, kGramSplit), 384 threads, two blocks per SM: weighted Gram of the augmented
 // block in double-float.  Block (r, j) takes the 64-pixel chunks j, j + kGramSplit, ... of
 // stamp r.  Each thread owns a 4 x 4 block of the Gram and one of `nsl` interleaved pixel
@@ -356,6 +141,7 @@ constexpr int kGramChunk = 64;
 // warp read (different columns, same pixel) in different shared-memory banks
 constexpr int kGramLd = kGramChunk + 1;
 constexpr int kGramThreads = 384;
+constexpr int kGramBatch = 4;
 
 __host__ __device__ constexpr int gram_slices(int npair) {
   int nsl = 1;
@@ -386,18 +172,28 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_stamp_gram_df(StampParams P
   const int nch = (nchunk - split + nsplit - 1) / nsplit;
   float* wh = Bl + ncr * kGramLd;
   float* wl = wh + nch * kGramChunk;
+  // and the pixel values of the images the zero-sum delta terms use (masked R; I2 for the
+  // dual kernel's columns), [chunk t][64] each; the masks do not gate the pixel loads, so all
+  // of a pixel's loads are in flight together
+  float* xr = wl + nch * kGramChunk;
+  float* xi = xr + nch * kGramChunk;
   for (int i = tid; i < nch * kGramChunk; i += kGramThreads) {
     const int t = i / kGramChunk;
     const int pix = (split + t * nsplit) * kGramChunk + (i - t * kGramChunk);
     df wv = {0.f, 0.f};
+    float vr = 0.f, vi = 0.f;
     if (pix < P.P) {
       const int py = pix / P.sw, px = pix - py * P.sw;
       const int gx = cx - P.s + px, gy = cy - P.s + py;
       if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
         const int64_t o = (int64_t)gy * P.g.pitch + gx;
-        if (!((P.m1[o] | P.m2[o]) & P.badmask)) {
-          const float a = P.i1[o], b = P.i2[o], vv = P.v1[o] + P.v2[o];
-          const double wd = 1.0 / ((double)P.v1[o] + (double)P.v2[o]);
+        const uint16_t m1 = P.m1[o], m2 = P.m2[o];
+        const float a = P.i1[o], b = P.i2[o], v1 = P.v1[o], v2 = P.v2[o];
+        vr = (m1 & P.badmask) ? 0.f : a;
+        vi = b;
+        if (!((m1 | m2) & P.badmask)) {
+          const float vv = v1 + v2;
+          const double wd = 1.0 / ((double)v1 + (double)v2);
           if (!isfinite(a) || !isfinite(b) || !isfinite(vv) || !isfinite(wd))
             raise_error(P.st, PSFM_ERR_NONFINITE);
           wv = df_split(wd);
@@ -406,17 +202,16 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_stamp_gram_df(StampParams P
     }
     wh[i] = wv.hi;
     wl[i] = wv.lo;
+    xr[i] = vr;
+    xi[i] = vi;
   }
   const float2* Cr = reinterpret_cast<const float2*>(P.C) + (int64_t)r * Nb * P.P;
   double* Gp = P.Gpart + ((int64_t)r * kGramSplit + split) * Nc * Nc;
-  // psi_k and s_k of every design column as double-floats, and the chunk's pixel values of the
-  // images the zero-sum delta terms use (masked R; I2 for the dual kernel's columns)
-  float* psh = wl + nch * kGramChunk;
+  // psi_k and s_k of every design column as double-floats
+  float* psh = xi + nch * kGramChunk;
   float* psl = psh + Nb;
   float* skh = psl + Nb;
   float* skl = skh + Nb;
-  float* xr = skl + Nb;
-  float* xi = xr + kGramChunk;
   const int nbk = P.b.Nb;
   for (int c = tid; c < Nb; c += kGramThreads) {
     const int k = c < nbk ? c : c - nbk;
@@ -445,46 +240,47 @@ __global__ void __launch_bounds__(kGramThreads, 2) k_stamp_gram_df(StampParams P
       const float* wht = wh + t * kGramChunk;
       const float* wlt = wl + t * kGramChunk;
       __syncthreads();
-      if (tid < kGramChunk) {
-        const int pix = base + tid;
-        float vr = 0.f, vi = 0.f;
-        if (pix < P.P) {
-          const int py = pix / P.sw, px = pix - py * P.sw;
-          const int gx = cx - P.s + px, gy = cy - P.s + py;
-          if (gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H) {
-            const int64_t o = (int64_t)gy * P.g.pitch + gx;
-            vr = (P.m1[o] & P.badmask) ? 0.f : P.i1[o];
-            vi = P.i2[o];
-          }
+      const float* xrt = xr + t * kGramChunk;
+      const float* xit = xi + t * kGramChunk;
+      // the design values of kGramBatch elements per thread are loaded before any is used,
+      // so that their global loads are in flight together
+      for (int i0 = tid; i0 < ncr * kGramChunk; i0 += kGramBatch * kGramThreads) {
+        float2 cv[kGramBatch];
+#pragma unroll
+        for (int e = 0; e < kGramBatch; ++e) {
+          const int i = i0 + e * kGramThreads;
+          const int c = i / kGramChunk, pix = base + (i - c * kGramChunk);
+          cv[e] = make_float2(0.f, 0.f);
+          if (i < ncr * kGramChunk && c < Nb && pix < P.P) cv[e] = Cr[(int64_t)c * P.P + pix];
         }
-        xr[tid] = vr;
-        xi[tid] = vi;
-      }
-      __syncthreads();
-      for (int i = tid; i < ncr * kGramChunk; i += kGramThreads) {
-        const int c = i / kGramChunk, j = i - c * kGramChunk, pix = base + j;
-        df v = {0.f, 0.f};
-        if (pix < P.P) {
-          if (c < Nb) {
-            const float2 cv = Cr[(int64_t)c * P.P + pix];
-            v = df_mul(df{psh[c], psl[c]}, df{cv.x, cv.y});
-            if (skh[c] != 0.f) {
-              const float x = c < nbk ? xr[j] : xi[j];
-              v = df_add(v, df_neg(df_mul(df{skh[c], skl[c]}, df{x, 0.f})));
+#pragma unroll
+        for (int e = 0; e < kGramBatch; ++e) {
+          const int i = i0 + e * kGramThreads;
+          if (i >= ncr * kGramChunk) break;
+          const int c = i / kGramChunk, j = i - c * kGramChunk, pix = base + j;
+          df v = {0.f, 0.f};
+          if (pix < P.P) {
+            if (c < Nb) {
+              v = df_mul(df{psh[c], psl[c]}, df{cv[e].x, cv[e].y});
+              if (skh[c] != 0.f) {
+                const float x = c < nbk ? xrt[j] : xit[j];
+                v = df_add(v, df_neg(df_mul(df{skh[c], skl[c]}, df{x, 0.f})));
+              }
+            } else if (c < Nc) {
+              v.hi = c == Nb ? xrt[j] : (c == Nb + 1 ? 1.f : xit[j]);
             }
-          } else if (c < Nc) {
-            v.hi = c == Nb ? xr[j] : (c == Nb + 1 ? 1.f : xi[j]);
           }
+          const df b = df_mul(df{wht[j], wlt[j]}, v);
+          Ah[c * kGramLd + j] = v.hi;
+          Al[c * kGramLd + j] = v.lo;
+          Bh[c * kGramLd + j] = b.hi;
+          Bl[c * kGramLd + j] = b.lo;
         }
-        const df b = df_mul(df{wht[j], wlt[j]}, v);
-        Ah[c * kGramLd + j] = v.hi;
-        Al[c * kGramLd + j] = v.lo;
-        Bh[c * kGramLd + j] = b.hi;
-        Bl[c * kGramLd + j] = b.lo;
       }
       __syncthreads();
       if (act) {
-        for (int j = sl; j < kGramChunk; j += nsl) {
+        const int jmax = min(kGramChunk, P.P - base);  // the last chunk of a stamp is ragged
+        for (int j = sl; j < jmax; j += nsl) {
           df a[4], b[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
@@ -1514,50 +1310,59 @@ __global__ void __launch_bounds__(1024) k_lu_solve(int N, int joint, const doubl
   }
 }
 
-// sum_k a_k C_k(pix): FP64 products for FP32 / FP64 design blocks, double-float products on
-// the FP32 pipes for double-float blocks.
-// sum_k a_k psi_k C_k at 4 stamp pixels at once (independent loads and accumulators; each
-// pixel still sums its terms in order k = 0..Nb-1).  pix < 0 marks an unused slot.
-__device__ __forceinline__ void basis_model4(const double* ak, const float2*, const float* C,
-                                             int Nb, int P, const int pix[4], double m[4]) {
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+// sum_k a_k psi_k C_k(pix) at NPX stamp pixels at once (independent loads and accumulators;
+// each pixel still sums its terms in order k = 0..Nb-1): FP64 products for FP32 / FP64 design
+// blocks, double-float products on the FP32 pipes for double-float blocks.  pix < 0 marks an
+// unused slot.
+template <int NPX>
+__device__ __forceinline__ void basis_model(const double* ak, const float2*, const float* C,
+                                            int Nb, int P, const int* pix, double* m) {
+  double acc[NPX];
+#pragma unroll
+  for (int j = 0; j < NPX; ++j) acc[j] = 0.0;
   for (int k = 0; k < Nb; ++k) {
     const double a = ak[k];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < NPX; ++j)
       if (pix[j] >= 0) acc[j] += a * (double)C[(int64_t)k * P + pix[j]];
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) m[j] = acc[j];
+  for (int j = 0; j < NPX; ++j) m[j] = acc[j];
 }
-__device__ __forceinline__ void basis_model4(const double* ak, const float2*, const double* C,
-                                             int Nb, int P, const int pix[4], double m[4]) {
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+template <int NPX>
+__device__ __forceinline__ void basis_model(const double* ak, const float2*, const double* C,
+                                            int Nb, int P, const int* pix, double* m) {
+  double acc[NPX];
+#pragma unroll
+  for (int j = 0; j < NPX; ++j) acc[j] = 0.0;
   for (int k = 0; k < Nb; ++k) {
     const double a = ak[k];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < NPX; ++j)
       if (pix[j] >= 0) acc[j] += a * C[(int64_t)k * P + pix[j]];
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) m[j] = acc[j];
+  for (int j = 0; j < NPX; ++j) m[j] = acc[j];
 }
-__device__ __forceinline__ void basis_model4(const double*, const float2* akf, const float2* C,
-                                             int Nb, int P, const int pix[4], double m[4]) {
-  df acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+template <int NPX>
+__device__ __forceinline__ void basis_model(const double*, const float2* akf, const float2* C,
+                                            int Nb, int P, const int* pix, double* m) {
+  df acc[NPX];
+#pragma unroll
+  for (int j = 0; j < NPX; ++j) acc[j] = df{0.f, 0.f};
   // unrolled so that the loads of several terms are in flight together
 #pragma unroll 8
   for (int k = 0; k < Nb; ++k) {
     const df a = {akf[k].x, akf[k].y};
-    float2 c[4];
+    float2 c[NPX];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < NPX; ++j)
       c[j] = pix[j] >= 0 ? C[(int64_t)k * P + pix[j]] : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) df_fma(acc[j], a, df{c[j].x, c[j].y});
+    for (int j = 0; j < NPX; ++j) df_fma(acc[j], a, df{c[j].x, c[j].y});
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) m[j] = df_to_d(df_norm(acc[j]));
+  for (int j = 0; j < NPX; ++j) m[j] = df_to_d(df_norm(acc[j]));
 }
 
 struct Chi2Params {
@@ -1567,40 +1372,65 @@ struct Chi2Params {
   double alpha;
   double* chi2;
   double* cand_chi2;
+  double* part;    // [nreg][kChi2Split][2] per-block sums (chi^2 terms, pixels)
+  int32_t* count;  // [nreg] blocks finished, reset by the block that combines them
 };
 
-// grid (nreg): chi^2 of the active stamp with the current solution (FP64).
+// grid (nreg, kChi2Split): chi^2 of the active stamp with the current solution (FP64).  Each
+// block takes one pixel range of the stamp, kChi2Px pixels per thread; the design-column loads
+// of a pixel depend only on the stamp geometry (the masks are applied afterwards), so they are
+// in flight together with the mask and image loads.  The last block of a stamp to finish
+// (counted with an atomic) adds the block sums in range order, so the value does not depend on
+// which block finishes last.
+constexpr int kChi2Threads = 256;
+constexpr int kChi2Px = 2;
 template <typename T>
-__global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
+__global__ void __launch_bounds__(kChi2Threads, 4) k_chi2(Chi2Params Q) {
   const StampParams& P = Q.sp;
   extern __shared__ double ak[];  // [Nd]: a_k(stamp) psi_k (then c_k psi_k, dual kernel)
-  __shared__ double red[2][8];
+  __shared__ double red[2][kChi2Threads / 32];
   __shared__ double s_delta, s_delta2;
-  const int r = blockIdx.x, tid = threadIdx.x;
+  __shared__ int s_last;
+  const int r = blockIdx.x, split = blockIdx.y, tid = threadIdx.x;
   if (block_skip(P.st)) return;
   int cx, cy;
   if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return;
   const int Nb = P.b.Nb, Nd = P.Nd, Ns = P.b.Ns;
   const double* gr = Q.gv + (int64_t)r * Ns;
-  for (int k = tid; k < Nd; k += 256) {
+  // a_k at the stamp centre, times psi_k, and the delta parts of the zero-sum terms (on R for
+  // the first N_b columns, on I2 for the dual kernel's), reduced over the block
+  double dd = 0.0, dd2 = 0.0;
+  for (int k = tid; k < Nd; k += kChi2Threads) {
     double a = 0.0;
     for (int s = 0; s < Ns; ++s) a += Q.dsol[2 + k * Ns + s] * gr[s];
-    ak[k] = a;
+    const int kb = k < Nb ? k : k - Nb;
+    if (k < Nb)
+      dd += a * P.sk[kb];
+    else
+      dd2 += a * P.sk[kb];
+    ak[k] = a * P.psi[kb];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dd += __shfl_xor_sync(0xffffffffu, dd, o);
+    dd2 += __shfl_xor_sync(0xffffffffu, dd2, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = dd;
+    red[1][tid >> 5] = dd2;
   }
   __syncthreads();
   if (tid == 0) {
-    // the delta parts of the zero-sum terms: on R for the first N_b columns, on I2 for the
-    // dual kernel's
-    double d = Q.dsol[0], d2 = 0.0;
-    for (int k = 0; k < Nb; ++k) d -= ak[k] * P.sk[k];
-    for (int k = Nb; k < Nd; ++k) d2 -= ak[k] * P.sk[k - Nb];
-    s_delta = d;
-    s_delta2 = d2;
+    double d = 0.0, d2 = 0.0;
+    for (int i = 0; i < kChi2Threads / 32; ++i) {
+      d += red[0][i];
+      d2 += red[1][i];
+    }
+    s_delta = Q.dsol[0] - d;
+    s_delta2 = -d2;
   }
-  __syncthreads();
   float2* akf = reinterpret_cast<float2*>(ak + Nd);  // the same split into FP32 pairs
-  for (int k = tid; k < Nd; k += 256) {
-    ak[k] *= P.psi[k < Nb ? k : k - Nb];
+  for (int k = tid; k < Nd; k += kChi2Threads) {
     const df d = df_split(ak[k]);
     akf[k] = make_float2(d.hi, d.lo);
   }
@@ -1608,31 +1438,34 @@ __global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
   const double delta = s_delta, delta2 = s_delta2, d0 = Q.dsol[1];
   const T* Cr = reinterpret_cast<const T*>(P.C) + (int64_t)r * Nd * P.P;
   double q = 0.0, n = 0.0;
-  // 4 pixels per thread at a time, so that their design-column loads overlap
-  for (int base = tid; base < P.P; base += 4 * 256) {
-    int pix[4];
-    int64_t off[4];
+  constexpr int kStride = kChi2Split * kChi2Threads * kChi2Px;
+  for (int base = split * kChi2Threads * kChi2Px + tid; base < P.P; base += kStride) {
+    int pix[kChi2Px];
+    int64_t off[kChi2Px];
+    uint16_t mk[kChi2Px];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kChi2Px; ++j) {
       pix[j] = -1;
-      const int pp = base + 256 * j;
+      off[j] = 0;
+      const int pp = base + kChi2Threads * j;
       if (pp >= P.P) continue;
       const int py = pp / P.sw, px = pp - py * P.sw;
       const int gx = cx - P.s + px, gy = cy - P.s + py;
       if (gx < 0 || gx >= P.g.W || gy < 0 || gy >= P.g.H) continue;
-      const int64_t o = (int64_t)gy * P.g.pitch + gx;
-      if ((P.m1[o] | P.m2[o]) & P.badmask) continue;
       pix[j] = pp;
-      off[j] = o;
+      off[j] = (int64_t)gy * P.g.pitch + gx;
     }
-    double mod[4];
-    basis_model4(ak, akf, Cr, Nd, P.P, pix, mod);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (pix[j] < 0) continue;
+    for (int j = 0; j < kChi2Px; ++j)
+      mk[j] = pix[j] >= 0 ? (uint16_t)((P.m1[off[j]] | P.m2[off[j]]) & P.badmask) : (uint16_t)1;
+    double mod[kChi2Px];
+    basis_model<kChi2Px>(ak, akf, Cr, Nd, P.P, pix, mod);
+#pragma unroll
+    for (int j = 0; j < kChi2Px; ++j) {
+      if (mk[j]) continue;
       const int64_t o = off[j];
       const double R = P.i1[o], I2 = P.i2[o];
-      const double model = delta * R + delta2 * (Nd > Nb ? (double)P.i2[o] : 0.0) + d0 + mod[j];
+      const double model = delta * R + delta2 * (Nd > Nb ? I2 : 0.0) + d0 + mod[j];
       const double res = I2 - model;
       const double den = ((double)P.v1[o] + (double)P.v2[o]) + Q.alpha * fabs(I2);
       q += res * res / den;
@@ -1644,6 +1477,7 @@ __global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
     q += __shfl_xor_sync(0xffffffffu, q, o);
     n += __shfl_xor_sync(0xffffffffu, n, o);
   }
+  __syncthreads();  // red is reused
   if ((tid & 31) == 0) {
     red[0][tid >> 5] = q;
     red[1][tid >> 5] = n;
@@ -1651,14 +1485,28 @@ __global__ void __launch_bounds__(256) k_chi2(Chi2Params Q) {
   __syncthreads();
   if (tid == 0) {
     double a = 0, b = 0;
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < kChi2Threads / 32; ++i) {
       a += red[0][i];
       b += red[1][i];
     }
-    const double c = a / (b > 1.0 ? b : 1.0);
-    Q.chi2[r] = c;
-    Q.cand_chi2[(int64_t)r * P.max_cand + P.ptr[r]] = c;
+    double* pr = Q.part + ((int64_t)r * kChi2Split + split) * 2;
+    pr[0] = a;
+    pr[1] = b;
+    __threadfence();
+    s_last = atomicAdd(&Q.count[r], 1) == kChi2Split - 1;
   }
+  __syncthreads();
+  if (!s_last || tid != 0) return;
+  __threadfence();
+  double a = 0, b = 0;
+  for (int k = 0; k < kChi2Split; ++k) {
+    a += __ldcg(Q.part + ((int64_t)r * kChi2Split + k) * 2);
+    b += __ldcg(Q.part + ((int64_t)r * kChi2Split + k) * 2 + 1);
+  }
+  const double c = a / (b > 1.0 ? b : 1.0);
+  Q.chi2[r] = c;
+  Q.cand_chi2[(int64_t)r * P.max_cand + P.ptr[r]] = c;
+  Q.count[r] = 0;
 }
 
 // Rejection decision of Sec. 3.3 and loop control; one CTA of 1024 threads.
@@ -1765,6 +1613,8 @@ void carve_solve(const Plan& p, Workspace& ws, SolveBuffers& b) {
   b.gram_count = ws.take<int32_t>(p.nreg);
   b.foot = ws.take<double>((size_t)p.nreg * 4);
   b.chi2 = ws.take<double>(p.nreg);
+  b.chi2_part = ws.take<double>((size_t)p.nreg * kChi2Split * 2);
+  b.chi2_count = ws.take<int32_t>(p.nreg);
   b.M = ws.take<double>((size_t)p.Nsys * p.Nsys);
   b.v = ws.take<double>(p.Nsys);
   b.L = ws.take<double>((size_t)p.Nsys * p.Nsys);
@@ -1862,6 +1712,8 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   cq.alpha = p.cfg.soften_alpha;
   cq.chi2 = b.chi2;
   cq.cand_chi2 = b.cand_chi2;
+  cq.part = b.chi2_part;
+  cq.count = b.chi2_count;
 
   // design block storage is double for the FP64 and double-float modes, float for FP32
   const int prec = p.cfg.precision;
@@ -1870,11 +1722,9 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   const int nblk = (p.Nc + 3) / 4, npair = nblk * (nblk + 1) / 2;
   size_t sm_gram = sizeof(double) * npair * 16 + esz * (nblk * 4 * 32 + 32);
   if (prec == PSFM_PREC_F32X2 || prec == PSFM_PREC_BF16X6) {
-    sm_design = sizeof(float) * ((size_t)p.foot * p.foot + 2 * (size_t)p.foot * p.sw +
-                                 2 * (size_t)(p.dmax + 1) * p.w);
+    sm_design = design_df_smem(p.foot, p.sw, p.h, p.dmax);
     const int maxch = ((p.P + kGramChunk - 1) / kGramChunk + kGramSplit - 1) / kGramSplit;
-    sm_gram = sizeof(float) * (4 * nblk * 4 * kGramLd + 2 * maxch * kGramChunk + 4 * p.Nd +
-                               2 * kGramChunk);
+    sm_gram = sizeof(float) * (4 * nblk * 4 * kGramLd + 4 * maxch * kGramChunk + 4 * p.Nd);
   }
   if (sm_design > 200 * 1024 || sm_gram > 200 * 1024) return PSFM_ERR_UNSUPPORTED;
   // TF32 / BF16X3: FP32 design blocks, the Gram on the tensor cores (k_gram_tc.cu)
@@ -1882,8 +1732,7 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   const bool tcm = prec == PSFM_PREC_TF32 || prec == PSFM_PREC_BF16X3;
   const bool ozm = prec == PSFM_PREC_BF16X6;
   const bool dfm = prec == PSFM_PREC_F32X2 || ozm;
-  auto design = prec == PSFM_PREC_FP64 ? k_stamp_design<double>
-                : dfm ? k_stamp_design_df : k_stamp_design<float>;
+  auto design = prec == PSFM_PREC_FP64 ? k_stamp_design<double> : k_stamp_design<float>;
   auto gram = prec == PSFM_PREC_FP64 ? k_stamp_gram<double>
               : dfm ? k_stamp_gram_df : k_stamp_gram<float>;
   auto chi2 = prec == PSFM_PREC_FP64 ? k_chi2<double> : dfm ? k_chi2<float2> : k_chi2<float>;
@@ -1913,11 +1762,18 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
       cudaMemsetAsync(b.fresh, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess ||
       cudaMemsetAsync(b.removed, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess ||
       cudaMemsetAsync(b.gram_count, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess ||
+      cudaMemsetAsync(b.chi2_count, 0, sizeof(int32_t) * p.nreg, s) != cudaSuccess ||
       cudaMemsetAsync(b.pdiag, 0, sizeof(double) * p.Nsys, s) != cudaSuccess)
     return PSFM_ERR_CUDA;
   for (int it = 0; it < p.cfg.max_iter; ++it) {
     prof_begin("stamps", s);
-    design<<<dim3(p.nreg, dfm ? p.NH * (p.cfg.dual ? 2 : 1) : p.ng), 256, sm_design, s>>>(sp);
+    if (dfm) {
+      if (launch_design_df(p.h, dim3(p.nreg, p.NH * (p.cfg.dual ? 2 : 1)), sm_design, sp, s) !=
+          cudaSuccess)
+        return PSFM_ERR_CUDA;
+    } else {
+      design<<<dim3(p.nreg, p.ng), 256, sm_design, s>>>(sp);
+    }
     if (tcm) {
       if (launch_gram_tc(prec == PSFM_PREC_TF32 ? 0 : 1, sp, p.nreg, s) != cudaSuccess)
         return PSFM_ERR_CUDA;
@@ -1952,7 +1808,8 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
     k_lu_solve<<<1, 1024, 0, s>>>(N, sy.joint, b.M, b.pdiag, b.v, b.L, b.y, b.piv, dsol, st);
     prof_end("cholesky", s, npanel + 7);
     prof_begin("chi2_reject", s);
-    chi2<<<p.nreg, 256, (sizeof(double) + sizeof(float2)) * p.Nd + 16, s>>>(cq);
+    chi2<<<dim3(p.nreg, kChi2Split), kChi2Threads, (sizeof(double) + sizeof(float2)) * p.Nd + 16,
+           s>>>(cq);
     k_reject<<<1, reject_threads, 0, s>>>(p.nreg, p.max_cand, p.cfg.max_iter, p.cfg.reject_nsigma, b.cand,
                                 b.ptr, b.cand_stat, b.chi2, b.fresh, b.removed, st);
     k_system_delta<<<(unsigned)((nthr + 255) / 256), 256, sm_asm, s>>>(sy, 1, asm_chunk);

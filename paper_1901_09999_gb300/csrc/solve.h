@@ -8,6 +8,8 @@ namespace psfm {
 
 // Blocks that share one stamp's Gram (pixel chunks split between them).
 constexpr int kGramSplit = 4;
+// Blocks that share one stamp's chi^2 (pixel ranges).
+constexpr int kChi2Split = 2;
 
 struct SolveBuffers {
   // extractor (Sec. 3.3)
@@ -33,6 +35,8 @@ struct SolveBuffers {
   int32_t* gram_count;  // [nreg] partial Grams finished for the stamp being built
   double* foot;  // [nreg][4] footprint sums F1, F2, n, unused
   double* chi2;  // [nreg] chi^2 of the active stamp
+  double* chi2_part;    // [nreg][kChi2Split][2] per-block chi^2 sums
+  int32_t* chi2_count;  // [nreg] chi^2 blocks finished
   // normal equations
   double* M;  // [Nsys][Nsys]
   double* v;  // [Nsys]
