@@ -252,15 +252,20 @@ __global__ void __launch_bounds__(4 * TY, TY == 64 ? 2 : 1) k_conv_image(ConvPar
     if (l + m <= S) v = (float)(P.dsol[2 + k * P.b.Ns + spatial_index(l, m, S)] * P.psi[k]);
     alpha[i] = v;
   }
-  if (tid < S1 * S1) {
-    const int m = tid / S1, l = tid - m * S1;
+  // beta's polynomial: warp w forms the coefficients (m, l) = w, w + NT / 32, ..., each lane
+  // summing the terms k = lane, lane + 32, ... and the warp adding the lanes' sums by shuffles
+  // (no serial FP64 chain in the CTA's prologue)
+  for (int c = tid >> 5; c < S1 * S1; c += NT / 32) {
+    const int m = c / S1, l = c - m * S1, lane = tid & 31;
     double v = 0.0;
     if (l + m <= S) {
       const int s = spatial_index(l, m, S);
-      if (s == 0) v = P.dsol[0];
-      for (int k = 0; k < P.b.Nb; ++k) v -= P.dsol[2 + k * P.b.Ns + s] * P.sk[k];
+      for (int k = lane; k < P.b.Nb; k += 32) v += P.dsol[2 + k * P.b.Ns + s] * P.sk[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      v = (s == 0 ? P.dsol[0] : 0.0) - v;
     }
-    beta[tid] = (float)v;
+    if (lane == 0) beta[c] = (float)v;
   }
   // masked reference tile with halo; zero padding to the row stride
   stage_masked_tile<8>(P.ref, P.mref, P.badmask, P.g.W, P.g.H, P.g.pitch, x0 - HW, y0 - HW, RR,

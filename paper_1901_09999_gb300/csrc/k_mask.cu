@@ -17,6 +17,10 @@ namespace {
 constexpr int kTileRows = 32;
 constexpr int kTileWords = 8;  // 256 pixels
 
+// Each thread loads kBitsBatch rows of its column before the first ballot, so that a CTA keeps
+// enough bytes in flight to stream the 2-byte mask at HBM rate.
+constexpr int kBitsBatch = 8;
+
 __global__ void __launch_bounds__(256) k_mask_bits(const uint16_t* m1, const uint16_t* m2, int W,
                                                    int H, int64_t pitch, int nwords,
                                                    uint16_t badmask, uint32_t* bits) {
@@ -24,17 +28,24 @@ __global__ void __launch_bounds__(256) k_mask_bits(const uint16_t* m1, const uin
   const int y0 = blockIdx.y * kTileRows;
   const int wx = x >> 5;
   const int rows = min(kTileRows, H - y0);
-#pragma unroll 4
-  for (int r = 0; r < rows; ++r) {
-    bool bad = false;
-    if (x < W) {
-      const int64_t o = (int64_t)(y0 + r) * pitch + x;
-      uint16_t m = m1[o];
-      if (m2) m |= m2[o];
-      bad = (m & badmask) != 0;
+  for (int r0 = 0; r0 < rows; r0 += kBitsBatch) {
+    uint16_t m[kBitsBatch];
+#pragma unroll
+    for (int q = 0; q < kBitsBatch; ++q) {
+      m[q] = 0;
+      if (x < W && r0 + q < rows) {
+        const int64_t o = (int64_t)(y0 + r0 + q) * pitch + x;
+        m[q] = m1[o];
+        if (m2) m[q] |= m2[o];
+      }
     }
-    const uint32_t word = __ballot_sync(0xffffffffu, bad);
-    if ((threadIdx.x & 31) == 0 && wx < nwords) bits[(int64_t)(y0 + r) * nwords + wx] = word;
+#pragma unroll
+    for (int q = 0; q < kBitsBatch; ++q) {
+      if (r0 + q >= rows) break;  // uniform over the CTA
+      const uint32_t word = __ballot_sync(0xffffffffu, (m[q] & badmask) != 0);
+      if ((threadIdx.x & 31) == 0 && wx < nwords)
+        bits[(int64_t)(y0 + r0 + q) * nwords + wx] = word;
+    }
   }
 }
 
@@ -119,25 +130,41 @@ __global__ void __launch_bounds__(256) k_mask_out(const uint32_t* hb_bad, const 
   const uint32_t bit = 1u << (tid & 31);
   const int wc = tid >> 5;
   const int rows = min(kTileRows, H - y0);
-  for (int r = 0; r < rows; ++r) {
-    const int64_t o = (int64_t)(y0 + r) * pitch + x;
-    bool nb = (vbs[r][wc] & bit) != 0, np = (vps[r][wc] & bit) != 0;
-    if (mode == 1) {
-      out[o] = (uint16_t)((nb ? conv_bad : 0) | (np ? conv_poor : 0));
-      continue;
+  // kBitsBatch rows at a time, their mask (and previous output) loads issued first
+  for (int r0 = 0; r0 < rows; r0 += kBitsBatch) {
+    uint16_t mv[kBitsBatch], pv[kBitsBatch];
+#pragma unroll
+    for (int q = 0; q < kBitsBatch; ++q) {
+      mv[q] = 0;
+      pv[q] = 0;
+      if (r0 + q < rows && mode != 1) {
+        const int64_t o = (int64_t)(y0 + r0 + q) * pitch + x;
+        mv[q] = m1[o];
+        if (m2) mv[q] |= m2[o];
+        if (mode == 2) pv[q] = out[o];
+      }
     }
-    if (mode == 2) {
-      const uint16_t prev = out[o];
-      nb = nb || (prev & conv_bad);
-      np = np || (prev & conv_poor);
+#pragma unroll
+    for (int q = 0; q < kBitsBatch; ++q) {
+      const int r = r0 + q;
+      if (r >= rows) break;
+      const int64_t o = (int64_t)(y0 + r) * pitch + x;
+      bool nb = (vbs[r][wc] & bit) != 0, np = (vps[r][wc] & bit) != 0;
+      if (mode == 1) {
+        out[o] = (uint16_t)((nb ? conv_bad : 0) | (np ? conv_poor : 0));
+        continue;
+      }
+      if (mode == 2) {
+        nb = nb || (pv[q] & conv_bad);
+        np = np || (pv[q] & conv_poor);
+      }
+      uint16_t m = mv[q];
+      if (nb)
+        m |= conv_bad;
+      else if (np)
+        m |= conv_poor;
+      out[o] = m;
     }
-    uint16_t m = m1[o];
-    if (m2) m |= m2[o];
-    if (nb)
-      m |= conv_bad;
-    else if (np)
-      m |= conv_poor;
-    out[o] = m;
   }
 }
 

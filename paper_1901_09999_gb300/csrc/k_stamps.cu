@@ -57,20 +57,28 @@ __device__ __forceinline__ void warp_hist(uint32_t* h, bool valid, uint32_t bin)
 }
 
 // First pass: keys, bad bits and the histogram of the top 11 key bits.  Rows strided over the
-// grid, two rows per step with all their loads issued first, one pixel per thread
+// grid, kKeyRows rows per step with all their loads issued first, one pixel per thread
 // (warp-uniform trip count for the warp-wide votes).
+constexpr int kKeyRows = 2;
 __global__ void __launch_bounds__(256) k_median_keys(HistParams P) {
   __shared__ uint32_t h[2048];
   for (int i = threadIdx.x; i < 2048; i += blockDim.x) h[i] = 0;
   __syncthreads();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int wx = x >> 5;
-  for (int y = blockIdx.y; y < P.H; y += 2 * gridDim.y) {
-    const int yr[2] = {y, y + (int)gridDim.y};
-    float a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f};
-    uint16_t m[2] = {0, 0};
+  for (int y = blockIdx.y; y < P.H; y += kKeyRows * gridDim.y) {
+    int yr[kKeyRows];
+    float a[kKeyRows], b[kKeyRows];
+    uint16_t m[kKeyRows];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < kKeyRows; ++q) {
+      yr[q] = y + q * (int)gridDim.y;
+      a[q] = 0.f;
+      b[q] = 0.f;
+      m[q] = 0;
+    }
+#pragma unroll
+    for (int q = 0; q < kKeyRows; ++q) {
       if (x < P.W && yr[q] < P.H) {
         const int64_t o = (int64_t)yr[q] * P.pitch + x;
         m[q] = P.m1[o] | P.m2[o];
@@ -79,7 +87,7 @@ __global__ void __launch_bounds__(256) k_median_keys(HistParams P) {
       }
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < kKeyRows; ++q) {
       if (yr[q] >= P.H) break;  // uniform over the block
       bool valid = false, bad = false;
       uint32_t k = 0;
@@ -271,17 +279,25 @@ __device__ __forceinline__ bool above_threshold(const DetectParams& P, int x, in
   return (double)s - (double)medf > thr;
 }
 
-// Block 32 x 8 threads covering 32 x 16 pixels: each thread tests rows y and y + 8 (all loads
-// issued first); the pixels that pass are appended to the candidate list, one atomic per warp.
+// Block 32 x 8 threads covering 32 x (8 kDetRows) pixels: each thread tests rows y, y + 8, ...
+// (all loads issued first); the pixels that pass are appended to the candidate list, one
+// atomic per warp.
+constexpr int kDetRows = 4;
 __global__ void __launch_bounds__(256) k_detect(DetectParams P) {
   const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y0 = blockIdx.y * 16 + threadIdx.y;
+  const int y0 = blockIdx.y * (8 * kDetRows) + threadIdx.y;
   if (P.st->error) return;
   const float medf = fkey_inv(P.st->median_key);
-  uint32_t key[2] = {0u, 0u};
-  float v1[2] = {0.f, 0.f}, v2[2] = {0.f, 0.f};
+  uint32_t key[kDetRows];
+  float v1[kDetRows], v2[kDetRows];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < kDetRows; ++q) {
+    key[q] = 0u;
+    v1[q] = 0.f;
+    v2[q] = 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < kDetRows; ++q) {
     const int y = y0 + 8 * q;
     if (x < P.W && y < P.H) {
       const int64_t o = (int64_t)y * P.pitch + x;
@@ -292,7 +308,7 @@ __global__ void __launch_bounds__(256) k_detect(DetectParams P) {
   }
   const int lane = threadIdx.x;
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < kDetRows; ++q) {
     const int y = y0 + 8 * q;
     const bool pass = above_threshold(P, x, y, key[q], v1[q], v2[q], medf);
     const unsigned bal = __ballot_sync(0xffffffffu, pass);
@@ -494,7 +510,8 @@ cudaError_t launch_extract(const Plan& p, DevState* st, const SolveBuffers& b, c
   dp.over = b.over;
   dp.n_over = b.n_over;
   dp.over_cap = over_capacity(p);
-  k_detect<<<dim3((p.W + 31) / 32, (p.H + 15) / 16), dim3(32, 8), 0, s>>>(dp);
+  k_detect<<<dim3((p.W + 31) / 32, (p.H + 8 * kDetRows - 1) / (8 * kDetRows)), dim3(32, 8), 0, s>>>(
+      dp);
   k_detect_peaks<<<1216, 256, 0, s>>>(dp);
   k_rank_candidates<<<p.nreg, 256, 0, s>>>(b.bin_val, b.bin_idx, b.bin_cnt, p.W, p.max_cand,
                                           b.cand, b.cand_stat, b.cand_chi2, b.ptr, b.have);
