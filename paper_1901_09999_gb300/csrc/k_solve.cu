@@ -19,6 +19,7 @@
 // the raw separable convolutions and psi / s_k are applied when the system is assembled.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "dfloat.cuh"
@@ -1365,6 +1366,24 @@ __device__ __forceinline__ void basis_model(const double*, const float2* akf, co
   for (int j = 0; j < NPX; ++j) m[j] = df_to_d(df_norm(acc[j]));
 }
 
+// The double-float model sum_k a_k psi_k C_k at NPX pixels, left as a double-float.
+template <int NPX>
+__device__ __forceinline__ void basis_model_df(const float2* akf, const float2* C, int Nb, int P,
+                                               const int* pix, df* m) {
+#pragma unroll
+  for (int j = 0; j < NPX; ++j) m[j] = df{0.f, 0.f};
+#pragma unroll 8
+  for (int k = 0; k < Nb; ++k) {
+    const df a = {akf[k].x, akf[k].y};
+    float2 c[NPX];
+#pragma unroll
+    for (int j = 0; j < NPX; ++j)
+      c[j] = pix[j] >= 0 ? C[(int64_t)k * P + pix[j]] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < NPX; ++j) df_fma(m[j], a, df{c[j].x, c[j].y});
+  }
+}
+
 struct Chi2Params {
   StampParams sp;
   const double* gv;
@@ -1436,6 +1455,8 @@ __global__ void __launch_bounds__(kChi2Threads, 4) k_chi2(Chi2Params Q) {
   }
   __syncthreads();
   const double delta = s_delta, delta2 = s_delta2, d0 = Q.dsol[1];
+  const df dl = df_split(delta), dl2 = df_split(delta2), dd0 = df_split(d0);
+  const float alpha_f = (float)Q.alpha;
   const T* Cr = reinterpret_cast<const T*>(P.C) + (int64_t)r * Nd * P.P;
   double q = 0.0, n = 0.0;
   constexpr int kStride = kChi2Split * kChi2Threads * kChi2Px;
@@ -1458,18 +1479,51 @@ __global__ void __launch_bounds__(kChi2Threads, 4) k_chi2(Chi2Params Q) {
 #pragma unroll
     for (int j = 0; j < kChi2Px; ++j)
       mk[j] = pix[j] >= 0 ? (uint16_t)((P.m1[off[j]] | P.m2[off[j]]) & P.badmask) : (uint16_t)1;
-    double mod[kChi2Px];
-    basis_model<kChi2Px>(ak, akf, Cr, Nd, P.P, pix, mod);
+    if constexpr (std::is_same<T, float2>::value) {
+      // double-float blocks: the model and the residual in double-float on the FP32 pipes
+      // (the cancellation I2 - model is exact there), the residual's square over the softened
+      // variance in FP32 (one rounding per term); the pixel loads go out with the design loads
+      float R[kChi2Px], I2v[kChi2Px], Vs[kChi2Px];
 #pragma unroll
-    for (int j = 0; j < kChi2Px; ++j) {
-      if (mk[j]) continue;
-      const int64_t o = off[j];
-      const double R = P.i1[o], I2 = P.i2[o];
-      const double model = delta * R + delta2 * (Nd > Nb ? I2 : 0.0) + d0 + mod[j];
-      const double res = I2 - model;
-      const double den = ((double)P.v1[o] + (double)P.v2[o]) + Q.alpha * fabs(I2);
-      q += res * res / den;
-      n += 1.0;
+      for (int j = 0; j < kChi2Px; ++j) {
+        R[j] = 0.f;
+        I2v[j] = 0.f;
+        Vs[j] = 1.f;
+        if (pix[j] >= 0) {
+          R[j] = P.i1[off[j]];
+          I2v[j] = P.i2[off[j]];
+          Vs[j] = __fadd_rn(P.v1[off[j]], P.v2[off[j]]);
+        }
+      }
+      df mdf[kChi2Px];
+      basis_model_df<kChi2Px>(akf, Cr, Nd, P.P, pix, mdf);
+#pragma unroll
+      for (int j = 0; j < kChi2Px; ++j) {
+        if (mk[j]) continue;
+        df m = mdf[j];
+        df_fma_f(m, R[j], dl);
+        if (Nd > Nb) df_fma_f(m, I2v[j], dl2);
+        m = df_add(m, dd0);
+        const df res = df_add(df{I2v[j], 0.f}, df_neg(m));
+        const float r = __fadd_rn(res.hi, res.lo);
+        const float den = __fadd_rn(Vs[j], __fmul_rn(alpha_f, fabsf(I2v[j])));
+        q += (double)__fdiv_rn(__fmul_rn(r, r), den);
+        n += 1.0;
+      }
+    } else {
+      double mod[kChi2Px];
+      basis_model<kChi2Px>(ak, akf, Cr, Nd, P.P, pix, mod);
+#pragma unroll
+      for (int j = 0; j < kChi2Px; ++j) {
+        if (mk[j]) continue;
+        const int64_t o = off[j];
+        const double R = P.i1[o], I2 = P.i2[o];
+        const double model = delta * R + delta2 * (Nd > Nb ? I2 : 0.0) + d0 + mod[j];
+        const double res = I2 - model;
+        const double den = ((double)P.v1[o] + (double)P.v2[o]) + Q.alpha * fabs(I2);
+        q += res * res / den;
+        n += 1.0;
+      }
     }
   }
 #pragma unroll

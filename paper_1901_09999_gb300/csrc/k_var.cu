@@ -10,6 +10,7 @@
 // One CTA per patch: it realises K_t from the separable basis in FP32 (N_H w^2 FMAs per
 // patch), stages the variance tile with its halo, and each thread convolves a 16-row column
 // strip, one kernel column at a time, with the strip in registers.
+#include "dfloat.cuh"
 #include "psfm_internal.h"
 
 namespace psfm {
@@ -44,6 +45,16 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+__device__ __forceinline__ double warp_sum_f(float x) {
+  df v = {x, 0.f};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const df u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = df_add(v, u);
+  }
+  return df_to_d(v);
 }
 
 template <int HW>
@@ -208,9 +219,11 @@ __global__ void __launch_bounds__(256) k_variance(VarParams P) {
     }
   }
   if (P.want_stats) {
-    const double s_conv = warp_sum((double)t_conv);
-    const double s_img = warp_sum((double)t_img);
-    const double s_n = warp_sum((double)t_n);
+    // warp sums of the FP32 partials in double-float on the FP32 pipes (exact for these
+    // 32-term sums, as FP64 would be, without the FP64 pipe's 1/64 rate), then FP64
+    const double s_conv = warp_sum_f(t_conv);
+    const double s_img = warp_sum_f(t_img);
+    const double s_n = (double)__reduce_add_sync(0xffffffffu, (unsigned)t_n);
     if ((tid & 31) == 0) {
       red[tid >> 5][0] = s_conv;
       red[tid >> 5][1] = s_img;
