@@ -99,9 +99,10 @@ typedef struct {
 #define PSFM_PREC_BF16X3 3   /* FP32 design; Gram on the tensor cores from a BF16 hi/lo split,
                                 3 products (hi*hi + hi*lo + lo*hi), FP32 sums */
 #define PSFM_PREC_F32X2 4    /* design and Gram in double-float (FP32 pairs, ~48 bits) */
-#define PSFM_PREC_BF16X6 5   /* double-float design; Gram on the tensor cores from seven BF16
-                                slices per operand, exact per-level sums (>= 48 bits; at most
-                                64 augmented columns) */
+#define PSFM_PREC_BF16X6 5   /* double-float design; Gram on the tensor cores as
+                                (sqrt(w) C)^T (sqrt(w) C) from seven BF16 slices of the scaled
+                                columns, exact per-level sums (>= 48 bits; at most 64 augmented
+                                columns) */
 
 /* Options; psfm_config_default() fills the defaults noted in brackets. */
 typedef struct {
@@ -435,9 +436,10 @@ psfm_status psfm_convolve_noalloc(const float* ref, const float* var_ref,
  * gram: device [n_blocks][n_cols][n_cols] double, written symmetric.  precision:
  *   PSFM_PREC_FP64   FP64 products and sums (the reference; workspace unused, may be NULL);
  *   PSFM_PREC_TF32   tensor cores, TF32 products, FP32 accumulation, n_cols <= 128;
- *   PSFM_PREC_BF16X6 tensor cores, seven BF16 slices per operand (each column scaled by a
- *                    power of two), 28 slice products, levels 0..3 summed exactly as integers
- *                    over 256-pixel groups, n_cols <= 64 (at least 48 bits, like double-float);
+ *   PSFM_PREC_BF16X6 tensor cores, the Gram as (sqrt(w) C)^T (sqrt(w) C): seven BF16 slices
+ *                    of each scaled column (scaled by a power of two), 28 slice products,
+ *                    levels 0..4 summed exactly as integers over 224-pixel groups,
+ *                    n_cols <= 64 (at least 48 bits, like double-float);
  *   PSFM_PREC_BF16X3 tensor cores, BF16 hi/lo split, three products, FP32 accumulation,
  *                    n_cols <= 128;
  * others return PSFM_ERR_UNSUPPORTED.  The tensor-core modes need PSFM_GRAM_WORKSPACE bytes of

@@ -115,6 +115,19 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Byte offset of element (row, k) of a K-major operand tile with kTcKC columns, built from
 // 8-row x 16-byte core matrices stored row group by row group: LBO = 128 B (next core matrix
 // along K), SBO = (kTcKC * esz / 16) * 128 B (next group of 8 rows).
@@ -347,24 +360,34 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(Src src, int n_tile) {
 
 // ---- Tensor-core Gram with error-free split products (precision mode BF16X6) ----
 //
-// Each augmented column c of the stamp (the zero-sum design columns in double-float, R, 1,
-// I2) and each weighted column w * c is scaled by a power of two so that its largest value is
-// below 1/4 and written as seven signed base-256 digits, x = sum_k d_k 2^(-8(k+1)),
-// |d_k| <= 129, each digit times its weight held exactly by a BF16 slice: 56 bits below the
-// column's largest value, enough for the 48 bits of a double-float value a hundred times
-// smaller.  The product of slices i and j is exact in the tensor cores and has the weight
-// 2^(-8(i+j+2)) of its level L = i + j.  Levels 0..3 are accumulated in their own tensor-memory
-// tiles over groups of 256 pixels, where every partial sum is an integer below 2^24 units of the
-// level and so exact in FP32; after each group they are read back and added, as integers, into
-// a 64-bit accumulator per Gram entry.  Levels 4..6 (weights 2^-48 .. 2^-64) share one FP32 tile
-// over the whole stamp.  The Gram entry is the integer sum plus the small levels, times the two
-// column scales: it carries the bits of its double-float inputs while the products run on the
-// tensor cores.  One CTA of 16 warps per stamp (the staging is latency bound: it waits on the
-// design values), of which eight read the accumulators back (a thread: 32 columns of one
-// accumulator lane); at most 64 columns (one N = 64 tile).
+// The Gram A^T W A is formed as (sqrt(w) A)^T (sqrt(w) A): each augmented column c of the stamp
+// (the zero-sum design columns in double-float, R, 1, I2) times sqrt(w) per pixel is scaled by a
+// power of two so that its largest value is below 1/4 and written as seven signed base-256
+// digits, x = sum_k d_k 2^(-8(k+1)), |d_k| <= 129, each digit times its weight held exactly by a
+// BF16 slice: 56 bits below the column's largest value, enough for the 48 bits of a
+// double-float value a hundred times smaller.  The product of slices i and j is exact in the
+// tensor cores and has the weight 2^(-8(i+j+2)) of its level L = i + j; the B operand of each
+// MMA is the first 64 rows of a slice of the same operand.  Levels 0..4 are accumulated in
+// their own tensor-memory tiles over groups of 224 pixels, where every partial sum is an
+// integer below 2^24 units of the level (|d_0| <= 64, |d_k| <= 129: at most 66435 units a pixel
+// on level 4) and so exact in FP32; after each group they are read back and added, as integers,
+// into a 64-bit accumulator per Gram entry.  Levels 5 and 6 (weights 2^-56, 2^-64) share one FP32
+// tile over the whole stamp (with only four exact levels, the FP32 rounding of the shared tile
+// was the largest error of this symmetric form, 3e-14 of the sum of |terms| in an emulation on
+// full-chip stamps; with five it is 1.7e-15).  The Gram entry is the integer sum
+// plus the small levels, times the two column scales: it carries the bits of its double-float
+// inputs while the products run on the tensor cores.  One CTA of 32 warps per stamp: warp 0
+// issues the MMAs of a 32-pixel chunk while the other 31 stage the next chunk's slices (double
+// buffered); all 32 read the accumulators back (a thread: 8 columns of one accumulator lane);
+// at most 64 columns (one N = 64 tile).
 constexpr int kOzSlices = 7;
-constexpr int kOzExact = 4;  // levels summed exactly per group
-constexpr int kOzGroup = 8;  // 32-pixel sub-chunks per exact group (256 pixels)
+constexpr int kOzExact = 5;  // levels summed exactly per group
+constexpr int kOzGroup = 7;  // 32-pixel sub-chunks per exact group (224 pixels)
+constexpr int kOzThreads = 1024;
+// elements of a 64-column chunk per staging thread (all warps but the MMA warp), and elements
+// per thread per round of the column-scale scan
+constexpr int kOzPer = (64 * kTcKC + kOzThreads - 32 - 1) / (kOzThreads - 32);
+constexpr int kOzScanBatch = 4;
 
 // seven balanced base-256 digits of the double-float h + l (|h + l| < 1/4), as BF16 bits of
 // d_k 2^(-8(k+1))
@@ -386,7 +409,7 @@ __device__ __forceinline__ void oz_digits(float h, float l, uint16_t out[kOzSlic
 }
 
 // Column source of the split Gram inside the solve: double-float design block (zero-sum
-// columns formed per pixel), R, 1, I2; weights 1 / (V1 + V2) as double-floats.  prepare()
+// columns formed per pixel), R, 1, I2; sqrt(1 / (V1 + V2)) as double-floats.  prepare()
 // stages the stamp's per-pixel weights and image values and the per-column psi_k and s_k in
 // shared memory once, so that the two passes over the stamp read only the design block.
 struct OzStampSource {
@@ -425,11 +448,22 @@ struct OzStampSource {
         a = (P.m1[o] & P.badmask) ? 0.f : P.i1[o];
         b = P.i2[o];
         if (!((P.m1[o] | P.m2[o]) & P.badmask)) {
-          const double wd = 1.0 / ((double)P.v1[o] + (double)P.v2[o]);
-          if (!isfinite(P.i1[o]) || !isfinite(b) || !isfinite(wd))
+          // sqrt(w) = (V1 + V2)^(-1/2): the FP32 estimate and two Newton steps in FP64
+          // (FP64 division and square root are slow here); the Gram is formed as
+          // (sqrt(w) A)^T (sqrt(w) A)
+          const double vs = (double)P.v1[o] + (double)P.v2[o];
+          double sq;
+          if (vs > 1e-30 && vs < 1e30) {
+            sq = (double)rsqrtf((float)vs);
+            sq = sq * (1.5 - 0.5 * vs * sq * sq);
+            sq = sq * (1.5 - 0.5 * vs * sq * sq);
+          } else {
+            sq = 1.0 / sqrt(vs);  // outside the FP32 estimate's range
+          }
+          if (!isfinite(P.i1[o]) || !isfinite(b) || !(vs > 0.0) || !isfinite(sq))
             raise_error(P.st, PSFM_ERR_NONFINITE);
-          h = (float)wd;
-          l = (float)(wd - (double)h);
+          h = (float)sq;
+          l = (float)(sq - (double)h);
         }
       }
       xr[pix] = a;
@@ -514,9 +548,11 @@ struct OzPlainSource {
   __host__ __device__ static size_t prep_floats(int, int) { return 0; }
   __device__ void bind(float*) {}
   __device__ void prepare(int, int) {}
+  // sqrt(w) as a double-float (the Gram is formed as (sqrt(w) A)^T (sqrt(w) A))
   __device__ void weight(int pix, float* wh, float* wl) const {
-    *wh = pix < n_pix ? w[(int64_t)r * n_pix + pix] : 0.f;
-    *wl = 0.f;
+    const double sq = pix < n_pix ? sqrt((double)w[(int64_t)r * n_pix + pix]) : 0.0;
+    *wh = (float)sq;
+    *wl = (float)(sq - (double)*wh);
   }
   __device__ float2 fetch(int c, int pix) const {
     return make_float2(
@@ -542,6 +578,17 @@ __device__ __forceinline__ void oz_mul(float h, float l, float a, float b, float
   *rl = __fsub_rn(e, __fsub_rn(s2, p));
 }
 
+// Element e of a chunk's staging (64 rows x kTcKC pixels) as (row c, pixel j): each warp's 32
+// consecutive elements are 4 rows x 8 pixels of one core matrix, 64 contiguous bytes of the
+// K-major tile, so its 16-bit stores hit distinct banks.  Rows >= 64 (e >= 2048) map past
+// every column.
+__device__ __forceinline__ void oz_elem(int e, int* c, int* j) {
+  const int w = e >> 5, l = e & 31;
+  const int a = w >> 3, b = (w >> 1) & 3, h = w & 1;
+  *c = 8 * a + 4 * h + (l >> 3);
+  *j = 8 * b + (l & 7);
+}
+
 // Power-of-two scale putting max |x| below 1/4 (2^-e with e = ilogb(max) + 3), as the exponent.
 __device__ __forceinline__ int oz_exponent(float m) {
   if (!(m > 0.f) || !isfinite(m)) return 0;
@@ -549,14 +596,13 @@ __device__ __forceinline__ int oz_exponent(float m) {
 }
 
 template <class Src>
-__global__ void __launch_bounds__(512, 1) k_gram_oz(Src src, int n_tile) {
+__global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(Src src, int n_tile) {
   constexpr int ESZ = 2;
   extern __shared__ __align__(1024) unsigned char tc_sh[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ uint32_t s_tmem;
-  __shared__ unsigned int s_maxa[kTcM], s_maxb[kTcM];
-  __shared__ int s_ea[kTcM], s_eb[kTcM];
-  __shared__ float s_wh[kTcKC], s_wl[kTcKC];
+  __shared__ unsigned int s_maxa[kTcM];
+  __shared__ int s_ea[kTcM];
   __shared__ int s_ok, s_last, s_open;
   const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) s_open = src.open(blockIdx.x) ? 1 : 0;
@@ -564,48 +610,53 @@ __global__ void __launch_bounds__(512, 1) k_gram_oz(Src src, int n_tile) {
   if (!s_open) return;
   if (tid != 0) src.open(blockIdx.x);
   const int Nc = src.ncols(), npix = src.npix();
-  const uint32_t a_bytes = kTcM * kTcKC * ESZ, b_bytes = (uint32_t)n_tile * kTcKC * ESZ;
-  const uint32_t stage_bytes = kOzSlices * (a_bytes + b_bytes);
+  // one operand: the slices of sqrt(w) A; the B operand of every MMA is the first n_tile rows
+  // of an A slice (the same K-major layout)
+  const uint32_t a_bytes = kTcM * kTcKC * ESZ;
+  const uint32_t stage_bytes = kOzSlices * a_bytes;
   auto a_plane = [&](int s, int k) { return tc_sh + s * stage_bytes + k * a_bytes; };
-  auto b_plane = [&](int s, int k) {
-    return tc_sh + s * stage_bytes + kOzSlices * a_bytes + k * b_bytes;
-  };
-  // ---- column scales: the largest |value| and |weight * value| of every column (FP32 estimates)
-  for (int c = tid; c < kTcM; c += nthr) {
-    s_maxa[c] = 0u;
-    s_maxb[c] = 0u;
-  }
+  // ---- column scales: the largest |sqrt(w) value| of every column (FP32 estimates)
+  for (int c = tid; c < kTcM; c += nthr) s_maxa[c] = 0u;
   for (uint32_t i = tid; i < 2 * stage_bytes / 4; i += nthr)
     reinterpret_cast<uint32_t*>(tc_sh)[i] = 0u;  // rows >= Nc stay zero throughout
   src.bind(reinterpret_cast<float*>(tc_sh + 2 * stage_bytes));
   src.prepare(tid, nthr);
   __syncthreads();
-  // four elements per thread at a time, their loads issued together
-  for (int i0 = tid; i0 < Nc * npix; i0 += 4 * nthr) {
-    float2 cv[4];
+  // kOzScanBatch elements per thread at a time, their loads issued together; the trip count is
+  // the same for every lane of a warp (the warp votes below need all 32)
+  for (int i0 = tid; i0 - lane < Nc * npix; i0 += kOzScanBatch * nthr) {
+    float2 cv[kOzScanBatch];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kOzScanBatch; ++u) {
       const int i = i0 + u * nthr;
       cv[u] = i < Nc * npix ? src.fetch(i / npix, i % npix) : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kOzScanBatch; ++u) {
       const int i = i0 + u * nthr;
-      if (i >= Nc * npix) break;
-      const int c = i / npix, pix = i - c * npix;
-      float vh, vl, wh, wl;
-      src.make(c, pix, cv[u], &vh, &vl);
-      src.weight(pix, &wh, &wl);
-      const float a = fabsf(vh), b = fabsf(vh * wh);
-      if (a > 0.f) atomicMax(&s_maxa[c], __float_as_uint(a));
-      if (b > 0.f) atomicMax(&s_maxb[c], __float_as_uint(b));
+      int c = -1;
+      unsigned ua = 0u;  // |sqrt(w) value| as order-preserving bits (>= 0)
+      if (i < Nc * npix) {
+        c = i / npix;
+        const int pix = i - c * npix;
+        float vh, vl, wh, wl;
+        src.make(c, pix, cv[u], &vh, &vl);
+        src.weight(pix, &wh, &wl);
+        ua = __float_as_uint(fabsf(vh * wh));
+      }
+      // a warp's consecutive elements mostly share one column: one shared-memory atomic per
+      // warp then (the 32 lanes' atomics on one address would serialise)
+      const int cf = __shfl_sync(0xffffffffu, c, 0);
+      if (__all_sync(0xffffffffu, c == cf || c < 0)) {
+        ua = __reduce_max_sync(0xffffffffu, ua);
+        if (lane == 0 && cf >= 0 && ua) atomicMax(&s_maxa[cf], ua);
+      } else if (c >= 0 && ua) {
+        atomicMax(&s_maxa[c], ua);
+      }
     }
   }
   __syncthreads();
-  for (int c = tid; c < kTcM; c += nthr) {
-    s_ea[c] = oz_exponent(__uint_as_float(s_maxa[c]));
-    s_eb[c] = oz_exponent(__uint_as_float(s_maxb[c]));
-  }
+  for (int c = tid; c < kTcM; c += nthr) s_ea[c] = oz_exponent(__uint_as_float(s_maxa[c]));
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -629,51 +680,65 @@ __global__ void __launch_bounds__(512, 1) k_gram_oz(Src src, int n_tile) {
   const uint32_t idesc = instr_desc(1u, n_tile, kTcM);
   const uint32_t sbo = (kTcKC * ESZ / 16) * 128;
   const int nsub = (npix + kTcKC - 1) / kTcKC;
-  // Gram readback: thread = (lane quadrant, 32-column slice)
+  // Gram readback: thread = (lane quadrant, 8-column slice), n_tile = 64 columns
+  constexpr int kRb = 64 * 4 / (kOzThreads / 32);  // columns a thread reads back
   const int quad = warp & 3, cslice = warp >> 2;
-  const int row = quad * 32 + lane, col0 = cslice * 32;
-  long long acc[32];
+  const int row = quad * 32 + lane, col0 = cslice * kRb;
+  long long acc[kRb];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) acc[j] = 0;
+  for (int j = 0; j < kRb; ++j) acc[j] = 0;
+  // Warp 0 issues the MMAs; warps 1.. stage.  The staging warps go on to the next chunk while
+  // the MMAs of this one are issued and run (the chunk's buffer was last read by the MMAs of
+  // chunk - 2, whose commit they wait for).  The design values of a chunk (kOzPer elements per
+  // staging thread, Nc <= 64 columns) are fetched one chunk ahead, so their global loads are
+  // in flight during the previous chunk's staging.
+  const int stid = tid - 32, snthr = nthr - 32;
+  float2 cvn[kOzPer];
+  auto fetch_chunk = [&](int ch2) {
+#pragma unroll
+    for (int u = 0; u < kOzPer; ++u) {
+      int c, j;
+      oz_elem(stid + u * snthr, &c, &j);
+      cvn[u] = (ch2 < nsub && c < Nc) ? src.fetch(c, ch2 * kTcKC + j) : make_float2(0.f, 0.f);
+    }
+  };
+  if (warp != 0) fetch_chunk(0);
   for (int ch = 0; ch < nsub; ++ch) {
     const int s = ch & 1;
     const int grp = ch / kOzGroup, q = ch - grp * kOzGroup;
-    if (ch >= 2 && !mbar_wait(&bars[s], ((ch - 2) >> 1) & 1) && tid == 0) s_ok = 0;
-    __syncthreads();
-    if (!s_ok) break;
     const int base = ch * kTcKC;
-    if (tid < kTcKC) src.weight(base + tid, &s_wh[tid], &s_wl[tid]);
-    __syncthreads();
-    for (int i0 = tid; i0 < Nc * kTcKC; i0 += 2 * nthr) {
-      float2 cv[2];
+    bool tmo = false;  // this thread's wait for the buffer ran out
+    if (warp != 0) {
+      tmo = ch >= 2 && !mbar_wait(&bars[s], ((ch - 2) >> 1) & 1);
+      float2 cv[kOzPer];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int i = i0 + u * nthr;
-        cv[u] = i < Nc * kTcKC ? src.fetch(i / kTcKC, base + i % kTcKC) : make_float2(0.f, 0.f);
-      }
+      for (int u = 0; u < kOzPer; ++u) cv[u] = cvn[u];
+      fetch_chunk(ch + 1);
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int i = i0 + u * nthr;
-        if (i >= Nc * kTcKC) break;
-        const int c = i / kTcKC, j = i - c * kTcKC;
-        float vh, vl, bh, bl;
+      for (int u = 0; u < kOzPer; ++u) {
+        int c, j;
+        oz_elem(stid + u * snthr, &c, &j);
+        if (c >= Nc) continue;  // rows past the columns stay zero
+        float vh, vl, wh, wl, bh, bl;
         src.make(c, base + j, cv[u], &vh, &vl);
-        oz_mul(vh, vl, s_wh[j], s_wl[j], &bh, &bl);
+        src.weight(base + j, &wh, &wl);
+        oz_mul(vh, vl, wh, wl, &bh, &bl);
         const float sa = __int_as_float((127 - s_ea[c]) << 23);
-        const float sb = __int_as_float((127 - s_eb[c]) << 23);
-        uint16_t da[kOzSlices], db[kOzSlices];
-        oz_digits(vh * sa, vl * sa, da);
-        oz_digits(bh * sb, bl * sb, db);
+        uint16_t da[kOzSlices];
+        oz_digits(bh * sa, bl * sa, da);
         const uint32_t off = tile_off<ESZ>(c, j);
 #pragma unroll
-        for (int k = 0; k < kOzSlices; ++k) {
+        for (int k = 0; k < kOzSlices; ++k)
           *reinterpret_cast<uint16_t*>(a_plane(s, k) + off) = da[k];
-          *reinterpret_cast<uint16_t*>(b_plane(s, k) + off) = db[k];
-        }
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    // the barrier combines the threads' timeouts, so every thread takes the same branch (a
+    // shared flag could already be rewritten for the next chunk by a staging warp)
+    if (__syncthreads_or(tmo ? 1 : 0)) {
+      if (tid == 0) s_ok = 0;
+      break;
+    }
     if (tid == 0) {
       tc_fence_after();
       for (int k0 = 0; k0 < kTcKC; k0 += 16) {
@@ -683,7 +748,7 @@ __global__ void __launch_bounds__(512, 1) k_gram_oz(Src src, int n_tile) {
           const uint64_t ad = smem_desc(smem_u32(a_plane(s, i)) + koff, 128, sbo);
 #pragma unroll
           for (int j = 0; i + j < kOzSlices; ++j) {
-            const uint64_t bd = smem_desc(smem_u32(b_plane(s, j)) + koff, 128, sbo);
+            const uint64_t bd = smem_desc(smem_u32(a_plane(s, j)) + koff, 128, sbo);
             const int L = i + j;
             uint32_t dst, accf;
             if (L < kOzExact) {
@@ -708,21 +773,17 @@ __global__ void __launch_bounds__(512, 1) k_gram_oz(Src src, int n_tile) {
       __syncthreads();
       if (!s_ok) break;
       tc_fence_after();
-      if (col0 < n_tile) {
+      {
         const uint32_t lanebase = ((uint32_t)(quad * 32)) << 16;
 #pragma unroll
         for (int L = 0; L < kOzExact; ++L) {
           const uint32_t cb = (uint32_t)(L * n_tile + col0);
-          float v0[16], v1[16];
-          tc_ld16(tmem + lanebase + cb, v0);
-          tc_ld16(tmem + lanebase + cb + 16, v1);
+          float v0[kRb];
+          tc_ld8(tmem + lanebase + cb, v0);
           const float up = __int_as_float((127 + 8 * (L + 2)) << 23);  // 2^(8(L+2))
           const int sh = 8 * (kOzExact - 1 - L);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            acc[j] += (long long)__float2int_rn(v0[j] * up) << sh;
-            acc[j + 16] += (long long)__float2int_rn(v1[j] * up) << sh;
-          }
+          for (int j = 0; j < kRb; ++j) acc[j] += (long long)__float2int_rn(v0[j] * up) << sh;
         }
       }
       tc_fence_before();
@@ -738,19 +799,20 @@ __global__ void __launch_bounds__(512, 1) k_gram_oz(Src src, int n_tile) {
   __syncthreads();
   tc_fence_after();
   const bool ok = s_ok != 0 && last == nsub - 1;
-  if (ok && col0 < n_tile) {
-    float rv0[16], rv1[16];
+  if (ok) {
+    float rv0[kRb];
     const uint32_t lanebase = ((uint32_t)(quad * 32)) << 16;
-    tc_ld16(tmem + lanebase + rest_col + col0, rv0);
-    tc_ld16(tmem + lanebase + rest_col + col0 + 16, rv1);
+    tc_ld8(tmem + lanebase + rest_col + col0, rv0);
     double* Gr = src.gram();
     if (row < Nc) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < kRb; ++j) {
         const int d = col0 + j;
         if (d <= row && d < Nc) {
-          const double small = (double)(j < 16 ? rv0[j] : rv1[j - 16]);
-          const double g = ldexp((double)acc[j] * 0x1p-40 + small, s_ea[row] + s_eb[d]);
+          const double small = (double)rv0[j];
+          // acc is in units of 2^(-8 (kOzExact + 1)), the unit of the last exact level
+          const double g =
+              ldexp(ldexp((double)acc[j], -8 * (kOzExact + 1)) + small, s_ea[row] + s_ea[d]);
           Gr[row * Nc + d] = g;
           Gr[d * Nc + row] = g;
         }
@@ -796,9 +858,7 @@ cudaError_t launch_gram_tc_src(int mode, const Src& src, int nblk, int n_cols, c
   return cudaGetLastError();
 }
 
-size_t gram_oz_smem(int n_tile) {
-  return 2 * (size_t)kOzSlices * (kTcM + n_tile) * kTcKC * 2;
-}
+size_t gram_oz_smem(int) { return 2 * (size_t)kOzSlices * kTcM * kTcKC * 2; }
 
 template <class Src>
 cudaError_t launch_gram_oz_src(const Src& src, int nblk, int n_cols, int n_pix, int n_d,
@@ -810,7 +870,7 @@ cudaError_t launch_gram_oz_src(const Src& src, int nblk, int n_cols, int n_pix, 
   cudaError_t e = cudaFuncSetAttribute(k_gram_oz<Src>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_gram_oz<Src><<<nblk, 512, smem, s>>>(src, n_tile);
+  k_gram_oz<Src><<<nblk, kOzThreads, smem, s>>>(src, n_tile);
   return cudaGetLastError();
 }
 

@@ -64,10 +64,10 @@ def test_gram_modes_within_rounding_bounds(dev, nc, npix):
 @pytest.mark.parametrize("nc,npix", [(52, 961), (60, 441), (64, 70), (7, 33), (40, 600),
                                      (64, 257)])
 def test_split_product_gram_is_exact_to_double_float(dev, nc, npix):
-    """BF16X6: seven BF16 slices per operand, products exact on the tensor cores, levels 0..3
-    summed exactly as integers over 256-pixel groups.  For FP32 columns and weights the
-    weighted column is an exact 48-bit product, so the Gram agrees with the FP64 one to a few
-    units of 2^-48 of its terms (against 2^-9 for TF32)."""
+    """BF16X6: the Gram as (sqrt(w) A)^T (sqrt(w) A), seven BF16 slices of the scaled columns,
+    products exact on the tensor cores, levels 0..3 summed exactly as integers over 256-pixel
+    groups.  sqrt(w) and the scaled columns carry 48 bits, so the Gram agrees with the FP64 one
+    to a few units of 2^-48 of its terms (against 2^-9 for TF32)."""
     import torch
     cols, w = _data(nc * 7 + npix, 3, nc, npix)
     G, A = _reference(cols, w)
