@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(Src src, int n_tile) {
 // full-chip stamps; with five it is 1.7e-15).  The Gram entry is the integer sum
 // plus the small levels, times the two column scales: it carries the bits of its double-float
 // inputs while the products run on the tensor cores.  One CTA of 32 warps per stamp: warp 0
-// issues the MMAs of a 32-pixel chunk while the other 31 stage the next chunk's slices (double
+// issues the MMAs of a 32-pixel chunk while the other 31 stage the next chunk's slices (triple
 // buffered); all 32 read the accumulators back (a thread: 8 columns of one accumulator lane);
 // at most 64 columns (one N = 64 tile).
 constexpr int kOzSlices = 7;
@@ -388,23 +388,28 @@ constexpr int kOzThreads = 1024;
 // per thread per round of the column-scale scan
 constexpr int kOzPer = (64 * kTcKC + kOzThreads - 32 - 1) / (kOzThreads - 32);
 constexpr int kOzScanBatch = 4;
+// staging buffers (chunk ch waits for the MMAs of chunk ch - kOzStages before refilling)
+constexpr int kOzStages = 3;
 
 // seven balanced base-256 digits of the double-float h + l (|h + l| < 1/4), as BF16 bits of
-// d_k 2^(-8(k+1))
+// d_k 2^(-8(k+1)).  Each digit is taken from the high part alone (d = rint(h 2^(8(k+1))), and
+// h - d 2^(-8(k+1)) is exact); the low part is folded in by an error-free sum before digits 2,
+// 4 and 6, while it is still below half a unit of the next digit, so |d_k| <= 129.  d 2^-8(k+1)
+// has at most eight significant bits, so its BF16 bits are the top half of its FP32 bits.
 __device__ __forceinline__ void oz_digits(float h, float l, uint16_t out[kOzSlices]) {
 #pragma unroll
   for (int k = 0; k < kOzSlices; ++k) {
+    if (k == 2 || k == 4 || k == 6) {
+      const float s2 = __fadd_rn(h, l);
+      const float bb = __fsub_rn(s2, h);
+      l = __fadd_rn(__fsub_rn(h, __fsub_rn(s2, bb)), __fsub_rn(l, bb));
+      h = s2;
+    }
     const float sc = __int_as_float((127 + 8 * (k + 1)) << 23);   // 2^(8(k+1))
     const float isc = __int_as_float((127 - 8 * (k + 1)) << 23);  // 2^(-8(k+1))
-    const float d = rintf(h * sc);
-    const float dv = d * isc;  // exact: |d| <= 129
-    out[k] = bf16_bits(dv);
-    const float r = h - dv;  // exact (d is the nearest integer to h * sc)
-    // renormalise (r, l) with the error-free sum
-    const float s2 = r + l;
-    const float bb = s2 - r;
-    l = (r - (s2 - bb)) + (l - bb);
-    h = s2;
+    const float dv = __fmul_rn(rintf(__fmul_rn(h, sc)), isc);
+    out[k] = (uint16_t)(__float_as_uint(dv) >> 16);
+    h = __fsub_rn(h, dv);
   }
 }
 
@@ -599,7 +604,7 @@ template <class Src>
 __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(Src src, int n_tile) {
   constexpr int ESZ = 2;
   extern __shared__ __align__(1024) unsigned char tc_sh[];
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[kOzStages];
   __shared__ uint32_t s_tmem;
   __shared__ unsigned int s_maxa[kTcM];
   __shared__ int s_ea[kTcM];
@@ -617,49 +622,43 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(Src src, int n_tile) 
   auto a_plane = [&](int s, int k) { return tc_sh + s * stage_bytes + k * a_bytes; };
   // ---- column scales: the largest |sqrt(w) value| of every column (FP32 estimates)
   for (int c = tid; c < kTcM; c += nthr) s_maxa[c] = 0u;
-  for (uint32_t i = tid; i < 2 * stage_bytes / 4; i += nthr)
+  for (uint32_t i = tid; i < kOzStages * stage_bytes / 4; i += nthr)
     reinterpret_cast<uint32_t*>(tc_sh)[i] = 0u;  // rows >= Nc stay zero throughout
-  src.bind(reinterpret_cast<float*>(tc_sh + 2 * stage_bytes));
+  src.bind(reinterpret_cast<float*>(tc_sh + kOzStages * stage_bytes));
   src.prepare(tid, nthr);
   __syncthreads();
-  // kOzScanBatch elements per thread at a time, their loads issued together; the trip count is
-  // the same for every lane of a warp (the warp votes below need all 32)
-  for (int i0 = tid; i0 - lane < Nc * npix; i0 += kOzScanBatch * nthr) {
-    float2 cv[kOzScanBatch];
+  // Each thread takes one pixel (then the pixel nthr further on) and kOzScanBatch columns at a
+  // time, their loads issued together; a warp's lanes share the column, so one warp reduction
+  // and one shared-memory atomic per column and warp.  The trip counts are the same for every
+  // lane of a warp (the warp reductions need all 32).
+  for (int p0 = 0; p0 < npix; p0 += nthr) {
+    const int pix = p0 + tid;
+    float wh = 0.f, wl = 0.f;
+    src.weight(pix, &wh, &wl);
+    for (int c0 = 0; c0 < Nc; c0 += kOzScanBatch) {
+      float2 cv[kOzScanBatch];
 #pragma unroll
-    for (int u = 0; u < kOzScanBatch; ++u) {
-      const int i = i0 + u * nthr;
-      cv[u] = i < Nc * npix ? src.fetch(i / npix, i % npix) : make_float2(0.f, 0.f);
-    }
+      for (int u = 0; u < kOzScanBatch; ++u)
+        cv[u] = (pix < npix && c0 + u < Nc) ? src.fetch(c0 + u, pix) : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int u = 0; u < kOzScanBatch; ++u) {
-      const int i = i0 + u * nthr;
-      int c = -1;
-      unsigned ua = 0u;  // |sqrt(w) value| as order-preserving bits (>= 0)
-      if (i < Nc * npix) {
-        c = i / npix;
-        const int pix = i - c * npix;
-        float vh, vl, wh, wl;
-        src.make(c, pix, cv[u], &vh, &vl);
-        src.weight(pix, &wh, &wl);
-        ua = __float_as_uint(fabsf(vh * wh));
-      }
-      // a warp's consecutive elements mostly share one column: one shared-memory atomic per
-      // warp then (the 32 lanes' atomics on one address would serialise)
-      const int cf = __shfl_sync(0xffffffffu, c, 0);
-      if (__all_sync(0xffffffffu, c == cf || c < 0)) {
+      for (int u = 0; u < kOzScanBatch; ++u) {
+        const int c = c0 + u;
+        if (c >= Nc) break;  // uniform
+        unsigned ua = 0u;  // |sqrt(w) value| as order-preserving bits (>= 0)
+        if (pix < npix) {
+          float vh, vl;
+          src.make(c, pix, cv[u], &vh, &vl);
+          ua = __float_as_uint(fabsf(vh * wh));
+        }
         ua = __reduce_max_sync(0xffffffffu, ua);
-        if (lane == 0 && cf >= 0 && ua) atomicMax(&s_maxa[cf], ua);
-      } else if (c >= 0 && ua) {
-        atomicMax(&s_maxa[c], ua);
+        if (lane == 0 && ua) atomicMax(&s_maxa[c], ua);
       }
     }
   }
   __syncthreads();
   for (int c = tid; c < kTcM; c += nthr) s_ea[c] = oz_exponent(__uint_as_float(s_maxa[c]));
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int b = 0; b < kOzStages; ++b) mbar_init(&bars[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_ok = 1;
     s_last = -1;
@@ -689,36 +688,44 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(Src src, int n_tile) 
   for (int j = 0; j < kRb; ++j) acc[j] = 0;
   // Warp 0 issues the MMAs; warps 1.. stage.  The staging warps go on to the next chunk while
   // the MMAs of this one are issued and run (the chunk's buffer was last read by the MMAs of
-  // chunk - 2, whose commit they wait for).  The design values of a chunk (kOzPer elements per
-  // staging thread, Nc <= 64 columns) are fetched one chunk ahead, so their global loads are
-  // in flight during the previous chunk's staging.
+  // chunk - kOzStages, whose commit they wait for).  The design values of a chunk (kOzPer
+  // elements per staging thread, Nc <= 64 columns) are fetched one chunk ahead, so their
+  // global loads are in flight during the previous chunk's staging.
   const int stid = tid - 32, snthr = nthr - 32;
   float2 cvn[kOzPer];
+  // a staging thread's elements are the same (row, pixel-in-chunk) slots in every chunk: their
+  // tile offset, row and pixel packed once (row 255 marks a slot past the columns)
+  uint32_t pk[kOzPer];
+#pragma unroll
+  for (int u = 0; u < kOzPer; ++u) {
+    int c, j;
+    oz_elem(stid + u * snthr, &c, &j);
+    pk[u] = c < Nc ? tile_off<ESZ>(c, j) | ((uint32_t)c << 16) | ((uint32_t)j << 24)
+                   : (255u << 16);
+  }
   auto fetch_chunk = [&](int ch2) {
 #pragma unroll
     for (int u = 0; u < kOzPer; ++u) {
-      int c, j;
-      oz_elem(stid + u * snthr, &c, &j);
-      cvn[u] = (ch2 < nsub && c < Nc) ? src.fetch(c, ch2 * kTcKC + j) : make_float2(0.f, 0.f);
+      const int c = (pk[u] >> 16) & 255, j = pk[u] >> 24;
+      cvn[u] = (ch2 < nsub && c != 255) ? src.fetch(c, ch2 * kTcKC + j) : make_float2(0.f, 0.f);
     }
   };
   if (warp != 0) fetch_chunk(0);
   for (int ch = 0; ch < nsub; ++ch) {
-    const int s = ch & 1;
+    const int s = ch % kOzStages, use = ch / kOzStages;  // use: earlier commits on bars[s]
     const int grp = ch / kOzGroup, q = ch - grp * kOzGroup;
     const int base = ch * kTcKC;
     bool tmo = false;  // this thread's wait for the buffer ran out
     if (warp != 0) {
-      tmo = ch >= 2 && !mbar_wait(&bars[s], ((ch - 2) >> 1) & 1);
+      tmo = use >= 1 && !mbar_wait(&bars[s], (use - 1) & 1);
       float2 cv[kOzPer];
 #pragma unroll
       for (int u = 0; u < kOzPer; ++u) cv[u] = cvn[u];
       fetch_chunk(ch + 1);
 #pragma unroll
       for (int u = 0; u < kOzPer; ++u) {
-        int c, j;
-        oz_elem(stid + u * snthr, &c, &j);
-        if (c >= Nc) continue;  // rows past the columns stay zero
+        const int c = (pk[u] >> 16) & 255, j = pk[u] >> 24;
+        if (c == 255) continue;  // rows past the columns stay zero
         float vh, vl, wh, wl, bh, bl;
         src.make(c, base + j, cv[u], &vh, &vl);
         src.weight(base + j, &wh, &wl);
@@ -726,7 +733,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(Src src, int n_tile) 
         const float sa = __int_as_float((127 - s_ea[c]) << 23);
         uint16_t da[kOzSlices];
         oz_digits(bh * sa, bl * sa, da);
-        const uint32_t off = tile_off<ESZ>(c, j);
+        const uint32_t off = pk[u] & 0xffffu;
 #pragma unroll
         for (int k = 0; k < kOzSlices; ++k)
           *reinterpret_cast<uint16_t*>(a_plane(s, k) + off) = da[k];
@@ -769,7 +776,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(Src src, int n_tile) 
       // the group's exact levels: wait for its MMAs, read them back, add them as integers (the
       // next group's first MMAs overwrite the tiles only after the barrier below)
       __syncthreads();
-      if (!mbar_wait(&bars[s], (ch >> 1) & 1) && tid == 0) s_ok = 0;
+      if (!mbar_wait(&bars[s], use & 1) && tid == 0) s_ok = 0;
       __syncthreads();
       if (!s_ok) break;
       tc_fence_after();
@@ -793,7 +800,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(Src src, int n_tile) 
   __syncthreads();
   // drain: every MMA issued is complete before the tensor memory is read or freed
   const int last = s_last;
-  const bool drained = last < 0 || mbar_wait(&bars[last & 1], (last >> 1) & 1);
+  const bool drained =
+      last < 0 || mbar_wait(&bars[last % kOzStages], (last / kOzStages) & 1);
   __syncthreads();
   if (!drained && tid == 0) s_ok = 0;
   __syncthreads();
@@ -858,7 +866,7 @@ cudaError_t launch_gram_tc_src(int mode, const Src& src, int nblk, int n_cols, c
   return cudaGetLastError();
 }
 
-size_t gram_oz_smem(int) { return 2 * (size_t)kOzSlices * kTcM * kTcKC * 2; }
+size_t gram_oz_smem(int) { return (size_t)kOzStages * kOzSlices * kTcM * kTcKC * 2; }
 
 template <class Src>
 cudaError_t launch_gram_oz_src(const Src& src, int nblk, int n_cols, int n_pix, int n_d,
