@@ -101,8 +101,8 @@ typedef struct {
 #define PSFM_PREC_F32X2 4    /* design and Gram in double-float (FP32 pairs, ~48 bits) */
 #define PSFM_PREC_BF16X6 5   /* double-float design; Gram on the tensor cores as
                                 (sqrt(w) C)^T (sqrt(w) C) from seven BF16 slices of the scaled
-                                columns, exact per-level sums (>= 48 bits; at most 64 augmented
-                                columns) */
+                                columns, exact per-level sums (>= 48 bits); a basis with more
+                                than 64 augmented columns takes the double-float Gram */
 
 /* Options; psfm_config_default() fills the defaults noted in brackets. */
 typedef struct {

@@ -1784,8 +1784,10 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
   // TF32 / BF16X3: FP32 design blocks, the Gram on the tensor cores (k_gram_tc.cu)
   // BF16X6: double-float design blocks, the Gram on the tensor cores from exact split products
   const bool tcm = prec == PSFM_PREC_TF32 || prec == PSFM_PREC_BF16X3;
-  const bool ozm = prec == PSFM_PREC_BF16X6;
-  const bool dfm = prec == PSFM_PREC_F32X2 || ozm;
+  // the split-product tensor-core Gram takes up to 64 augmented columns (one N = 64 tile);
+  // wider BF16X6 bases use the double-float Gram
+  const bool ozm = prec == PSFM_PREC_BF16X6 && p.Nc <= 64;
+  const bool dfm = prec == PSFM_PREC_F32X2 || prec == PSFM_PREC_BF16X6;  // double-float design
   auto design = prec == PSFM_PREC_FP64 ? k_stamp_design<double> : k_stamp_design<float>;
   auto gram = prec == PSFM_PREC_FP64 ? k_stamp_gram<double>
               : dfm ? k_stamp_gram_df : k_stamp_gram<float>;

@@ -155,9 +155,8 @@ psfm_status make_plan(Plan& p, psfm_shape shape, const psfm_basis_spec* b, const
   // the tensor-core Gram holds the augmented block in one 128-lane accumulator tile
   if ((c->precision == PSFM_PREC_TF32 || c->precision == PSFM_PREC_BF16X3) && p.Nc > 128)
     return PSFM_ERR_UNSUPPORTED;
-  // the split-product Gram holds its four exact levels and the small ones in tensor memory for
-  // one N = 64 tile
-  if (c->precision == PSFM_PREC_BF16X6 && p.Nc > 64) return PSFM_ERR_UNSUPPORTED;
+  // (PSFM_PREC_BF16X6: the split-product Gram holds one N = 64 tile; a basis with more
+  // augmented columns takes the double-float Gram, with the same double-float design)
   return PSFM_OK;
 }
 

@@ -70,6 +70,24 @@ def test_solve_small_field_with_extractor(dev, prec):
     _check_solution(sol, osol, ob, 512, 512)
 
 
+def test_wide_basis_in_split_product_mode_takes_the_double_float_gram(dev):
+    """A basis with more than 64 augmented columns (degrees 6, 6, 2: 62 terms, 65 columns) in
+    PREC_BF16X6 solves with the double-float Gram: the same kernels as PREC_F32X2, so the same
+    bits."""
+    f = synth.small_gaussian_field(1)
+    t = upload(f, dev, pad=3)
+    sols = []
+    for prec in (P.PREC_BF16X6, P.PREC_F32X2):
+        b, c, ob, oc = specs((0.7, 1.5, 3.0), (6, 6, 2), 10, 0, badmask=synth.BADMASK,
+                             precision=prec)
+        assert P.basis_size(b) == 62
+        sols.append(P.psfm_solve_kernel(t["sci"], t["ref"], t["var_sci"], t["var_ref"],
+                                        t["mask_sci"], t["mask_ref"], b, c))
+    a, f32 = sols
+    assert np.array_equal(a.coeff, f32.coeff)
+    assert a.b0 == f32.b0 and a.n_iter == f32.n_iter and a.n_used == f32.n_used
+
+
 @pytest.mark.parametrize("prec", PRECISIONS)
 @pytest.mark.parametrize("mode", ["separate", "joint"])
 def test_solve_spatial_order_2_with_rejection(dev, mode, prec):
