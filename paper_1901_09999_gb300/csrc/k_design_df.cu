@@ -110,7 +110,8 @@ __device__ __forceinline__ void vpass(const float2* H, int sw, int sw2, const fl
         }
       }
       const bool any_odd = nq - q0 > 1;
-#pragma unroll
+      // partly unrolled: the fully unrolled passes of every q outgrow the instruction cache
+#pragma unroll 5
       for (int u = 1; u <= HW; ++u) {
         df sm[kVc], df_[kVc];
 #pragma unroll

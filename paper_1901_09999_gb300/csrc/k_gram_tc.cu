@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(Src src, int n_tile) 
   const int Nc = src.ncols(), npix = src.npix();
   // one operand: the slices of sqrt(w) A; the B operand of every MMA is the first n_tile rows
   // of an A slice (the same K-major layout)
-  const uint32_t a_bytes = kTcM * kTcKC * ESZ;
+  constexpr uint32_t a_bytes = kTcM * kTcKC * ESZ;
   const uint32_t stage_bytes = kOzSlices * a_bytes;
   auto a_plane = [&](int s, int k) { return tc_sh + s * stage_bytes + k * a_bytes; };
   // ---- column scales: the largest |sqrt(w) value| of every column (FP32 estimates)
@@ -748,14 +748,19 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(Src src, int n_tile) 
     }
     if (tid == 0) {
       tc_fence_after();
+      // the descriptors of this stage's slices and K steps differ only in the start-address
+      // field ((address & 0x3FFFF) >> 4, shared memory being below 256 KB): one descriptor and
+      // constant offsets
+      const uint64_t d0 = smem_desc(smem_u32(a_plane(s, 0)), 128, sbo);
+#pragma unroll
       for (int k0 = 0; k0 < kTcKC; k0 += 16) {
         const uint32_t koff = (uint32_t)(k0 / 8) * 128;
 #pragma unroll
         for (int i = 0; i < kOzSlices; ++i) {
-          const uint64_t ad = smem_desc(smem_u32(a_plane(s, i)) + koff, 128, sbo);
+          const uint64_t ad = d0 + ((i * a_bytes + koff) >> 4);
 #pragma unroll
           for (int j = 0; i + j < kOzSlices; ++j) {
-            const uint64_t bd = smem_desc(smem_u32(a_plane(s, j)) + koff, 128, sbo);
+            const uint64_t bd = d0 + ((j * a_bytes + koff) >> 4);
             const int L = i + j;
             uint32_t dst, accf;
             if (L < kOzExact) {
@@ -818,9 +823,15 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(Src src, int n_tile) 
         const int d = col0 + j;
         if (d <= row && d < Nc) {
           const double small = (double)rv0[j];
-          // acc is in units of 2^(-8 (kOzExact + 1)), the unit of the last exact level
-          const double g =
-              ldexp(ldexp((double)acc[j], -8 * (kOzExact + 1)) + small, s_ea[row] + s_ea[d]);
+          // acc is in units of 2^(-8 (kOzExact + 1)), the unit of the last exact level; the
+          // column scales as an exact power of two built from its exponent bits (ldexp where
+          // the exponent leaves the normal range)
+          const double lev = (double)acc[j] * 0x1p-48 + small;
+          static_assert(8 * (kOzExact + 1) == 48, "unit of the exact levels");
+          const int e = s_ea[row] + s_ea[d];
+          const double g = (e > -1000 && e < 1000)
+                               ? lev * __longlong_as_double((long long)(1023 + e) << 52)
+                               : ldexp(lev, e);
           Gr[row * Nc + d] = g;
           Gr[d * Nc + row] = g;
         }
