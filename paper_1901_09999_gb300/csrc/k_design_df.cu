@@ -20,9 +20,10 @@ namespace psfm {
 namespace {
 
 constexpr int kDesignThreads = 256;
-// vertical outputs of one plane formed together from one set of mirrored sums (every q of a
-// plane up to degree 7; a degree-8 Gaussian's first plane takes two groups)
-constexpr int kVq = 8;
+// vertical outputs of one plane formed together from one set of mirrored sums (planes with
+// more q take several groups, each forming its sums again: smaller code, measured faster than
+// eight at a time, which outgrew the instruction cache)
+constexpr int kVq = 4;
 // footprint elements staged per thread per round
 constexpr int kStageBatch = 8;
 // neighbouring outputs of one row per thread in the horizontal pass, and neighbouring columns
