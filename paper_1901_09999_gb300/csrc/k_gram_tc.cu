@@ -11,6 +11,8 @@
 // tcgen05.commit arrives on the buffer's mbarrier when they have consumed it.  Every wait is
 // bounded: a wait that runs out records PSFM_ERR_TIMEOUT and the CTA still frees its tensor
 // memory before it returns.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 
 #include "psfm_internal.h"
@@ -419,16 +421,23 @@ __device__ __forceinline__ void oz_digits(float h, float l, uint16_t out[kOzSlic
 // shared memory once, so that the two passes over the stamp read only the design block.
 struct OzStampSource {
   StampParams P;
-  int r, cx, cy;
+  // nsplit > 1: block blk takes part blk % nsplit (a range of 32-pixel chunks) of stamp
+  // blk / nsplit and writes a partial Gram; the last part to finish adds the partials
+  int nsplit;
+  int r, cx, cy, part, pix0, np;
   float *wh, *wl, *xr, *xi, *ph, *pl, *sh, *sl;  // shared memory, set by prepare()
   __device__ bool open(int blk) {
-    r = blk;
+    r = blk / nsplit;
+    part = blk - r * nsplit;
+    const int nch = (P.P + kTcKC - 1) / kTcKC;  // >= nsplit (checked by the launch)
+    pix0 = (part * nch / nsplit) * kTcKC;
+    np = min(((part + 1) * nch / nsplit) * kTcKC, P.P) - pix0;
     if (P.st->error || P.st->done) return false;
     if (!region_active(P.ptr, P.cand, r, P.max_cand, &cx, &cy)) return false;
     return P.have[r] != P.ptr[r];
   }
   __device__ int ncols() const { return P.Nc; }
-  __device__ int npix() const { return P.P; }
+  __device__ int npix() const { return np; }
   __host__ __device__ static size_t prep_floats(int npix, int nd) {
     return 4 * (size_t)npix + 4 * (size_t)nd;
   }
@@ -444,7 +453,8 @@ struct OzStampSource {
     sl = sh + nd;
   }
   __device__ void prepare(int tid, int nthr) {
-    for (int pix = tid; pix < P.P; pix += nthr) {
+    for (int lp = tid; lp < np; lp += nthr) {
+      const int pix = pix0 + lp;
       const int py = pix / P.sw, px = pix - py * P.sw;
       const int gx = cx - P.s + px, gy = cy - P.s + py;
       float a = 0.f, b = 0.f, h = 0.f, l = 0.f;
@@ -471,10 +481,10 @@ struct OzStampSource {
           l = (float)(sq - (double)h);
         }
       }
-      xr[pix] = a;
-      xi[pix] = b;
-      wh[pix] = h;
-      wl[pix] = l;
+      xr[lp] = a;
+      xi[lp] = b;
+      wh[lp] = h;
+      wl[lp] = l;
     }
     const int nbk = P.b.Nb;
     for (int c = tid; c < P.Nd; c += nthr) {
@@ -486,19 +496,20 @@ struct OzStampSource {
       sl[c] = (float)(skd - (double)sh[c]);
     }
   }
+  // pixel indices from here on are the part's (0 .. np - 1)
   __device__ void weight(int pix, float* h, float* l) const {
-    *h = pix < P.P ? wh[pix] : 0.f;
-    *l = pix < P.P ? wl[pix] : 0.f;
+    *h = pix < np ? wh[pix] : 0.f;
+    *l = pix < np ? wl[pix] : 0.f;
   }
   // the design value of column c at pixel pix (the global load, issued ahead of its use)
   __device__ float2 fetch(int c, int pix) const {
-    if (pix >= P.P || c >= P.Nd) return make_float2(0.f, 0.f);
-    return reinterpret_cast<const float2*>(P.C)[((int64_t)r * P.Nd + c) * P.P + pix];
+    if (pix >= np || c >= P.Nd) return make_float2(0.f, 0.f);
+    return reinterpret_cast<const float2*>(P.C)[((int64_t)r * P.Nd + c) * P.P + pix0 + pix];
   }
   __device__ void make(int c, int pix, float2 cv, float* vh, float* vl) const {
     *vh = 0.f;
     *vl = 0.f;
-    if (pix >= P.P || c >= P.Nc) return;
+    if (pix >= np || c >= P.Nc) return;
     const int Nd = P.Nd, nbk = P.b.Nb;
     if (c < Nd) {
       // psi C - s X in double-float, X = masked R (or I2 for the dual kernel's terms)
@@ -527,9 +538,33 @@ struct OzStampSource {
     else if (c == Nd + 1) *vh = 1.f;
     else *vh = xi[pix];
   }
-  __device__ double* gram() const { return P.Gt + (int64_t)r * P.Nc * P.Nc; }
+  __device__ double* gram() const {
+    const int64_t n2 = (int64_t)P.Nc * P.Nc;
+    return nsplit == 1 ? P.Gt + r * n2 : P.Gpart + ((int64_t)r * kGramSplit + part) * n2;
+  }
   __device__ void fail(int code) const { atomicCAS(&P.st->error, 0, code); }
+  // after the block's Gram (or partial) is written, by every thread of the block
   __device__ void finish(int tid) const {
+    if (nsplit > 1) {
+      __shared__ int s_lastp;
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) s_lastp = atomicAdd(&P.gram_count[r], 1) == nsplit - 1;
+      __syncthreads();
+      if (!s_lastp) return;
+      __threadfence();
+      // the partials added in part order, so the Gram does not depend on which part ends last
+      const int n2 = P.Nc * P.Nc;
+      const double* Gp0 = P.Gpart + (int64_t)r * kGramSplit * n2;
+      double* Gr = P.Gt + (int64_t)r * n2;
+      for (int q = tid; q < n2; q += blockDim.x) {
+        double v = 0.0;
+        for (int k = 0; k < nsplit; ++k) v += __ldcg(Gp0 + (int64_t)k * n2 + q);
+        Gr[q] = v;
+      }
+      __syncthreads();
+      if (tid == 0) P.gram_count[r] = 0;
+    }
     if (tid == 0) {
       P.have[r] = P.ptr[r];
       P.fresh[r] = 1;
@@ -893,10 +928,13 @@ cudaError_t launch_gram_oz_src(const Src& src, int nblk, int n_cols, int n_pix, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_gram_oz(const StampParams& sp, int nreg, cudaStream_t s) {
+cudaError_t launch_gram_oz(const StampParams& sp, int nreg, int nsplit, cudaStream_t s) {
+  const int nch = (sp.P + kTcKC - 1) / kTcKC;
+  nsplit = std::max(1, std::min({nsplit, kGramSplit, nch}));
   OzStampSource src;
   src.P = sp;
-  return launch_gram_oz_src(src, nreg, sp.Nc, sp.P, sp.Nd, s);
+  src.nsplit = nsplit;
+  return launch_gram_oz_src(src, nreg * nsplit, sp.Nc, sp.P, sp.Nd, s);
 }
 
 cudaError_t launch_gram_oz_plain(const float* cols, const float* w, int n_blocks, int n_cols,

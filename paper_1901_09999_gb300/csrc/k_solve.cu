@@ -30,7 +30,7 @@
 namespace psfm {
 
 cudaError_t launch_gram_tc(int mode, const StampParams& sp, int nreg, cudaStream_t s);
-cudaError_t launch_gram_oz(const StampParams& sp, int nreg, cudaStream_t s);
+cudaError_t launch_gram_oz(const StampParams& sp, int nreg, int nsplit, cudaStream_t s);
 size_t design_df_smem(int foot, int sw, int h, int dmax);
 cudaError_t launch_design_df(int h, dim3 grid, size_t smem, const StampParams& sp,
                              cudaStream_t s);
@@ -1834,7 +1834,10 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
       if (launch_gram_tc(prec == PSFM_PREC_TF32 ? 0 : 1, sp, p.nreg, s) != cudaSuccess)
         return PSFM_ERR_CUDA;
     } else if (ozm) {
-      if (launch_gram_oz(sp, p.nreg, s) != cudaSuccess) return PSFM_ERR_CUDA;
+      // the first iteration's Grams fill the GPU one stamp per CTA; the few stamps replaced in
+      // later iterations split over kGramSplit CTAs each, which shortens the solve's chain
+      if (launch_gram_oz(sp, p.nreg, it == 0 ? 1 : kGramSplit, s) != cudaSuccess)
+        return PSFM_ERR_CUDA;
     } else {
       gram<<<dim3(p.nreg, dfm ? kGramSplit : 1), dfm ? kGramThreads : 256, sm_gram, s>>>(sp);
     }
