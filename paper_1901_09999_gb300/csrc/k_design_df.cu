@@ -153,6 +153,51 @@ __device__ __forceinline__ void vpass(const float2* H, int sw, int sw2, const fl
   }
 }
 
+// Footprint staging: kStageBatch elements per thread per round, all of their loads (masks and
+// pixels, independent of each other) issued before any is used.  SUMS: also the unweighted
+// footprint sums of the normalisation (Sec. 3.2) in FP64, only in the one block per stamp that
+// forms them (the FP64 adds of every element would otherwise be issued, predicated off, by all
+// blocks).
+template <bool SUMS>
+__device__ __forceinline__ void stage_footprint(const StampParams& P, int set, float* F, int fs,
+                                                int foot, int x0, int y0, int tid, double* f1,
+                                                double* f2, double* nf) {
+  const int nst = foot * fs;
+  for (int i0 = tid; i0 < nst; i0 += kStageBatch * kDesignThreads) {
+    int64_t off[kStageBatch];
+    bool in[kStageBatch];
+#pragma unroll
+    for (int e = 0; e < kStageBatch; ++e) {
+      const int i = i0 + e * kDesignThreads;
+      const int rr = i / fs, cc = i - rr * fs;
+      const int gx = x0 + cc, gy = y0 + rr;
+      in[e] = i < nst && cc < foot && gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H;
+      off[e] = in[e] ? (int64_t)gy * P.g.pitch + gx : 0;
+    }
+    uint16_t ma[kStageBatch], mb[kStageBatch];
+    float va[kStageBatch], vb[kStageBatch];
+#pragma unroll
+    for (int e = 0; e < kStageBatch; ++e) {
+      ma[e] = in[e] ? P.m1[off[e]] : (uint16_t)0;
+      mb[e] = in[e] ? P.m2[off[e]] : (uint16_t)0;
+      va[e] = in[e] ? (set == 0 ? P.i1[off[e]] : P.i2[off[e]]) : 0.f;
+      vb[e] = (SUMS && in[e]) ? P.i2[off[e]] : 0.f;
+    }
+#pragma unroll
+    for (int e = 0; e < kStageBatch; ++e) {
+      const int i = i0 + e * kDesignThreads;
+      if (i >= nst) break;
+      const bool a = (ma[e] & P.badmask) != 0, b = (mb[e] & P.badmask) != 0;
+      F[i] = (set == 0 ? a : b) ? 0.f : va[e];
+      if (SUMS && in[e] && !a && !b) {
+        *f1 += va[e];
+        *f2 += vb[e];
+        *nf += 1.0;
+      }
+    }
+  }
+}
+
 template <int HW>
 __global__ void __launch_bounds__(kDesignThreads, 3) k_stamp_design_df(StampParams P) {
   constexpr int W = 2 * HW + 1;
@@ -185,42 +230,10 @@ __global__ void __launch_bounds__(kDesignThreads, 3) k_stamp_design_df(StampPara
   const int x0 = cx - P.s - HW, y0 = cy - P.s - HW;
   const bool sums = set == 0 && pl == 0;
   double f1 = 0.0, f2 = 0.0, nf = 0.0;
-  // footprint staging: kStageBatch elements per thread per round, all of their loads (masks
-  // and pixels, independent of each other) issued before any is used
-  const int nst = foot * fs;
-  for (int i0 = tid; i0 < nst; i0 += kStageBatch * kDesignThreads) {
-    int64_t off[kStageBatch];
-    bool in[kStageBatch];
-#pragma unroll
-    for (int e = 0; e < kStageBatch; ++e) {
-      const int i = i0 + e * kDesignThreads;
-      const int rr = i / fs, cc = i - rr * fs;
-      const int gx = x0 + cc, gy = y0 + rr;
-      in[e] = i < nst && cc < foot && gx >= 0 && gx < P.g.W && gy >= 0 && gy < P.g.H;
-      off[e] = in[e] ? (int64_t)gy * P.g.pitch + gx : 0;
-    }
-    uint16_t ma[kStageBatch], mb[kStageBatch];
-    float va[kStageBatch], vb[kStageBatch];
-#pragma unroll
-    for (int e = 0; e < kStageBatch; ++e) {
-      ma[e] = in[e] ? P.m1[off[e]] : (uint16_t)0;
-      mb[e] = in[e] ? P.m2[off[e]] : (uint16_t)0;
-      va[e] = in[e] ? (set == 0 ? P.i1[off[e]] : P.i2[off[e]]) : 0.f;
-      vb[e] = in[e] && sums ? P.i2[off[e]] : 0.f;
-    }
-#pragma unroll
-    for (int e = 0; e < kStageBatch; ++e) {
-      const int i = i0 + e * kDesignThreads;
-      if (i >= nst) break;
-      const bool a = (ma[e] & P.badmask) != 0, b = (mb[e] & P.badmask) != 0;
-      F[i] = (set == 0 ? a : b) ? 0.f : va[e];
-      if (sums && in[e] && !a && !b) {
-        f1 += va[e];
-        f2 += vb[e];
-        nf += 1.0;
-      }
-    }
-  }
+  if (sums)
+    stage_footprint<true>(P, set, F, fs, foot, x0, y0, tid, &f1, &f2, &nf);
+  else
+    stage_footprint<false>(P, set, F, fs, foot, x0, y0, tid, &f1, &f2, &nf);
   if (sums) {
     // unweighted footprint sums for the normalisation (Sec. 3.2)
     __shared__ double red[3][kDesignThreads / 32];
