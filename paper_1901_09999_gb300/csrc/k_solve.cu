@@ -1459,6 +1459,10 @@ __global__ void __launch_bounds__(kChi2Threads, 4) k_chi2(Chi2Params Q) {
   const float alpha_f = (float)Q.alpha;
   const T* Cr = reinterpret_cast<const T*>(P.C) + (int64_t)r * Nd * P.P;
   double q = 0.0, n = 0.0;
+  // double-float blocks: each thread's few terms (at most kChi2Px per pass over the stamp)
+  // summed in FP32 and counted as an integer, FP64 from the warp sums on
+  float qf = 0.f;
+  int ni = 0;
   constexpr int kStride = kChi2Split * kChi2Threads * kChi2Px;
   for (int base = split * kChi2Threads * kChi2Px + tid; base < P.P; base += kStride) {
     int pix[kChi2Px];
@@ -1507,8 +1511,8 @@ __global__ void __launch_bounds__(kChi2Threads, 4) k_chi2(Chi2Params Q) {
         const df res = df_add(df{I2v[j], 0.f}, df_neg(m));
         const float r = __fadd_rn(res.hi, res.lo);
         const float den = __fadd_rn(Vs[j], __fmul_rn(alpha_f, fabsf(I2v[j])));
-        q += (double)__fdiv_rn(__fmul_rn(r, r), den);
-        n += 1.0;
+        qf = __fadd_rn(qf, __fdiv_rn(__fmul_rn(r, r), den));
+        ++ni;
       }
     } else {
       double mod[kChi2Px];
@@ -1526,6 +1530,8 @@ __global__ void __launch_bounds__(kChi2Threads, 4) k_chi2(Chi2Params Q) {
       }
     }
   }
+  q += (double)qf;
+  n += (double)ni;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     q += __shfl_xor_sync(0xffffffffu, q, o);
