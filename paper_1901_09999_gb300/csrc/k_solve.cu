@@ -678,23 +678,24 @@ __global__ void __launch_bounds__(256) k_system_delta(SysParams P, int mode, int
     }
     __syncthreads();
     if (mine) {
-      // four independent partial sums keep four Gram loads in flight (fixed order)
+      // eight independent partial sums keep eight Gram loads in flight (fixed order)
       const double* Gr = P.Gt + (int64_t)r0 * Nc * Nc + gij;
       const double* gq = gsh + pidx;
       const int64_t gs = (int64_t)Nc * Nc;
       const int ps = N1 * N1;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      double a[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = 0.0;
       int f = 0;
-      for (; f + 3 < nf; f += 4) {
-        const double g0 = Gr[list[f] * gs], g1 = Gr[list[f + 1] * gs];
-        const double g2 = Gr[list[f + 2] * gs], g3 = Gr[list[f + 3] * gs];
-        a0 = fma(gq[f * ps], g0, a0);
-        a1 = fma(gq[(f + 1) * ps], g1, a1);
-        a2 = fma(gq[(f + 2) * ps], g2, a2);
-        a3 = fma(gq[(f + 3) * ps], g3, a3);
+      for (; f + 7 < nf; f += 8) {
+        double g[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) g[k] = Gr[list[f + k] * gs];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(gq[(f + k) * ps], g[k], a[k]);
       }
-      for (; f < nf; ++f) a0 = fma(gq[f * ps], Gr[list[f] * gs], a0);
-      acc += (a0 + a1) + (a2 + a3);
+      for (; f < nf; ++f) a[0] = fma(gq[f * ps], Gr[list[f] * gs], a[0]);
+      acc += ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     }
   }
   if (!mine) return;
