@@ -641,12 +641,19 @@ __global__ void __launch_bounds__(256) k_system_delta(SysParams P, int mode, int
   const int Ns = P.b.Ns, N1 = Ns + 1, Nc = P.Nc, N = P.Nsys;
   const int32_t* flag = mode == 0 ? P.fresh : P.removed;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // one thread per entry of the upper triangle (uj >= ui), row by row: row i starts at
+  // i N - i (i - 1) / 2
   int ui = 0, uj = 0, ai = 0, aj = 0, si = -1, sj = -1;
-  bool mine = t < (int64_t)N * N;
+  const bool mine = t < (int64_t)N * (N + 1) / 2;
   if (mine) {
-    ui = (int)(t / N);
-    uj = (int)(t - (int64_t)ui * N);
-    mine = uj >= ui;
+    const float b = 2.f * N + 1.f;
+    int i = (int)((b - sqrtf(fmaxf(b * b - 8.f * (float)t, 0.f))) * 0.5f);
+    i = max(0, min(N - 1, i));
+    auto start = [&](int k) { return (int64_t)k * N - (int64_t)k * (k - 1) / 2; };
+    while (i > 0 && start(i) > t) --i;
+    while (i + 1 < N && start(i + 1) <= t) ++i;
+    ui = i;
+    uj = ui + (int)(t - start(i));
     unknown_col(P, ui, &ai, &si);
     unknown_col(P, uj, &aj, &sj);
   }
@@ -1805,7 +1812,7 @@ psfm_status run_solve(const Plan& p, const DevTables& t, DevState* st, double* d
           cudaSuccess)
     return PSFM_ERR_CUDA;
   const int N = p.Nsys;
-  const int64_t nthr = (int64_t)N * N;
+  const int64_t nthr = (int64_t)N * (N + 1) / 2;  // the assembly's upper-triangle entries
   const int N1 = p.Ns + 1;
   const int asm_chunk = (40 * 1024) / (N1 * N1 * (int)sizeof(double));
   // the rejection kernel works per region: one thread each (FP64 reductions over idle warps
